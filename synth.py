@@ -1,0 +1,208 @@
+"""Seeded synthetic point clouds and random inputs.
+
+This module is shared by the tests, the benchmark and the smoke check.  It
+holds the random streams and the shape samplers only: nothing here evaluates
+a winding number or touches the orientation method.
+
+Random numbers come from a counter-based generator, splitmix64 (Steele,
+Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA
+2014): value i of stream (seed, stream) is splitmix64's output function
+applied to  key + (i + 1) * GAMMA,  with  key = mix(seed * 2^32 + stream).
+Uniform doubles take the top 53 bits.  The CUDA library implements the same
+definition for its on-device random normal initialisation, so the two can be
+compared without passing numbers between them.
+
+Shapes are generated in float64 and returned as float32 (the library's input
+type); analytic normals are returned alongside for orientation checks.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    """splitmix64 output function on uint64 arrays (wrapping arithmetic)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_key(seed: int, stream: int) -> np.uint64:
+    s = (np.uint64(seed & 0xFFFFFFFF) << np.uint64(32)) | np.uint64(stream & 0xFFFFFFFF)
+    return _mix(np.array([s], dtype=np.uint64))[0]
+
+
+def u64(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    key = stream_key(seed, stream)
+    i = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix(key + i * GAMMA)
+
+
+def uniform(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1): top 53 bits of each 64-bit value times 2^-53."""
+    return (u64(seed, stream, count, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, stream: int, count: int) -> np.ndarray:
+    """Standard normals by Box-Muller on consecutive uniform pairs."""
+    m = (count + 1) // 2
+    u = uniform(seed, stream, 2 * m)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
+    out = np.empty(2 * m)
+    out[0::2] = z[:m]
+    out[1::2] = z[m:]
+    return out[:count]
+
+
+def random_unit_normals(n: int, seed: int, stream: int = 7) -> np.ndarray:
+    """Uniform directions on S^2: z = 1 - 2 u0, phi = 2 pi u1 (uniforms 2i, 2i+1).
+
+    This is the definition the library's on-device RANDOM initialisation
+    follows (it evaluates it in float32 arithmetic).
+    """
+    u = uniform(seed, stream, 2 * n).reshape(n, 2)
+    z = 1.0 - 2.0 * u[:, 0]
+    phi = 2.0 * np.pi * u[:, 1]
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
+
+
+def _as_f32(p: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(p, dtype=np.float32)
+
+
+def bbox_diag(p: np.ndarray) -> float:
+    p = np.asarray(p, dtype=np.float64)
+    return float(np.linalg.norm(p.max(0) - p.min(0)))
+
+
+# ----------------------------------------------------------------------------
+# shapes
+# ----------------------------------------------------------------------------
+
+def sphere(n: int, seed: int = 0, radius: float = 1.0, center=(0.0, 0.0, 0.0)):
+    """Uniform points on a sphere by normalising isotropic Gaussians."""
+    g = normal(seed, 1, 3 * n).reshape(n, 3)
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    p = np.asarray(center) + radius * g
+    return _as_f32(p), g.copy()
+
+
+def fibonacci_sphere(n: int, radius: float = 1.0):
+    """Deterministic near-uniform sphere sampling (golden-angle spiral)."""
+    i = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * i / n
+    phi = np.pi * (3.0 - math.sqrt(5.0)) * i
+    s = np.sqrt(1.0 - z * z)
+    u = np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
+    return _as_f32(radius * u), u
+
+
+def torus(n: int, seed: int = 0, R: float = 1.0, r: float = 0.3, noise: float = 0.0):
+    """Area-uniform samples on a torus about the z axis.
+
+    u (around the axis) is uniform; v (around the tube) is drawn by rejection
+    with acceptance (R + r cos v) / (R + r), which makes the density uniform
+    in area.  noise is the isotropic per-coordinate Gaussian sigma as a
+    fraction of the bounding-box diagonal of the clean torus.
+    """
+    pts = []
+    nrm = []
+    got = 0
+    batch = 0
+    while got < n:
+        m = 2 * (n - got) + 64
+        u = 2 * np.pi * uniform(seed, 100 + batch, m)
+        v = 2 * np.pi * uniform(seed, 200 + batch, m)
+        acc = uniform(seed, 300 + batch, m) < (R + r * np.cos(v)) / (R + r)
+        u, v = u[acc], v[acc]
+        cu, su, cv, sv = np.cos(u), np.sin(u), np.cos(v), np.sin(v)
+        pts.append(np.stack([(R + r * cv) * cu, (R + r * cv) * su, r * sv], 1))
+        nrm.append(np.stack([cv * cu, cv * su, sv], 1))
+        got += len(u)
+        batch += 1
+    p = np.concatenate(pts)[:n]
+    nt = np.concatenate(nrm)[:n]
+    if noise > 0:
+        diag = math.sqrt((2 * (R + r)) ** 2 * 2 + (2 * r) ** 2)
+        p = p + noise * diag * normal(seed, 400, 3 * n).reshape(n, 3)
+    return _as_f32(p), nt
+
+
+def ellipsoid_points(n: int, axes, seed: int, stream: int):
+    """Near-area-uniform ellipsoid samples (sphere samples, rejection on the
+    area-element ratio), with analytic outward normals."""
+    a = np.asarray(axes, dtype=np.float64)
+    out_p, out_n = [], []
+    got, b = 0, 0
+    while got < n:
+        m = 3 * (n - got) + 64
+        g = normal(seed, stream * 1000 + b, 3 * m).reshape(m, 3)
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        x = g * a
+        # the map S^2 -> ellipsoid, g -> a*g, scales area by prod(a) * |g / a|;
+        # |g / a| <= 1 / min(a), so accept with probability min(a) * |g / a|
+        acc = uniform(seed, stream * 1000 + b + 500, m) < a.min() * np.linalg.norm(g / a, axis=1)
+        x = x[acc]
+        nn = x / a ** 2
+        nn /= np.linalg.norm(nn, axis=1, keepdims=True)
+        out_p.append(x)
+        out_n.append(nn)
+        got += len(x)
+        b += 1
+    return np.concatenate(out_p)[:n], np.concatenate(out_n)[:n]
+
+
+def add_noise(p: np.ndarray, level: float, seed: int, stream: int = 900) -> np.ndarray:
+    """Isotropic Gaussian noise with sigma = level * bbox diagonal."""
+    p64 = np.asarray(p, dtype=np.float64)
+    sig = level * bbox_diag(p64)
+    return _as_f32(p64 + sig * normal(seed, stream, p64.size).reshape(p64.shape))
+
+
+def uniform_box(n: int, lo, hi, seed: int, stream: int = 950) -> np.ndarray:
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    u = uniform(seed, stream, 3 * n).reshape(n, 3)
+    return _as_f32(lo + u * (hi - lo))
+
+
+def default_eps(area_total: float, n: int) -> float:
+    """Softening length: half the mean point spacing sqrt(A / N)."""
+    return 0.5 * math.sqrt(area_total / max(n, 1))
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+
+def workload_sphere2k():
+    """2,000 uniform unit-sphere points (seed 0), area weight 4 pi / N."""
+    n = 2000
+    p, nt = sphere(n, seed=0)
+    a = np.full(n, 4 * np.pi / n, dtype=np.float32)
+    return dict(name="sphere-2k", points=p, normals_true=nt, weights=a,
+                eps=default_eps(4 * np.pi, n), depth=5, max_iters=30, tol=0.1)
+
+
+def workload_torus100k(noise: float = 0.005):
+    """100,000 torus points (R=1, r=0.3), Gaussian noise 0.5% of the diagonal."""
+    n = 100_000
+    R, r = 1.0, 0.3
+    p, nt = torus(n, seed=0, R=R, r=r, noise=noise)
+    area = 4 * np.pi ** 2 * R * r
+    a = np.full(n, area / n, dtype=np.float32)
+    return dict(name="torus-100k", points=p, normals_true=nt, weights=a,
+                eps=default_eps(area, n), depth=8, max_iters=30, tol=0.1)

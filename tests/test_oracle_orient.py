@@ -1,0 +1,57 @@
+"""The oracle's Algorithm 1 against analytic normals on closed shapes (CPU).
+
+The paper gives no worked example; what pins the iteration is the shapes'
+known outward normals: the converged normals must agree with them up to one
+global sign (the orientation is defined only up to a flip)."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def agreement(n, nt):
+    d = np.sum(n * nt, axis=1)
+    s = 1.0 if d.sum() >= 0 else -1.0
+    return float(np.mean(s * d > 0))
+
+
+def test_sphere_levelset_converges_to_analytic(oracle_mod):
+    W = synth.workload_sphere2k()
+    n0 = synth.random_unit_normals(2000, seed=1)
+    prm = oracle_mod.params(eps=W["eps"], depth=6, max_iters=40, tol=0.1)
+    r = oracle_mod.orient(W["points"], W["weights"], n0, prm)
+    assert r["converged"] and r["iters"] <= 30
+    assert agreement(r["normals"], W["normals_true"]) == 1.0
+    # converged normals are outward or inward as a whole; with outward ones
+    # w_bar approaches 1/2 (w = 1 inside, 0 outside), with inward ones -1/2
+    assert abs(abs(r["iso"][-1]) - 0.5) < 0.05
+    # mean alignment with the analytic normal (cf. Fig. 2's mean dot near 1)
+    s = np.sign(np.sum(r["normals"] * W["normals_true"]))
+    assert np.mean(s * np.sum(r["normals"] * W["normals_true"], axis=1)) > 0.98
+
+
+@pytest.mark.parametrize("lam,kernel", [(0.0, 0), (10.0, 1)])
+def test_torus_levelset_converges_to_analytic(oracle_mod, lam, kernel):
+    n = 3000
+    p, nt = synth.torus(n, seed=0)
+    area = 4 * np.pi ** 2 * 0.3
+    a = np.full(n, area / n)
+    n0 = synth.random_unit_normals(n, seed=1)
+    prm = oracle_mod.params(kernel=kernel, lam=lam, eps=synth.default_eps(area, n), depth=6,
+                            max_iters=40, tol=0.1)
+    r = oracle_mod.orient(p, a, n0, prm)
+    assert agreement(r["normals"], nt) >= 0.999
+    assert r["stat"][-1] < 1.0
+
+
+def test_point_gradient_update_stalls(oracle_mod):
+    """The point form n <- -grad w(p) / |grad w(p)| (one reading of Eq. 4)
+    does not orient a sphere consistently from random normals: it stalls in
+    domains of opposite orientation, which is why the level-set rule of
+    Eq. 7 is the update of the hot path."""
+    W = synth.workload_sphere2k()
+    n0 = synth.random_unit_normals(2000, seed=1)
+    prm = oracle_mod.params(eps=W["eps"], depth=6, max_iters=40, tol=0.1,
+                            mode=oracle_mod.MODE_DIRECT)
+    r = oracle_mod.orient(W["points"], W["weights"], n0, prm)
+    assert agreement(r["normals"], W["normals_true"]) < 0.9
