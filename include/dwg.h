@@ -1,0 +1,226 @@
+/*
+ * dwg.h -- C ABI of the Diffusing Winding Gradients engine (libdwg.so).
+ *
+ * The engine orients an unoriented point cloud by the iteration of the
+ * paper's Algorithm 1 (Diffusing Winding Gradients, arXiv 2405.13839,
+ * Sec. 4.3):
+ *   1. evaluate the generalized winding number w and its gradient at every
+ *      input point, and w at the corners of the leaves of an octree of depth
+ *      d around the cloud (Sec. 3 Eq. 2/3; screened variant Sec. 4.2 Eq. 5);
+ *   2. take the iso-value w_bar as the mean of w over the input points
+ *      (Eq. 6, averaged over the inputs as in the abstract and Sec. 4.1);
+ *   3. extract the w_bar level set in every leaf, give each face the
+ *      gradient from its cross product, add it to the face's k nearest input
+ *      points and normalise (Eq. 7);
+ *   4. stop when the mean of the largest 1% of the per-point normal changes
+ *      is at most tol degrees (Sec. 5.1, "Model-independent Parameters").
+ * Every step runs in this library's CUDA kernels on one GPU; there is no CPU
+ * fallback.  A call that needs the GPU and finds none returns DWG_ERR_CUDA.
+ *
+ * Conventions for every function below:
+ *   - Return value: DWG_OK (0), DWG_NOT_CONVERGED (1, informational), or a
+ *     negative DWG_ERR_* code; dwg_last_error() then describes the failure.
+ *   - Pointer arguments may be host memory (pageable or pinned) or device
+ *     memory of the handle's device; the library tells them apart with
+ *     cudaPointerGetAttributes.  The caller keeps ownership of every buffer
+ *     it passes; the library copies what it needs and never frees it.
+ *   - Point arrays are float32, n x 3, row-major (x, y, z per point), in the
+ *     caller's units: no implicit normalisation, so rotations and
+ *     translations of the input rotate and translate every result.
+ *   - All GPU work is issued on the handle's stream (dwg_set_stream), and
+ *     every function returns only after its results are in the caller's
+ *     buffers.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef DWG_H
+#define DWG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DWG_OK 0
+#define DWG_NOT_CONVERGED 1
+#define DWG_ERR_INVALID (-1)   /* bad argument or size */
+#define DWG_ERR_CUDA (-2)      /* CUDA error or no usable GPU */
+#define DWG_ERR_OOM (-3)       /* device allocation failed */
+#define DWG_ERR_NONFINITE (-4) /* NaN or Inf in an input */
+#define DWG_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define DWG_ERR_STATE (-6)     /* call not valid in the handle's state */
+
+/* GWN kernels: plain Poisson kernel (Eq. 3) or screened (Eq. 5). */
+#define DWG_KERNEL_PLAIN 0
+#define DWG_KERNEL_SCREENED 1
+
+/* Normal update: the level-set rule of Eq. 7 (default), or the point form
+ * n_i <- -grad w(p_i) / |grad w(p_i)| (a reading of Eq. 4 kept for study). */
+#define DWG_UPDATE_LEVELSET 0
+#define DWG_UPDATE_DIRECT 1
+
+/* Initial normals (Sec. 5.1): uniform random directions drawn on the
+ * device from a seed, or caller-given normals. */
+#define DWG_INIT_RANDOM 0
+#define DWG_INIT_GIVEN 1
+
+typedef struct dwg_ctx *dwg_handle;
+
+/*
+ * Create a handle for a cloud of n >= 1 points (float32 n x 3, host or
+ * device).  Copies the points to the current CUDA device, checks them for
+ * NaN/Inf (DWG_ERR_NONFINITE), sorts them along a Morton curve and builds
+ * the spatial structures that depend on positions only.  Area weights
+ * default to a_i = 1 (Sec. 5.1, "Computing Area Weights").  Default
+ * parameters: plain kernel, eps = 0.5 * L / sqrt(n) with L the largest
+ * bounding-box extent, no screening, 30 iterations, tol 0.1 degrees
+ * (Sec. 5.1), octree depth 8, k = 10 (Sec. 5.1), level-set update, random
+ * initialisation with seed 1.  On failure *out is NULL.
+ */
+int dwg_create(const float *points, int64_t n, dwg_handle *out);
+
+/* Release every device resource of the handle.  NULL is ignored. */
+void dwg_destroy(dwg_handle h);
+
+/* Text of the last failure on this handle, or of the last failed
+ * dwg_create when h is NULL.  Valid until the next call on the handle. */
+const char *dwg_last_error(dwg_handle h);
+
+/* Issue all further work of the handle on this cudaStream_t (NULL: the
+ * library's own stream).  The stream must belong to the handle's device. */
+int dwg_set_stream(dwg_handle h, void *stream);
+
+/*
+ * Method parameters.
+ *   kernel:    DWG_KERNEL_PLAIN or DWG_KERNEL_SCREENED.
+ *   eps:       softening length > 0, in the caller's length unit: every
+ *              kernel term uses rho^2 = |p - q|^2 + eps^2, the paper's
+ *              "small constant added to the denominator" (Sec. 3).
+ *   screening: lambda >= 0 of Eq. 5, in 1 / length^2; ignored for PLAIN.
+ *   max_iters: >= 1, iteration cap of dwg_orient.
+ *   tol:       > 0, convergence threshold in degrees (Sec. 5.1 uses 0.1).
+ */
+int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max_iters,
+                   float tol);
+
+/*
+ * Discretisation and update rule.
+ *   depth: octree depth d in [1, 14] (Sec. 5.1 recommends 8-10 up to 1M
+ *          points, 11-13 beyond).
+ *   knn:   k of Eq. 7's face-to-point assignment, in [1, 32] (paper: 10).
+ *   mode:  DWG_UPDATE_LEVELSET or DWG_UPDATE_DIRECT.
+ */
+int dwg_set_update(dwg_handle h, int depth, int knn, int mode);
+
+/* Area weights a_i > 0 (float32, n, input order, host or device). */
+int dwg_set_weights(dwg_handle h, const float *a);
+
+/*
+ * Initial normals for the next dwg_orient.  DWG_INIT_RANDOM draws uniform
+ * unit vectors from the splitmix64 stream (seed, 7): with u0, u1 the
+ * uniforms 2i and 2i+1 (top 53 bits * 2^-53), z = 1 - 2 u0,
+ * phi = 2 pi u1, n = (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z);
+ * normals is ignored.  DWG_INIT_GIVEN copies normals (float32 n x 3, input
+ * order, host or device; each is normalised, zero vectors rejected).
+ */
+int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals);
+
+/*
+ * Run Algorithm 1 from the initial normals until convergence or max_iters.
+ * normals_out (float32 n x 3, input order, host or device, may be NULL)
+ * receives the final normals; *iters_out (may be NULL) the number of
+ * iterations performed.  Returns DWG_NOT_CONVERGED if the cap was reached
+ * (the normals are still written).  The whole loop runs on the device: one
+ * CUDA graph launch whose conditional node repeats the iteration body.
+ */
+int dwg_orient(dwg_handle h, float *normals_out, int *iters_out);
+
+/*
+ * One iteration from the handle's current normals (the initial normals
+ * before the first orient or step, else the latest ones), updating them.
+ * Optional outputs in input order (each may be NULL, host or device):
+ * w_out (n) and grad_out (n x 3) at the input points for the normals the
+ * step started from; dtheta_out (n) the per-point change in degrees;
+ * iso_out the iso-value w_bar; stat_out the convergence statistic.
+ */
+int dwg_step(dwg_handle h, float *w_out, float *grad_out, float *dtheta_out, double *iso_out,
+             double *stat_out);
+
+/* Current normals (float32 n x 3, input order). */
+int dwg_get_normals(dwg_handle h, float *normals_out);
+
+/* Replace the current normals (same layout); they become the initial
+ * normals of the next dwg_step.  Zero vectors are rejected. */
+int dwg_set_normals(dwg_handle h, const float *normals);
+
+/*
+ * w (and, if grad_out is not NULL, grad w) of the current oriented cloud at
+ * m >= 1 arbitrary query points (float32 m x 3).  A query that coincides
+ * exactly with input points skips those terms, as at the inputs.
+ */
+int dwg_eval_gwn(dwg_handle h, const float *queries, int64_t m, float *w_out,
+                 float *grad_out);
+
+typedef struct {
+    int64_t n_points;
+    int64_t n_leaves;        /* octree leaves at the current depth */
+    int64_t n_corners;       /* distinct leaf corners (w query points) */
+    int iters;               /* iterations of the last dwg_orient */
+    int converged;
+    int64_t faces_last;      /* level-set faces of the last iteration */
+    double iso_last;         /* w_bar of the last iteration */
+    double stat_last;        /* convergence statistic of the last iteration */
+    double interactions;     /* kernel evaluations of the last dwg_orient */
+    double ms_orient;        /* device time of the last dwg_orient */
+} dwg_stats;
+
+int dwg_get_stats(dwg_handle h, dwg_stats *out);
+
+/* Per-iteration trace of the last dwg_orient: iso-value, convergence
+ * statistic (degrees), mean |n_new - n_old|, face count.  Arrays of cap
+ * entries (host memory, any may be NULL); *count receives the iterations. */
+int dwg_get_trace(dwg_handle h, double *iso, double *stat, double *mean_dn, int64_t *faces,
+                  int cap, int *count);
+
+/*
+ * Structures, for inspection and tests.
+ * dwg_get_leaves: octree leaves at the current depth as int64 records
+ *   (level, ix, iy, iz, nonempty), coordinates in units of the leaf's level,
+ *   sorted by (level, ix, iy, iz); cap records at most (host or device).
+ * dwg_get_corners: distinct leaf corners as sorted int64 keys
+ *   X * (2^d + 1)^2 + Y * (2^d + 1) + Z in depth-d lattice units.
+ * Both write *count (host) even when cap is too small (then nothing else).
+ */
+int dwg_get_leaves(dwg_handle h, int64_t *leaves_out, int64_t cap, int64_t *count);
+int dwg_get_corners(dwg_handle h, int64_t *keys_out, int64_t cap, int64_t *count);
+
+/*
+ * Per-kernel device times of one iteration, for profiling.  Runs one
+ * iteration exactly like dwg_step (same kernels, same launch shapes, on the
+ * handle's stream) with a CUDA event pair around each launch, and writes the
+ * elapsed milliseconds into ms_out (host, cap entries) in this fixed order:
+ *   0 eval_points    w and grad w at the input points (all-pairs)
+ *   1 reduce_points  combine the source-chunk partials, coincident terms
+ *   2 iso            w_bar
+ *   3 eval_corners   w at the octree leaf corners (all-pairs)
+ *   4 reduce_corners combine the source-chunk partials
+ *   5 mc_faces       level-set faces
+ *   6 knn_scatter    face gradients to the k nearest points
+ *   7 normal_update  new normals, per-point change
+ *   8 select         convergence statistic
+ * Entries 3-6 are 0 for DWG_UPDATE_DIRECT.  *count receives 9.
+ */
+int dwg_profile_step(dwg_handle h, float *ms_out, int cap, int *count);
+
+/*
+ * k nearest input points (1 <= k <= 32) of m query points (float32 m x 3):
+ * idx_out (int64 m x k, input-order indices, nearest first; ties in squared
+ * float32 distance go to the smaller input index; -1 when n < k).
+ */
+int dwg_knn(dwg_handle h, const float *queries, int64_t m, int k, int64_t *idx_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWG_H */

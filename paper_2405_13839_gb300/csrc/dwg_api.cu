@@ -1,0 +1,880 @@
+// dwg_api.cu -- the C ABI (include/dwg.h) and the host engine around the
+// kernels: handle state, pointer classification, buffer management, the
+// iteration body of Alg. 1 and its capture into a CUDA graph whose
+// conditional WHILE node repeats the body until the convergence rule of
+// Sec. 5.1 holds (no host synchronisation between iterations).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "dwg_internal.cuh"
+
+
+using namespace dwg;
+
+struct dwg_ctx : public Ctx {};
+
+static std::mutex g_err_mu;
+static std::string g_create_err;
+
+static int fail(Ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+static bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy bytes from a caller buffer (host or device) into device memory.
+static int upload(Ctx *c, void *dst, const void *src, size_t bytes)
+{
+    cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    DWG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+    return DWG_OK;
+}
+static int download(Ctx *c, void *dst, const void *src, size_t bytes)
+{
+    cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    DWG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+    return DWG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels used only by the engine
+// ---------------------------------------------------------------------------
+// normals: caller layout (input order, float xyz) -> sorted float4, normalised
+__global__ void k_normals_in(const float *__restrict__ v, const int64_t *__restrict__ perm,
+                             int64_t n, float4 *out, int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    float x = v[3 * j], y = v[3 * j + 1], z = v[3 * j + 2];
+    float l = sqrtf(x * x + y * y + z * z);
+    if (!(l > 0.f) || !isfinite(l)) {
+        atomicOr(err, kErrNonfinite);
+        l = 1.f;
+    }
+    out[i] = make_float4(x / l, y / l, z / l, 0.f);
+}
+// sorted float4 -> caller layout (input order)
+__global__ void k_normals_out(const float4 *__restrict__ v, const int64_t *__restrict__ perm,
+                              int64_t n, float *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    float4 a = v[i];
+    out[3 * j] = a.x;
+    out[3 * j + 1] = a.y;
+    out[3 * j + 2] = a.z;
+}
+__global__ void k_scalar_out(const float *__restrict__ v, const int64_t *__restrict__ perm,
+                             int64_t n, float *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = v[i];
+}
+__global__ void k_wg_out(const float4 *__restrict__ v, const int64_t *__restrict__ perm, int64_t n,
+                         float *w, float *g)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm ? perm[i] : i;
+    float4 a = v[i];
+    if (w) w[j] = a.w;
+    if (g) {
+        g[3 * j] = a.x;
+        g[3 * j + 1] = a.y;
+        g[3 * j + 2] = a.z;
+    }
+}
+__global__ void k_xyz_to_f4(const float *__restrict__ v, int64_t m, float4 *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = make_float4(v[3 * i], v[3 * i + 1], v[3 * i + 2], 0.f);
+}
+__global__ void k_weights_in(const float *__restrict__ a, const int64_t *__restrict__ perm,
+                             int64_t n, float4 *p4, int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = a[perm[i]];
+    if (!(v > 0.f) || !isfinite(v)) atomicOr(err, kErrNonfinite);
+    p4[i].w = v;
+}
+__global__ void k_iter_reset(IterState *st, int max_iters)
+{
+    st->iter = 0;
+    st->done = 0;
+    st->max_iters = max_iters;
+    st->nfaces = 0;
+    st->iso = 0.0;
+    st->stat = 0.0;
+}
+
+#define LAUNCH_CHECK(c)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                             \
+        if (e_ != cudaSuccess) return fail(c, DWG_ERR_CUDA, cudaGetErrorString(e_));     \
+    } while (0)
+
+static unsigned nblk(int64_t n, int b = 256) { return (unsigned)ceil_div(n, b); }
+
+// ---------------------------------------------------------------------------
+// buffers
+// ---------------------------------------------------------------------------
+static int ensure_iter_buffers(Ctx *c)
+{
+    // partial sums for the point evaluation
+    c->nchunks_p = eval_chunks(c, c->n, true);
+    size_t need_p = (size_t)c->nchunks_p * 8 * (size_t)c->n;
+    if (need_p > c->part_p_cap) {
+        cudaFree(c->d_part_p);
+        c->d_part_p = nullptr;
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_part_p, need_p * sizeof(float)));
+        c->part_p_cap = need_p;
+    }
+    if (c->mode == DWG_UPDATE_LEVELSET) {
+        int rc = build_discretization(c, c->depth);
+        if (rc) return rc;
+        c->nchunks_c = eval_chunks(c, c->ncorners, false);
+        size_t need_c = (size_t)c->nchunks_c * 2 * (size_t)c->ncorners;
+        if (need_c > c->part_c_cap) {
+            cudaFree(c->d_part_c);
+            c->d_part_c = nullptr;
+            DWG_CUDA_TRY(c, cudaMalloc(&c->d_part_c, need_c * sizeof(float)));
+            c->part_c_cap = need_c;
+        }
+    }
+    if (c->trace_cap < c->max_iters) {
+        cudaFree(c->d_tr_iso);
+        cudaFree(c->d_tr_stat);
+        cudaFree(c->d_tr_dn);
+        cudaFree(c->d_tr_faces);
+        c->d_tr_iso = c->d_tr_stat = c->d_tr_dn = nullptr;
+        c->d_tr_faces = nullptr;
+        c->trace_cap = 0;
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_tr_iso, c->max_iters * sizeof(double)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_tr_stat, c->max_iters * sizeof(double)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_tr_dn, c->max_iters * sizeof(double)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_tr_faces, c->max_iters * sizeof(long long)));
+        c->trace_cap = c->max_iters;
+    }
+    return DWG_OK;
+}
+
+static void invalidate_graph(Ctx *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    c->graph_valid = false;
+}
+
+// ---------------------------------------------------------------------------
+// the iteration body (Alg. 1, one pass of the repeat loop)
+// ---------------------------------------------------------------------------
+// ev (optional): 10 events recorded around the body's launches for profiling
+static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
+                        cudaEvent_t *ev = nullptr)
+{
+    int rc;
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecord(ev[k], c->stream);
+    };
+    // w and grad w at the input points
+    mark(0);
+    if ((rc = eval_launch(c, c->d_p4, c->n, true, c->nchunks_p, c->d_part_p, c->n))) return rc;
+    mark(1);
+    if (launch_reduce_points(c, c->d_part_p, c->nchunks_p, c->n, c->d_p4, 1, true, c->d_wg,
+                             c->d_wsum_blocks) != cudaSuccess)
+        return fail(c, DWG_ERR_CUDA, "reduce launch failed");
+    mark(2);
+    if (launch_iso(c) != cudaSuccess) return fail(c, DWG_ERR_CUDA, "iso launch failed");
+    mark(3);
+    if (c->mode == DWG_UPDATE_LEVELSET) {
+        // w at the octree leaf corners, level set, face gradients to the k nearest points
+        if ((rc = eval_launch(c, c->d_corner_pos, c->ncorners, false, c->nchunks_c, c->d_part_c,
+                              c->ncorners)))
+            return rc;
+        mark(4);
+        if (launch_reduce_w(c, c->d_part_c, c->nchunks_c, c->ncorners, c->d_wc) != cudaSuccess)
+            return fail(c, DWG_ERR_CUDA, "reduce_w launch failed");
+        mark(5);
+        if (launch_mc_faces(c) != cudaSuccess) return fail(c, DWG_ERR_CUDA, "mc launch failed");
+        mark(6);
+        if (launch_knn_scatter(c) != cudaSuccess)
+            return fail(c, DWG_ERR_CUDA, "knn launch failed");
+        mark(7);
+    } else {
+        mark(4); mark(5); mark(6); mark(7);
+    }
+    if (launch_normal_update(c) != cudaSuccess) return fail(c, DWG_ERR_CUDA, "update launch failed");
+    mark(8);
+    if (launch_select(c, cond, use_cond) != cudaSuccess)
+        return fail(c, DWG_ERR_CUDA, "select launch failed");
+    mark(9);
+    return DWG_OK;
+}
+
+static int build_graph(Ctx *c)
+{
+    invalidate_graph(c);
+    cudaGraph_t g = nullptr;
+    DWG_CUDA_TRY(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(c, DWG_ERR_CUDA, std::string("conditional handle: ") + cudaGetErrorString(e));
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(c, DWG_ERR_CUDA, std::string("conditional node: ") + cudaGetErrorString(e));
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // capture on the library's own stream (never the legacy default stream)
+    cudaStream_t saved = c->stream;
+    c->stream = c->own_stream;
+    e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        c->stream = saved;
+        cudaGraphDestroy(g);
+        return fail(c, DWG_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    }
+    int rc = enqueue_body(c, cond, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(c->stream, &captured);
+    c->stream = saved;
+    if (rc || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (rc) return rc;
+        return fail(c, DWG_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph_exec = nullptr;
+        return fail(c, DWG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    c->graph_valid = true;
+    return DWG_OK;
+}
+
+static int check_device_err(Ctx *c)
+{
+    int herr = 0;
+    DWG_CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (herr) {
+        DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        if (herr & kErrTimeout) return fail(c, DWG_ERR_TIMEOUT, "a device-side wait gave up");
+        if (herr & kErrNonfinite) return fail(c, DWG_ERR_NONFINITE, "non-finite or invalid input");
+        if (herr & kErrOverflow) return fail(c, DWG_ERR_CUDA, "face buffer overflow");
+        if (herr & kErrStack) return fail(c, DWG_ERR_CUDA, "kNN traversal stack overflow");
+        return fail(c, DWG_ERR_CUDA, "device error flag set");
+    }
+    return DWG_OK;
+}
+
+// initial normals into d_nrm and source records from them
+static int prepare_normals(Ctx *c)
+{
+    if (c->normals_pending) {
+        if (c->init_mode == DWG_INIT_RANDOM) {
+            if (launch_random_normals(c->d_nrm, c->d_perm, c->n, c->seed, c->stream) !=
+                cudaSuccess)
+                return fail(c, DWG_ERR_CUDA, "random normals launch failed");
+        } else {
+            DWG_CUDA_TRY(c, cudaMemcpyAsync(c->d_nrm, c->d_nrm_init, c->n * sizeof(float4),
+                                            cudaMemcpyDeviceToDevice, c->stream));
+        }
+        c->normals_pending = false;
+    }
+    if (launch_pack_sources(c->d_p4, c->d_nrm, c->n, c->npad, c->d_src, c->stream) != cudaSuccess)
+        return fail(c, DWG_ERR_CUDA, "pack launch failed");
+    return DWG_OK;
+}
+
+static double interactions_per_iter(const Ctx *c)
+{
+    double n = (double)c->n;
+    double it = n * n;
+    if (c->mode == DWG_UPDATE_LEVELSET) it += (double)c->ncorners * n;
+    return it;
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *dwg_last_error(dwg_handle h)
+{
+    if (h) return h->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    return g_create_err.c_str();
+}
+
+void dwg_destroy(dwg_handle h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    invalidate_graph(h);
+    void *bufs[] = {h->d_p4, h->d_perm, h->d_codes, h->d_src, h->d_nrm, h->d_nrm_init,
+                    h->d_dtheta, h->d_wg, h->d_bvh_lo, h->d_bvh_hi, h->d_leaves,
+                    h->d_leaf_corners, h->d_corner_keys, h->d_corner_pos, h->d_wc, h->d_faces,
+                    h->d_acc, h->d_part_p, h->d_part_c, h->d_wsum_blocks, h->d_dn_blocks,
+                    h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err};
+    for (void *p : bufs) cudaFree(p);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+static int create_impl(dwg_ctx *c, const float *points, int64_t n)
+{
+    DWG_CUDA_TRY(c, cudaGetDevice(&c->device));
+    DWG_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    c->stream = c->own_stream;
+    c->n = n;
+    c->npad = ceil_div(n, kSrcTile) * kSrcTile;
+    DWG_CUDA_TRY(c, cudaMalloc(&c->d_err, sizeof(int)));
+    DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    float *xyz = nullptr;
+    bool own_xyz = false;
+    if (is_device_ptr(points)) {
+        xyz = const_cast<float *>(points);
+    } else {
+        DWG_CUDA_TRY(c, cudaMalloc(&xyz, n * 3 * sizeof(float)));
+        own_xyz = true;
+        int rc = upload(c, xyz, points, n * 3 * sizeof(float));
+        if (rc) { cudaFree(xyz); return rc; }
+    }
+    auto body = [&]() -> int {
+        if (launch_check_finite(xyz, 3 * n, c->d_err, c->stream) != cudaSuccess)
+            return fail(c, DWG_ERR_CUDA, "finite-check launch failed");
+        int rc = check_device_err(c);
+        if (rc) return rc;
+        float *mm = nullptr;
+        DWG_CUDA_TRY(c, cudaMalloc(&mm, 6 * sizeof(float)));
+        launch_bbox(xyz, n, mm, c->stream);
+        float hm[6];
+        DWG_CUDA_TRY(c, cudaMemcpyAsync(hm, mm, sizeof(hm), cudaMemcpyDeviceToHost, c->stream));
+        DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaFree(mm);
+        // root cube of the octree: bounding-box centre, edge 1.125 x largest extent
+        double mn[3] = {hm[0], hm[1], hm[2]}, mx[3] = {hm[3], hm[4], hm[5]};
+        double ext = 0.0;
+        for (int k = 0; k < 3; ++k) ext = std::max(ext, mx[k] - mn[k]);
+        double L = ext > 0.0 ? ext * 1.125 : 1.0;
+        for (int k = 0; k < 3; ++k) {
+            double cen = (mn[k] + mx[k]) * 0.5;
+            c->cube_lo[k] = cen - L * 0.5;
+        }
+        c->cube_L = L;
+        // default softening: half the spacing of n points over an extent^2 patch
+        c->eps = (float)(0.5 * (ext > 0.0 ? ext : 1.0) / sqrt((double)n));
+        // Morton order
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_codes, n * sizeof(uint64_t)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_perm, n * sizeof(int64_t)));
+        double inv_h21 = (double)(1 << kMortonBits) / L;
+        if (launch_morton(xyz, n, c->cube_lo[0], c->cube_lo[1], c->cube_lo[2], inv_h21,
+                          c->d_codes, c->d_perm, c->stream) != cudaSuccess)
+            return fail(c, DWG_ERR_CUDA, "morton launch failed");
+        if ((rc = radix_sort_pairs(c, c->d_codes, c->d_perm, n, 3 * kMortonBits))) return rc;
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_p4, n * sizeof(float4)));
+        if (launch_gather_points(xyz, nullptr, c->d_perm, n, c->d_p4, c->stream) != cudaSuccess)
+            return fail(c, DWG_ERR_CUDA, "gather launch failed");
+        if ((rc = build_knn_tree(c))) return rc;
+        // per-point buffers
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_src, c->npad * kSrcFloats * sizeof(float)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_nrm, n * sizeof(float4)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_nrm_init, n * sizeof(float4)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_dtheta, n * sizeof(float)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_wg, n * sizeof(float4)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_acc, 3 * n * sizeof(unsigned long long)));
+        DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_acc, 0, 3 * n * sizeof(unsigned long long), c->stream));
+        c->wsum_blocks = wsum_block_count(n);
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_wsum_blocks, c->wsum_blocks * sizeof(double)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_dn_blocks, ceil_div(n, 256) * sizeof(double)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_state, sizeof(IterState)));
+        DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        c->stats.n_points = n;
+        return DWG_OK;
+    };
+    int rc = body();
+    if (own_xyz) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(xyz);
+    }
+    return rc;
+}
+
+int dwg_create(const float *points, int64_t n, dwg_handle *out)
+{
+    if (out) *out = nullptr;
+    auto set_err = [](const std::string &m) {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_create_err = m;
+    };
+    if (!out || !points) {
+        set_err("dwg_create: null argument");
+        return DWG_ERR_INVALID;
+    }
+    if (n < 1 || n > ((int64_t)1 << 31) - 1) {
+        set_err("dwg_create: n must be in [1, 2^31 - 1]");
+        return DWG_ERR_INVALID;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        set_err(std::string("dwg_create: no usable CUDA device: ") + cudaGetErrorString(e));
+        return DWG_ERR_CUDA;
+    }
+    dwg_ctx *c = new (std::nothrow) dwg_ctx();
+    if (!c) {
+        set_err("dwg_create: out of host memory");
+        return DWG_ERR_OOM;
+    }
+    int rc = create_impl(c, points, n);
+    if (rc) {
+        set_err("dwg_create: " + c->err);
+        dwg_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return DWG_OK;
+}
+
+int dwg_set_stream(dwg_handle h, void *stream)
+{
+    if (!h) return DWG_ERR_INVALID;
+    cudaStreamSynchronize(h->stream);
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return DWG_OK;
+}
+
+int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max_iters, float tol)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (kernel != DWG_KERNEL_PLAIN && kernel != DWG_KERNEL_SCREENED)
+        return fail(h, DWG_ERR_INVALID, "kernel must be DWG_KERNEL_PLAIN or DWG_KERNEL_SCREENED");
+    if (!(eps > 0.f) || !isfinite(eps)) return fail(h, DWG_ERR_INVALID, "eps must be > 0");
+    if (!(screening >= 0.f) || !isfinite(screening))
+        return fail(h, DWG_ERR_INVALID, "screening must be >= 0");
+    if (max_iters < 1 || max_iters > 100000)
+        return fail(h, DWG_ERR_INVALID, "max_iters must be in [1, 100000]");
+    if (!(tol > 0.f) || !isfinite(tol)) return fail(h, DWG_ERR_INVALID, "tol must be > 0");
+    h->kernel = kernel;
+    h->eps = eps;
+    h->lambda = screening;
+    h->max_iters = max_iters;
+    h->tol = tol;
+    invalidate_graph(h);
+    return DWG_OK;
+}
+
+int dwg_set_update(dwg_handle h, int depth, int knn, int mode)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (depth < 1 || depth > kMaxDepth) return fail(h, DWG_ERR_INVALID, "depth must be in [1, 14]");
+    if (knn < 1 || knn > kMaxK) return fail(h, DWG_ERR_INVALID, "knn must be in [1, 32]");
+    if (mode != DWG_UPDATE_LEVELSET && mode != DWG_UPDATE_DIRECT)
+        return fail(h, DWG_ERR_INVALID, "mode must be DWG_UPDATE_LEVELSET or DWG_UPDATE_DIRECT");
+    h->depth = depth;
+    h->knn = knn;
+    h->mode = mode;
+    invalidate_graph(h);
+    return DWG_OK;
+}
+
+int dwg_set_weights(dwg_handle h, const float *a)
+{
+    if (!h || !a) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    float *d = nullptr;
+    DWG_CUDA_TRY(h, cudaMalloc(&d, h->n * sizeof(float)));
+    int rc = upload(h, d, a, h->n * sizeof(float));
+    if (!rc) {
+        k_weights_in<<<nblk(h->n), 256, 0, h->stream>>>(d, h->d_perm, h->n, h->d_p4, h->d_err);
+        rc = check_device_err(h);
+        if (rc == DWG_ERR_NONFINITE) h->err = "weights must be finite and > 0";
+    }
+    cudaFree(d);
+    return rc;
+}
+
+static int normals_from_caller(dwg_handle h, const float *normals, float4 *dst)
+{
+    float *d = nullptr;
+    DWG_CUDA_TRY(h, cudaMalloc(&d, h->n * 3 * sizeof(float)));
+    int rc = upload(h, d, normals, h->n * 3 * sizeof(float));
+    if (!rc) {
+        k_normals_in<<<nblk(h->n), 256, 0, h->stream>>>(d, h->d_perm, h->n, dst, h->d_err);
+        rc = check_device_err(h);
+        if (rc == DWG_ERR_NONFINITE) h->err = "normals must be finite and non-zero";
+    }
+    cudaFree(d);
+    return rc;
+}
+
+int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals)
+{
+    if (!h) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    if (mode == DWG_INIT_RANDOM) {
+        h->init_mode = mode;
+        h->seed = seed;
+    } else if (mode == DWG_INIT_GIVEN) {
+        if (!normals) return fail(h, DWG_ERR_INVALID, "DWG_INIT_GIVEN needs normals");
+        int rc = normals_from_caller(h, normals, h->d_nrm_init);
+        if (rc) return rc;
+        h->init_mode = mode;
+    } else {
+        return fail(h, DWG_ERR_INVALID, "unknown init mode");
+    }
+    h->normals_pending = true;
+    return DWG_OK;
+}
+
+int dwg_set_normals(dwg_handle h, const float *normals)
+{
+    if (!h || !normals) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    int rc = normals_from_caller(h, normals, h->d_nrm);
+    if (rc) return rc;
+    h->normals_pending = false;
+    return DWG_OK;
+}
+
+int dwg_get_normals(dwg_handle h, float *normals_out)
+{
+    if (!h || !normals_out) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    if (h->normals_pending) {
+        int rc = prepare_normals(h);
+        if (rc) return rc;
+    }
+    float *d = nullptr;
+    DWG_CUDA_TRY(h, cudaMalloc(&d, h->n * 3 * sizeof(float)));
+    k_normals_out<<<nblk(h->n), 256, 0, h->stream>>>(h->d_nrm, h->d_perm, h->n, d);
+    int rc = download(h, normals_out, d, h->n * 3 * sizeof(float));
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (!rc && e != cudaSuccess) rc = fail(h, DWG_ERR_CUDA, cudaGetErrorString(e));
+    return rc;
+}
+
+static int read_state(dwg_handle h, IterState *st)
+{
+    DWG_CUDA_TRY(h, cudaMemcpyAsync(st, h->d_state, sizeof(IterState), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return DWG_OK;
+}
+
+int dwg_orient(dwg_handle h, float *normals_out, int *iters_out)
+{
+    if (!h) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    int rc = ensure_iter_buffers(h);
+    if (rc) return rc;
+    h->normals_pending = true;  // orient always starts from the initial normals
+    if ((rc = prepare_normals(h))) return rc;
+    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters);
+    LAUNCH_CHECK(h);
+    if (!h->graph_valid && (rc = build_graph(h))) return rc;
+    cudaEvent_t e0, e1;
+    DWG_CUDA_TRY(h, cudaEventCreate(&e0));
+    DWG_CUDA_TRY(h, cudaEventCreate(&e1));
+    cudaEventRecord(e0, h->stream);
+    cudaError_t e = cudaGraphLaunch(h->graph_exec, h->stream);
+    cudaEventRecord(e1, h->stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(h, DWG_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    }
+    IterState st;
+    rc = read_state(h, &st);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = check_device_err(h))) return rc;
+    int it = std::min(st.iter, h->max_iters);
+    h->tr_iso.assign(it, 0.0);
+    h->tr_stat.assign(it, 0.0);
+    h->tr_dn.assign(it, 0.0);
+    h->tr_faces.assign(it, 0);
+    if (it > 0) {
+        std::vector<long long> tf(it);
+        DWG_CUDA_TRY(h, cudaMemcpyAsync(h->tr_iso.data(), h->d_tr_iso, it * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        DWG_CUDA_TRY(h, cudaMemcpyAsync(h->tr_stat.data(), h->d_tr_stat, it * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        DWG_CUDA_TRY(h, cudaMemcpyAsync(h->tr_dn.data(), h->d_tr_dn, it * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        DWG_CUDA_TRY(h, cudaMemcpyAsync(tf.data(), h->d_tr_faces, it * sizeof(long long),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        for (int i = 0; i < it; ++i) h->tr_faces[i] = tf[i];
+    }
+    h->stats.iters = it;
+    h->stats.converged = st.done;
+    h->stats.iso_last = st.iso;
+    h->stats.stat_last = st.stat;
+    h->stats.faces_last = it > 0 ? h->tr_faces[it - 1] : 0;
+    h->stats.n_leaves = h->nleaves;
+    h->stats.n_corners = h->ncorners;
+    h->stats.interactions = interactions_per_iter(h) * it;
+    h->stats.ms_orient = ms;
+    if (iters_out) *iters_out = it;
+    if (normals_out && (rc = dwg_get_normals(h, normals_out))) return rc;
+    return st.done ? DWG_OK : DWG_NOT_CONVERGED;
+}
+
+int dwg_step(dwg_handle h, float *w_out, float *grad_out, float *dtheta_out, double *iso_out,
+             double *stat_out)
+{
+    if (!h) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    int rc = ensure_iter_buffers(h);
+    if (rc) return rc;
+    if ((rc = prepare_normals(h))) return rc;
+    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters);
+    LAUNCH_CHECK(h);
+    cudaGraphConditionalHandle none = 0;
+    if ((rc = enqueue_body(h, none, 0))) return rc;
+    IterState st;
+    if ((rc = read_state(h, &st))) return rc;
+    if ((rc = check_device_err(h))) return rc;
+    if (iso_out) *iso_out = st.iso;
+    if (stat_out) *stat_out = st.stat;
+    float *d = nullptr;
+    DWG_CUDA_TRY(h, cudaMalloc(&d, h->n * 4 * sizeof(float)));
+    if (w_out || grad_out) {
+        k_wg_out<<<nblk(h->n), 256, 0, h->stream>>>(h->d_wg, h->d_perm, h->n, d, d + h->n);
+        if (w_out && (rc = download(h, w_out, d, h->n * sizeof(float)))) goto out;
+        if (grad_out && (rc = download(h, grad_out, d + h->n, 3 * h->n * sizeof(float)))) goto out;
+    }
+    if (dtheta_out) {
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        k_scalar_out<<<nblk(h->n), 256, 0, h->stream>>>(h->d_dtheta, h->d_perm, h->n, d);
+        if ((rc = download(h, dtheta_out, d, h->n * sizeof(float)))) goto out;
+    }
+out:
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    return rc;
+}
+
+int dwg_profile_step(dwg_handle h, float *ms_out, int cap, int *count)
+{
+    if (!h) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    int rc = ensure_iter_buffers(h);
+    if (rc) return rc;
+    if ((rc = prepare_normals(h))) return rc;
+    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters);
+    LAUNCH_CHECK(h);
+    cudaEvent_t ev[10];
+    for (int k = 0; k < 10; ++k) DWG_CUDA_TRY(h, cudaEventCreate(&ev[k]));
+    cudaGraphConditionalHandle none = 0;
+    rc = enqueue_body(h, none, 0, ev);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    float ms[9] = {0};
+    for (int k = 0; k < 9; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    for (int k = 0; k < 10; ++k) cudaEventDestroy(ev[k]);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(h, DWG_ERR_CUDA, cudaGetErrorString(e));
+    if ((rc = check_device_err(h))) return rc;
+    if (count) *count = 9;
+    for (int k = 0; k < 9 && k < cap; ++k) ms_out[k] = ms[k];
+    return DWG_OK;
+}
+
+int dwg_eval_gwn(dwg_handle h, const float *queries, int64_t m, float *w_out, float *grad_out)
+{
+    if (!h || !queries || !w_out) return DWG_ERR_INVALID;
+    if (m < 1) return fail(h, DWG_ERR_INVALID, "m must be >= 1");
+    cudaSetDevice(h->device);
+    int rc;
+    if ((rc = prepare_normals(h))) return rc;
+    bool grad = grad_out != nullptr;
+    float *qx = nullptr, *part = nullptr, *o = nullptr;
+    float4 *q4 = nullptr, *wg = nullptr;
+    auto body = [&]() -> int {
+        DWG_CUDA_TRY(h, cudaMalloc(&qx, m * 3 * sizeof(float)));
+        if ((rc = upload(h, qx, queries, m * 3 * sizeof(float)))) return rc;
+        if (launch_check_finite(qx, 3 * m, h->d_err, h->stream) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "finite-check launch failed");
+        if ((rc = check_device_err(h))) return rc;
+        DWG_CUDA_TRY(h, cudaMalloc(&q4, m * sizeof(float4)));
+        k_xyz_to_f4<<<nblk(m), 256, 0, h->stream>>>(qx, m, q4);
+        int nch = eval_chunks(h, m, grad);
+        DWG_CUDA_TRY(h, cudaMalloc(&part, (size_t)nch * (grad ? 8 : 2) * m * sizeof(float)));
+        if ((rc = eval_launch(h, q4, m, grad, nch, part, m))) return rc;
+        DWG_CUDA_TRY(h, cudaMalloc(&wg, m * sizeof(float4)));
+        if (launch_reduce_points(h, part, nch, m, q4, grad ? 2 : 0, grad, wg, nullptr) !=
+            cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "reduce launch failed");
+        DWG_CUDA_TRY(h, cudaMalloc(&o, m * 4 * sizeof(float)));
+        k_wg_out<<<nblk(m), 256, 0, h->stream>>>(wg, nullptr, m, o, grad ? o + m : nullptr);
+        if ((rc = download(h, w_out, o, m * sizeof(float)))) return rc;
+        if (grad && (rc = download(h, grad_out, o + m, 3 * m * sizeof(float)))) return rc;
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return check_device_err(h);
+    };
+    rc = body();
+    cudaStreamSynchronize(h->stream);
+    cudaFree(qx);
+    cudaFree(q4);
+    cudaFree(part);
+    cudaFree(wg);
+    cudaFree(o);
+    return rc;
+}
+
+int dwg_get_stats(dwg_handle h, dwg_stats *out)
+{
+    if (!h || !out) return DWG_ERR_INVALID;
+    *out = h->stats;
+    out->n_points = h->n;
+    return DWG_OK;
+}
+
+int dwg_get_trace(dwg_handle h, double *iso, double *stat, double *mean_dn, int64_t *faces,
+                  int cap, int *count)
+{
+    if (!h) return DWG_ERR_INVALID;
+    int it = (int)h->tr_iso.size();
+    if (count) *count = it;
+    for (int i = 0; i < it && i < cap; ++i) {
+        if (iso) iso[i] = h->tr_iso[i];
+        if (stat) stat[i] = h->tr_stat[i];
+        if (mean_dn) mean_dn[i] = h->tr_dn[i];
+        if (faces) faces[i] = h->tr_faces[i];
+    }
+    return DWG_OK;
+}
+
+int dwg_get_leaves(dwg_handle h, int64_t *leaves_out, int64_t cap, int64_t *count)
+{
+    if (!h || !count) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    int rc = build_discretization(h, h->depth);
+    if (rc) return rc;
+    *count = h->nleaves;
+    if (!leaves_out || cap < h->nleaves) return DWG_OK;
+    std::vector<int4> L(h->nleaves);
+    DWG_CUDA_TRY(h, cudaMemcpyAsync(L.data(), h->d_leaves, h->nleaves * sizeof(int4),
+                                    cudaMemcpyDeviceToHost, h->stream));
+    DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    std::vector<int64_t> rec(5 * h->nleaves);
+    for (int64_t i = 0; i < h->nleaves; ++i) {
+        uint64_t code = (uint64_t)(uint32_t)L[i].y | ((uint64_t)(uint32_t)L[i].z << 32);
+        rec[5 * i] = L[i].x;
+        rec[5 * i + 1] = (int64_t)compact3(code);
+        rec[5 * i + 2] = (int64_t)compact3(code >> 1);
+        rec[5 * i + 3] = (int64_t)compact3(code >> 2);
+        rec[5 * i + 4] = L[i].w;
+    }
+    std::vector<int64_t> order(h->nleaves);
+    for (int64_t i = 0; i < h->nleaves; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        for (int k = 0; k < 4; ++k)
+            if (rec[5 * a + k] != rec[5 * b + k]) return rec[5 * a + k] < rec[5 * b + k];
+        return false;
+    });
+    std::vector<int64_t> sorted(5 * h->nleaves);
+    for (int64_t i = 0; i < h->nleaves; ++i)
+        for (int k = 0; k < 5; ++k) sorted[5 * i + k] = rec[5 * order[i] + k];
+    return download(h, leaves_out, sorted.data(), sorted.size() * sizeof(int64_t)) ||
+                   cudaStreamSynchronize(h->stream)
+               ? DWG_ERR_CUDA
+               : DWG_OK;
+}
+
+int dwg_get_corners(dwg_handle h, int64_t *keys_out, int64_t cap, int64_t *count)
+{
+    if (!h || !count) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    int rc = build_discretization(h, h->depth);
+    if (rc) return rc;
+    *count = h->ncorners;
+    if (!keys_out || cap < h->ncorners) return DWG_OK;
+    std::vector<uint64_t> K(h->ncorners);
+    DWG_CUDA_TRY(h, cudaMemcpyAsync(K.data(), h->d_corner_keys, h->ncorners * sizeof(uint64_t),
+                                    cudaMemcpyDeviceToHost, h->stream));
+    DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const int64_t S1 = ((int64_t)1 << h->depth) + 1;
+    std::vector<int64_t> out(h->ncorners);
+    for (int64_t i = 0; i < h->ncorners; ++i) {
+        int64_t X = (int64_t)compact3(K[i]), Y = (int64_t)compact3(K[i] >> 1),
+                Z = (int64_t)compact3(K[i] >> 2);
+        out[i] = (X * S1 + Y) * S1 + Z;
+    }
+    std::sort(out.begin(), out.end());
+    return download(h, keys_out, out.data(), out.size() * sizeof(int64_t)) ||
+                   cudaStreamSynchronize(h->stream)
+               ? DWG_ERR_CUDA
+               : DWG_OK;
+}
+
+int dwg_knn(dwg_handle h, const float *queries, int64_t m, int k, int64_t *idx_out)
+{
+    if (!h || !queries || !idx_out) return DWG_ERR_INVALID;
+    if (m < 1 || k < 1 || k > kMaxK) return fail(h, DWG_ERR_INVALID, "need m >= 1, 1 <= k <= 32");
+    cudaSetDevice(h->device);
+    float *qx = nullptr;
+    float4 *q4 = nullptr;
+    int64_t *idx = nullptr;
+    int rc;
+    auto body = [&]() -> int {
+        DWG_CUDA_TRY(h, cudaMalloc(&qx, m * 3 * sizeof(float)));
+        if ((rc = upload(h, qx, queries, m * 3 * sizeof(float)))) return rc;
+        DWG_CUDA_TRY(h, cudaMalloc(&q4, m * sizeof(float4)));
+        k_xyz_to_f4<<<nblk(m), 256, 0, h->stream>>>(qx, m, q4);
+        DWG_CUDA_TRY(h, cudaMalloc(&idx, m * k * sizeof(int64_t)));
+        if (launch_knn_query(h, q4, m, k, idx) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "knn launch failed");
+        if ((rc = download(h, idx_out, idx, m * k * sizeof(int64_t)))) return rc;
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return check_device_err(h);
+    };
+    rc = body();
+    cudaStreamSynchronize(h->stream);
+    cudaFree(qx);
+    cudaFree(q4);
+    cudaFree(idx);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,617 @@
+// dwg_eval.cu -- exact all-pairs evaluation of the generalized winding
+// number and its gradient (paper Sec. 3, Eq. 2/3; screened variant Sec. 4.2,
+// Eq. 5) on sm_103a.
+//
+// Work decomposition: a CTA of 128 threads owns a tile of 128 * 2P queries
+// (each thread holds P query pairs in registers) and one contiguous chunk of
+// the sources.  Source records (48 bytes: x, y, z, mx, my, mz, each stored
+// twice so that one 64-bit register pair feeds both lanes of a packed
+// f32x2 instruction) stream through a 4-stage shared-memory ring filled by
+// the bulk-copy (TMA) engine with mbarrier completion.  Every thread reads
+// each record by broadcast and updates its 2P queries with packed
+// fma/mul/add.f32x2 instructions; rsqrt (and ex2 for the screened kernel)
+// run on the MUFU unit.
+//
+// Precision: terms are FP32.  Each thread sums one 128-source tile in plain
+// FP32 and folds the tile sum into a (hi, lo) two-sum pair, so the long sum
+// over all sources is compensated.  The CTA writes its (hi, lo) partials for
+// its source chunk; a reduce kernel combines the chunks in a fixed order
+// (deterministic) and adds back the exactly-known coincident-point terms.
+//
+// Per term, with d = p - q, rho^2 = |d|^2 + eps^2, m = a n / (4 pi),
+// inv = rho^-1:
+//   plain    w += <m,d> inv^3;   grad += 3 <m,d> inv^5 d - m inv^3
+//   screened F = exp(-s rho)(1 + s rho):
+//            w += F <m,d> inv^3;
+//            grad += <m,d> inv^3 (3 F inv^2 + s^2 exp(-s rho)) d - F inv^3 m
+// A source equal to the query (d = 0) contributes exactly zero to w and to
+// the d-terms; its only contribution, -F inv^3 m to the gradient, is
+// subtracted after the sum (reduce kernel), which skips it exactly as the
+// definition requires without a per-term test.
+#include "dwg_internal.cuh"
+
+namespace dwg {
+
+// ---------------------------------------------------------------------------
+// packed FP32x2 arithmetic (PTX ISA 8.6, sm_100 family and later)
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float rsqrt_mufu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_mufu(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ f2 rsqrt2(f2 v)
+{
+    float a, b;
+    upk(v, a, b);
+    return pk(rsqrt_mufu(a), rsqrt_mufu(b));
+}
+__device__ __forceinline__ f2 ex22(f2 v)
+{
+    float a, b;
+    upk(v, a, b);
+    return pk(ex2_mufu(a), ex2_mufu(b));
+}
+// (hi, lo) += t with Knuth's two-sum, both lanes at once
+__device__ __forceinline__ void two_sum_acc(f2 &hi, f2 &lo, f2 t)
+{
+    f2 s = add2(hi, t);
+    f2 bb = sub2(s, hi);
+    f2 e = add2(sub2(hi, sub2(s, bb)), sub2(t, bb));
+    lo = add2(lo, e);
+    hi = s;
+}
+__device__ __forceinline__ void two_sum1(float &hi, float &lo, float t)
+{
+    float s = __fadd_rn(hi, t);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+    lo = __fadd_rn(lo, e);
+    hi = s;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (inline PTX), with bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Returns false when the wait gave up (about 2^24 polls, well beyond any
+// copy latency); the caller then reports DWG_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 24); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// the evaluation kernel
+// ---------------------------------------------------------------------------
+constexpr int kEvalThreads = 128;
+constexpr int kStages = 4;
+
+template <int P, bool GRAD, bool SCREENED>
+__global__ void __launch_bounds__(kEvalThreads)
+    k_gwn(const float *__restrict__ src, int64_t ntiles_total, const float4 *__restrict__ q,
+          int64_t m, int tiles_per_chunk, float *__restrict__ part, int64_t stride,
+          EvalParams ep, int *__restrict__ err)
+{
+    constexpr int T = kSrcTile;
+    constexpr int TILE_FLOATS = T * kSrcFloats;
+    constexpr uint32_t TILE_BYTES = TILE_FLOATS * 4;
+    constexpr int QB = kEvalThreads * 2 * P;
+    constexpr int NA = GRAD ? 4 : 1;
+
+    __shared__ __align__(128) float sbuf[kStages][TILE_FLOATS];
+    __shared__ __align__(8) uint64_t bar[kStages];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int64_t qbase = (int64_t)blockIdx.x * QB + tid;
+    const int chunk = blockIdx.y;
+    const int64_t tile0 = (int64_t)chunk * tiles_per_chunk;
+    int ntiles = (int)min((int64_t)tiles_per_chunk, ntiles_total - tile0);
+    if (ntiles < 0) ntiles = 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < kStages && s < ntiles; ++s) {
+            mbar_expect_tx(&bar[s], TILE_BYTES);
+            bulk_g2s(sbuf[s], src + (tile0 + s) * TILE_FLOATS, TILE_BYTES, &bar[s]);
+        }
+    }
+
+    // query pairs in registers (tail queries repeat the last valid query)
+    f2 qx[P], qy[P], qz[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        int64_t i0 = min(qbase + (int64_t)(2 * p) * kEvalThreads, m - 1);
+        int64_t i1 = min(qbase + (int64_t)(2 * p + 1) * kEvalThreads, m - 1);
+        float4 a = q[i0], b = q[i1];
+        qx[p] = pk(a.x, b.x);
+        qy[p] = pk(a.y, b.y);
+        qz[p] = pk(a.z, b.z);
+    }
+    const f2 eps2 = pk(ep.eps2, ep.eps2);
+    const f2 three = pk(3.f, 3.f);
+    const f2 zero = pk(0.f, 0.f);
+    const f2 sv = pk(ep.s, ep.s);
+    const f2 s2v = pk(ep.s2, ep.s2);
+    const f2 nl2e = pk(ep.nl2e_s, ep.nl2e_s);
+
+    f2 hw[P], lw[P];
+    f2 hgx[P], lgx[P], hgy[P], lgy[P], hgz[P], lgz[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        hw[p] = lw[p] = zero;
+        hgx[p] = lgx[p] = hgy[p] = lgy[p] = hgz[p] = lgz[p] = zero;
+    }
+
+    int t = 0;
+    for (; t < ntiles; ++t) {
+        const int s = t % kStages;
+        const uint32_t parity = (uint32_t)((t / kStages) & 1);
+        if (!mbar_wait_bounded(&bar[s], parity)) {
+            atomicOr(err, kErrTimeout);
+            s_abort = 1;
+        }
+        f2 tw[P], t1x[P], t1y[P], t1z[P], t2x[P], t2y[P], t2z[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            tw[p] = zero;
+            t1x[p] = t1y[p] = t1z[p] = t2x[p] = t2y[p] = t2z[p] = zero;
+        }
+        if (!s_abort) {
+            const ulonglong2 *rec = reinterpret_cast<const ulonglong2 *>(sbuf[s]);
+#pragma unroll 2
+            for (int j = 0; j < T; ++j) {
+                const ulonglong2 r0 = rec[3 * j + 0];  // (x,x) (y,y)
+                const ulonglong2 r1 = rec[3 * j + 1];  // (z,z) (mx,mx)
+                const ulonglong2 r2v = rec[3 * j + 2]; // (my,my) (mz,mz)
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    f2 dx = sub2(r0.x, qx[p]);
+                    f2 dy = sub2(r0.y, qy[p]);
+                    f2 dz = sub2(r1.x, qz[p]);
+                    f2 rr = fma2(dx, dx, eps2);
+                    rr = fma2(dy, dy, rr);
+                    rr = fma2(dz, dz, rr);
+                    f2 inv = rsqrt2(rr);
+                    f2 md = mul2(r1.y, dx);
+                    md = fma2(r2v.x, dy, md);
+                    md = fma2(r2v.y, dz, md);
+                    f2 i2 = mul2(inv, inv);
+                    f2 i3 = mul2(i2, inv);
+                    if (!SCREENED) {
+                        if (GRAD) {
+                            f2 phi = mul2(md, i3);
+                            tw[p] = add2(tw[p], phi);
+                            f2 c = mul2(phi, i2);
+                            t1x[p] = fma2(c, dx, t1x[p]);
+                            t1y[p] = fma2(c, dy, t1y[p]);
+                            t1z[p] = fma2(c, dz, t1z[p]);
+                            t2x[p] = fma2(r1.y, i3, t2x[p]);
+                            t2y[p] = fma2(r2v.x, i3, t2y[p]);
+                            t2z[p] = fma2(r2v.y, i3, t2z[p]);
+                        } else {
+                            tw[p] = fma2(md, i3, tw[p]);
+                        }
+                    } else {
+                        f2 rho = mul2(rr, inv);
+                        f2 e = ex22(mul2(rho, nl2e));
+                        f2 F = fma2(e, mul2(rho, sv), e);
+                        f2 phi = mul2(md, i3);
+                        tw[p] = fma2(F, phi, tw[p]);
+                        if (GRAD) {
+                            f2 fi3 = mul2(F, i3);
+                            f2 cc = fma2(three, mul2(F, i2), mul2(s2v, e));
+                            f2 c = mul2(phi, cc);
+                            t1x[p] = fma2(c, dx, t1x[p]);
+                            t1y[p] = fma2(c, dy, t1y[p]);
+                            t1z[p] = fma2(c, dz, t1z[p]);
+                            t2x[p] = fma2(r1.y, fi3, t2x[p]);
+                            t2y[p] = fma2(r2v.x, fi3, t2y[p]);
+                            t2z[p] = fma2(r2v.y, fi3, t2z[p]);
+                        }
+                    }
+                }
+            }
+        }
+        // fold the tile sums into the compensated totals
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            two_sum_acc(hw[p], lw[p], tw[p]);
+            if (GRAD) {
+                f2 gx, gy, gz;
+                if (!SCREENED) {
+                    gx = sub2(mul2(three, t1x[p]), t2x[p]);
+                    gy = sub2(mul2(three, t1y[p]), t2y[p]);
+                    gz = sub2(mul2(three, t1z[p]), t2z[p]);
+                } else {
+                    gx = sub2(t1x[p], t2x[p]);
+                    gy = sub2(t1y[p], t2y[p]);
+                    gz = sub2(t1z[p], t2z[p]);
+                }
+                two_sum_acc(hgx[p], lgx[p], gx);
+                two_sum_acc(hgy[p], lgy[p], gy);
+                two_sum_acc(hgz[p], lgz[p], gz);
+            }
+        }
+        __syncthreads();  // every thread is done with buffer s
+        if (s_abort) break;
+        if (tid == 0 && t + kStages < ntiles) {
+            mbar_expect_tx(&bar[s], TILE_BYTES);
+            bulk_g2s(sbuf[s], src + (tile0 + t + kStages) * TILE_FLOATS, TILE_BYTES, &bar[s]);
+        }
+    }
+    if (s_abort) {
+        // drain the copies still in flight before the CTA's shared memory goes away
+        if (tid == 0)
+            for (int u = t + 1; u < ntiles && u < t + kStages; ++u)
+                mbar_wait_bounded(&bar[u % kStages], (uint32_t)((u / kStages) & 1));
+        __syncthreads();
+    }
+
+    // write the (hi, lo) partials: part[((chunk * NA + a) * 2 + h) * stride + i]
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+        for (int lane = 0; lane < 2; ++lane) {
+            int64_t i = qbase + (int64_t)(2 * p + lane) * kEvalThreads;
+            if (i >= m) continue;
+            float vals[NA][2];
+            float a, b;
+            upk(hw[p], a, b);
+            vals[0][0] = lane ? b : a;
+            upk(lw[p], a, b);
+            vals[0][1] = lane ? b : a;
+            if (GRAD) {
+                upk(hgx[p], a, b); vals[1 % NA][0] = lane ? b : a;
+                upk(lgx[p], a, b); vals[1 % NA][1] = lane ? b : a;
+                upk(hgy[p], a, b); vals[2 % NA][0] = lane ? b : a;
+                upk(lgy[p], a, b); vals[2 % NA][1] = lane ? b : a;
+                upk(hgz[p], a, b); vals[3 % NA][0] = lane ? b : a;
+                upk(lgz[p], a, b); vals[3 % NA][1] = lane ? b : a;
+            }
+#pragma unroll
+            for (int aa = 0; aa < NA; ++aa)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    part[((int64_t)(chunk * NA + aa) * 2 + h) * stride + i] = vals[aa][h];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// source records: (x,x,y,y,z,z,mx,mx,my,my,mz,mz), m = a n / (4 pi);
+// padding records are at the origin with m = 0 and contribute exactly 0.
+// ---------------------------------------------------------------------------
+__global__ void k_pack_sources(const float4 *__restrict__ p4, const float4 *__restrict__ nrm,
+                               int64_t n, int64_t npad, float *__restrict__ src)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    float x = 0.f, y = 0.f, z = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+    if (i < n) {
+        float4 p = p4[i];
+        float4 v = nrm[i];
+        float c = p.w * (float)(1.0 / (4.0 * kPi));
+        x = p.x; y = p.y; z = p.z;
+        mx = c * v.x; my = c * v.y; mz = c * v.z;
+    }
+    float4 *r = reinterpret_cast<float4 *>(src + i * kSrcFloats);
+    r[0] = make_float4(x, x, y, y);
+    r[1] = make_float4(z, z, mx, mx);
+    r[2] = make_float4(my, my, mz, mz);
+}
+
+cudaError_t launch_pack_sources(const float4 *p4, const float4 *nrm, int64_t n, int64_t npad,
+                                float *src, cudaStream_t s)
+{
+    int blk = 256;
+    k_pack_sources<<<(unsigned)ceil_div(npad, blk), blk, 0, s>>>(p4, nrm, n, npad, src);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static EvalParams make_params(const Ctx *c)
+{
+    EvalParams ep;
+    ep.eps2 = c->eps * c->eps;
+    bool scr = c->kernel == DWG_KERNEL_SCREENED && c->lambda > 0.f;
+    ep.screened = scr ? 1 : 0;
+    double s = scr ? sqrt((double)c->lambda) : 0.0;
+    ep.s = (float)s;
+    ep.s2 = (float)(s * s);
+    ep.nl2e_s = (float)(-s * 1.4426950408889634);
+    return ep;
+}
+
+static int num_sms(int dev)
+{
+    static int cached[64] = {0};
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 148;
+    }
+    return cached[dev];
+}
+
+// Split the sources into chunks so that the grid covers every SM several
+// times over; each chunk keeps at least 8 tiles.
+static int pick_chunks(int64_t qtiles, int64_t ntiles_src, int sms)
+{
+    int64_t target = (int64_t)sms * 8;
+    int64_t ch = ceil_div(target, qtiles > 0 ? qtiles : 1);
+    int64_t maxch = ntiles_src / 8;
+    if (maxch < 1) maxch = 1;
+    if (ch > maxch) ch = maxch;
+    if (ch < 1) ch = 1;
+    return (int)ch;
+}
+
+template <int P, bool GRAD>
+static cudaError_t launch_gwn_t(const Ctx *c, const float4 *q, int64_t m, int nchunks,
+                                float *part, int64_t stride)
+{
+    EvalParams ep = make_params(c);
+    constexpr int QB = kEvalThreads * 2 * P;
+    int64_t qtiles = ceil_div(m, QB);
+    int64_t ntiles = c->npad / kSrcTile;
+    int tpc = (int)ceil_div(ntiles, nchunks);
+    dim3 grid((unsigned)qtiles, (unsigned)nchunks);
+    if (ep.screened)
+        k_gwn<P, GRAD, true><<<grid, kEvalThreads, 0, c->stream>>>(c->d_src, ntiles, q, m, tpc,
+                                                                   part, stride, ep, c->d_err);
+    else
+        k_gwn<P, GRAD, false><<<grid, kEvalThreads, 0, c->stream>>>(c->d_src, ntiles, q, m, tpc,
+                                                                    part, stride, ep, c->d_err);
+    return cudaGetLastError();
+}
+
+constexpr int kPGrad = 2;   // query pairs per thread, gradient kernel
+constexpr int kPW = 4;      // query pairs per thread, w-only kernel
+
+int eval_chunks(const Ctx *c, int64_t m, bool grad)
+{
+    int QB = kEvalThreads * 2 * (grad ? kPGrad : kPW);
+    return pick_chunks(ceil_div(m, QB), c->npad / kSrcTile, num_sms(c->device));
+}
+
+int eval_launch(Ctx *c, const float4 *q, int64_t m, bool grad, int nchunks, float *part,
+                int64_t stride)
+{
+    cudaError_t e = grad ? launch_gwn_t<kPGrad, true>(c, q, m, nchunks, part, stride)
+                         : launch_gwn_t<kPW, false>(c, q, m, nchunks, part, stride);
+    if (e != cudaSuccess) {
+        c->err = std::string("gwn kernel launch: ") + cudaGetErrorString(e);
+        return DWG_ERR_CUDA;
+    }
+    return DWG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reduce: combine chunk partials in chunk order; for gradients add back the
+// coincident-source terms; optionally per-block FP64 sums of w.
+// ---------------------------------------------------------------------------
+struct CubeQ {
+    double lo[3];
+    double inv_h21;
+};
+
+template <bool GRAD>
+__global__ void k_reduce_points(const float *__restrict__ part, int nchunks, int64_t m,
+                                int64_t stride, const float4 *__restrict__ q,
+                                const float *__restrict__ src, const uint64_t *__restrict__ codes,
+                                int64_t nsrc, int self_mode, CubeQ cq, EvalParams ep,
+                                float4 *__restrict__ out, double *__restrict__ wsum_blocks)
+{
+    constexpr int NA = GRAD ? 4 : 1;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double wloc = 0.0;
+    if (i < m) {
+        float h[NA], l[NA];
+        for (int a = 0; a < NA; ++a) { h[a] = 0.f; l[a] = 0.f; }
+        for (int ch = 0; ch < nchunks; ++ch)
+            for (int a = 0; a < NA; ++a) {
+                float ph = part[((int64_t)(ch * NA + a) * 2 + 0) * stride + i];
+                float pl = part[((int64_t)(ch * NA + a) * 2 + 1) * stride + i];
+                two_sum1(h[a], l[a], ph);
+                l[a] = __fadd_rn(l[a], pl);
+            }
+        if (GRAD && self_mode != 0) {
+            // The coincident sources' gradient term is -(F inv^3) m with
+            // rho = eps; add it back so that those sources are skipped.
+            float4 qi = q[i];
+            float inv = rsqrt_mufu(ep.eps2);
+            float i2 = inv * inv;
+            float i3 = i2 * inv;
+            float fi3 = i3;
+            if (ep.screened) {
+                float rho = ep.eps2 * inv;
+                float e = ex2_mufu(rho * ep.nl2e_s);
+                float F = fmaf(e, rho * ep.s, e);
+                fi3 = F * i3;
+            }
+            int64_t lo_j, hi_j;
+            if (self_mode == 1) {  // queries are the sources, same order
+                lo_j = i;
+                hi_j = i + 1;
+                uint64_t ci = codes[i];
+                while (lo_j > 0 && codes[lo_j - 1] == ci) --lo_j;
+                while (hi_j < nsrc && codes[hi_j] == ci) ++hi_j;
+            } else {  // arbitrary query: locate its code among the sorted codes
+                uint64_t ci = spread3((uint64_t)quant21(qi.x, cq.lo[0], cq.inv_h21)) |
+                              (spread3((uint64_t)quant21(qi.y, cq.lo[1], cq.inv_h21)) << 1) |
+                              (spread3((uint64_t)quant21(qi.z, cq.lo[2], cq.inv_h21)) << 2);
+                int64_t a = 0, b = nsrc;
+                while (a < b) {
+                    int64_t mid = (a + b) >> 1;
+                    if (codes[mid] < ci) a = mid + 1; else b = mid;
+                }
+                lo_j = a;
+                hi_j = a;
+                while (hi_j < nsrc && codes[hi_j] == ci) ++hi_j;
+            }
+            for (int64_t j = lo_j; j < hi_j; ++j) {
+                const float *r = src + j * kSrcFloats;
+                if (r[0] == qi.x && r[2] == qi.y && r[4] == qi.z) {
+                    two_sum1(h[1], l[1], r[6] * fi3);
+                    two_sum1(h[2], l[2], r[8] * fi3);
+                    two_sum1(h[3], l[3], r[10] * fi3);
+                }
+            }
+        }
+        float w = __fadd_rn(h[0], l[0]);
+        float4 o = make_float4(0.f, 0.f, 0.f, w);
+        if (GRAD) {
+            o.x = __fadd_rn(h[1], l[1]);
+            o.y = __fadd_rn(h[2], l[2]);
+            o.z = __fadd_rn(h[3], l[3]);
+        }
+        out[i] = o;
+        wloc = (double)h[0] + (double)l[0];
+    }
+    if (wsum_blocks) {
+        // deterministic block sum of w in FP64 (fixed tree)
+        __shared__ double sh[256];
+        sh[threadIdx.x] = wloc;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) wsum_blocks[blockIdx.x] = sh[0];
+    }
+}
+
+int wsum_block_count(int64_t n) { return (int)ceil_div(n, 256); }
+
+__global__ void k_reduce_w(const float *__restrict__ part, int nchunks, int64_t m, int64_t stride,
+                           float *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    float h = 0.f, l = 0.f;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        two_sum1(h, l, part[((int64_t)ch * 2 + 0) * stride + i]);
+        l = __fadd_rn(l, part[((int64_t)ch * 2 + 1) * stride + i]);
+    }
+    out[i] = __fadd_rn(h, l);
+}
+
+cudaError_t launch_reduce_w(Ctx *c, const float *part, int nchunks, int64_t m, float *out)
+{
+    k_reduce_w<<<(unsigned)ceil_div(m, 256), 256, 0, c->stream>>>(part, nchunks, m, m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t m,
+                                 const float4 *queries, int self_mode, bool grad,
+                                 float4 *out, double *wsum_blocks)
+{
+    CubeQ cq;
+    for (int k = 0; k < 3; ++k) cq.lo[k] = c->cube_lo[k];
+    cq.inv_h21 = (double)(1 << kMortonBits) / c->cube_L;
+    EvalParams ep = make_params(c);
+    unsigned blocks = (unsigned)ceil_div(m, 256);
+    if (grad)
+        k_reduce_points<true><<<blocks, 256, 0, c->stream>>>(part, nchunks, m, m, queries,
+                                                             c->d_src, c->d_codes, c->n, self_mode,
+                                                             cq, ep, out, wsum_blocks);
+    else
+        k_reduce_points<false><<<blocks, 256, 0, c->stream>>>(part, nchunks, m, m, queries,
+                                                              c->d_src, c->d_codes, c->n, 0, cq,
+                                                              ep, out, wsum_blocks);
+    return cudaGetLastError();
+}
+
+}  // namespace dwg

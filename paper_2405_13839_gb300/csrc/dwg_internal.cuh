@@ -1,0 +1,219 @@
+// dwg_internal.cuh -- declarations shared by the CUDA translation units of
+// libdwg.so: the engine context, device helpers and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dwg.h"
+
+namespace dwg {
+
+// ---------------------------------------------------------------------------
+// constants
+// ---------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMortonBits = 21;          // bits per axis of the point codes
+constexpr int kMaxDepth = 14;            // octree depth cap
+constexpr int kMaxK = 32;                // kNN cap
+constexpr int kSrcFloats = 12;           // duplicated source record (x,x,y,y,z,z,mx,mx,...)
+constexpr int kSrcTile = 128;            // sources per shared-memory tile
+constexpr int kBucket = 16;              // points per kNN bucket
+constexpr int kSelBins = 4096;           // radix-select bins (level 1 and 2)
+
+// device error flags (bitmask in ctx->d_err)
+constexpr int kErrTimeout = 1;
+constexpr int kErrNonfinite = 2;
+constexpr int kErrOverflow = 4;
+constexpr int kErrStack = 8;
+
+// ---------------------------------------------------------------------------
+// iteration state on the device (one struct, updated by kernels)
+// ---------------------------------------------------------------------------
+struct IterState {
+    int iter;            // iterations performed in the current orient
+    int done;            // converged flag
+    int max_iters;
+    int nfaces;          // faces emitted in the current iteration
+    double iso;          // w_bar of the current iteration
+    double stat;         // convergence statistic of the current iteration
+};
+
+struct EvalParams {
+    float eps2;        // eps^2
+    float s;           // sqrt(lambda)
+    float s2;          // lambda
+    float nl2e_s;      // -sqrt(lambda) * log2(e)
+    int screened;
+};
+
+// ---------------------------------------------------------------------------
+// engine context
+// ---------------------------------------------------------------------------
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    std::string err;
+
+    int64_t n = 0;        // points
+    int64_t npad = 0;     // sources padded to a multiple of kSrcTile
+    // parameters
+    int kernel = DWG_KERNEL_PLAIN;
+    float eps = 0.f, lambda = 0.f, tol = 0.1f;
+    int max_iters = 30;
+    int depth = 8, knn = 10, mode = DWG_UPDATE_LEVELSET;
+    int init_mode = DWG_INIT_RANDOM;
+    uint64_t seed = 1;
+    bool normals_pending = true;   // initial normals must be (re)generated
+
+    // geometry (sorted along the Morton curve)
+    double cube_lo[3] = {0, 0, 0};
+    double cube_L = 1.0;
+    float4 *d_p4 = nullptr;        // (x, y, z, a) sorted
+    int64_t *d_perm = nullptr;     // sorted index -> input index
+    uint64_t *d_codes = nullptr;   // 63-bit Morton codes, sorted
+    float *d_src = nullptr;        // npad x kSrcFloats source records
+    float4 *d_nrm = nullptr;       // current normals, sorted
+    float4 *d_nrm_init = nullptr;  // given initial normals, sorted
+    float *d_dtheta = nullptr;
+    float4 *d_wg = nullptr;        // (gx, gy, gz, w) at the points
+
+    // kNN bucket hierarchy: complete binary tree over buckets of kBucket points
+    int knn_levels = 0;            // leaves at level knn_levels (2^levels leaves)
+    float4 *d_bvh_lo = nullptr;    // node AABB min (x,y,z,_)
+    float4 *d_bvh_hi = nullptr;    // node AABB max
+
+    // discretisation (depth-dependent)
+    int built_depth = -1;
+    int64_t nleaves = 0, ncorners = 0, max_faces = 0;
+    int4 *d_leaves = nullptr;          // (level, code lo32, code hi32, nonempty) per leaf
+    int *d_leaf_corners = nullptr;     // nleaves x 8 corner indices
+    uint64_t *d_corner_keys = nullptr; // Morton keys of corners (sorted)
+    float4 *d_corner_pos = nullptr;
+    float *d_wc = nullptr;             // w at corners
+    float4 *d_faces = nullptr;         // 2 x max_faces: area vector, centroid
+    unsigned long long *d_acc = nullptr; // n x 3 fixed-point face sums
+    double acc_scale = 1.0;
+
+    // evaluation scratch: partial sums per source chunk
+    int nchunks_p = 1, nchunks_c = 1;
+    float *d_part_p = nullptr;   // [nchunks][4][2][n]
+    float *d_part_c = nullptr;   // [nchunks][2][ncorners]
+    size_t part_p_cap = 0, part_c_cap = 0;
+    double *d_wsum_blocks = nullptr;  // per-block w sums at the points
+    int wsum_blocks = 0;
+    double *d_dn_blocks = nullptr;    // per-block sums of |n_new - n_old|
+
+    // iteration state and traces
+    IterState *d_state = nullptr;
+    double *d_tr_iso = nullptr, *d_tr_stat = nullptr, *d_tr_dn = nullptr;
+    long long *d_tr_faces = nullptr;
+    int trace_cap = 0;
+    int *d_err = nullptr;
+
+    // graph
+    cudaGraphExec_t graph_exec = nullptr;
+    bool graph_valid = false;
+
+    // last results
+    dwg_stats stats{};
+    std::vector<double> tr_iso, tr_stat, tr_dn;
+    std::vector<int64_t> tr_faces;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define DWG_CUDA_TRY(ctx, call)                                                   \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+            return (e_ == cudaErrorMemoryAllocation) ? DWG_ERR_OOM : DWG_ERR_CUDA; \
+        }                                                                         \
+    } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Morton interleave of a 21-bit value (bit k goes to bit 3k).
+__host__ __device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+// inverse of spread3
+__host__ __device__ __forceinline__ uint64_t compact3(uint64_t v)
+{
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return v;
+}
+__host__ __device__ __forceinline__ uint64_t morton3(uint64_t x, uint64_t y, uint64_t z)
+{
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+#ifdef __CUDACC__
+// Cell index along one axis at 2^21 cells per cube edge: floor((x - lo) * inv_h)
+// clamped to [0, 2^21 - 1], with explicitly rounded double operations (no
+// contraction) so that the result is reproducible bit for bit.
+__device__ __forceinline__ int64_t quant21(float x, double lo, double inv_h)
+{
+    double t = __dmul_rn(__dsub_rn((double)x, lo), inv_h);
+    double f = floor(t);
+    if (f < 0.0) return 0;
+    if (f > 2097151.0) return 2097151;
+    return (int64_t)f;
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files); all return cudaGetLastError()
+// ---------------------------------------------------------------------------
+// dwg_build.cu
+cudaError_t launch_check_finite(const float *xyz, int64_t n, int *err, cudaStream_t s);
+cudaError_t launch_bbox(const float *xyz, int64_t n, float *d_minmax /*6*/, cudaStream_t s);
+cudaError_t launch_morton(const float *xyz, int64_t n, double lo0, double lo1, double lo2,
+                          double inv_h21, uint64_t *keys, int64_t *idx, cudaStream_t s);
+int radix_sort_pairs(Ctx *c, uint64_t *keys, int64_t *vals, int64_t n, int key_bits);
+cudaError_t launch_gather_points(const float *xyz, const float *a, const int64_t *perm,
+                                 int64_t n, float4 *p4, cudaStream_t s);
+int build_knn_tree(Ctx *c);
+int build_discretization(Ctx *c, int depth);
+
+// dwg_eval.cu
+int eval_chunks(const Ctx *c, int64_t m, bool grad);
+int eval_launch(Ctx *c, const float4 *q, int64_t m, bool grad, int nchunks, float *part,
+                int64_t stride);
+cudaError_t launch_pack_sources(const float4 *p4, const float4 *nrm, int64_t n, int64_t npad,
+                                float *src, cudaStream_t s);
+cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t m,
+                                 const float4 *queries, int self_mode, bool grad, float4 *out,
+                                 double *wsum_blocks);
+cudaError_t launch_reduce_w(Ctx *c, const float *part, int nchunks, int64_t m, float *out);
+int wsum_block_count(int64_t n);
+
+// dwg_iter.cu
+cudaError_t launch_iso(Ctx *c);
+cudaError_t launch_mc_faces(Ctx *c);
+cudaError_t launch_knn_scatter(Ctx *c);
+cudaError_t launch_normal_update(Ctx *c);
+cudaError_t launch_select(Ctx *c, cudaGraphConditionalHandle cond, int use_cond);
+cudaError_t launch_random_normals(float4 *nrm, const int64_t *perm, int64_t n, uint64_t seed,
+                                  cudaStream_t s);
+cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t *idx_out);
+
+}  // namespace dwg

@@ -1,0 +1,593 @@
+// dwg_iter.cu -- the per-iteration steps after the GWN evaluation
+// (paper Alg. 1, Sec. 4.3, Sec. 5.1):
+//   k_iso          iso-value w_bar = mean of w over the input points (Eq. 6,
+//                  averaged over the inputs), FP64, fixed summation order;
+//   k_mc_faces     level set of w - w_bar in every octree leaf, realised as
+//                  the six-tetrahedron split of the leaf cube; one face per
+//                  cut tetrahedron with its vector area (the cross-product
+//                  gradient of Sec. 4.3) oriented toward increasing w;
+//   k_knn_scatter  each face adds its vector to its k nearest input points
+//                  (Eq. 7); sums are 64-bit fixed point, so the result does
+//                  not depend on the order of the atomic additions;
+//   k_normal_update  n_i <- -sum / |sum| (a point no face chose keeps its
+//                  normal), the per-point change in degrees, next sources;
+//   k_select       convergence statistic of Sec. 5.1: mean of the
+//                  ceil(n / 100) largest changes, by exact three-level radix
+//                  select on the float bits, then the loop condition.
+#include "dwg_internal.cuh"
+
+namespace dwg {
+
+// ---------------------------------------------------------------------------
+// iso-value
+// ---------------------------------------------------------------------------
+__global__ void k_iso(const double *__restrict__ wsum_blocks, int nb, int64_t n, IterState *st)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += wsum_blocks[b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st->iso = sh[0] / (double)n;
+        st->nfaces = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// level-set faces
+// ---------------------------------------------------------------------------
+__constant__ int c_tets[6][4] = {{0, 1, 3, 7}, {0, 3, 2, 7}, {0, 2, 6, 7},
+                                 {0, 6, 4, 7}, {0, 4, 5, 7}, {0, 5, 1, 7}};
+
+struct F3 {
+    float x, y, z;
+};
+__device__ __forceinline__ F3 f3(float4 v) { return {v.x, v.y, v.z}; }
+__device__ __forceinline__ F3 operator-(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ F3 cross(F3 a, F3 b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ F3 lerp0(F3 xa, float fa, F3 xb, float fb)
+{
+    float t = fa / (fa - fb);
+    return {xa.x + t * (xb.x - xa.x), xa.y + t * (xb.y - xa.y), xa.z + t * (xb.z - xa.z)};
+}
+
+// polygon of one tetrahedron: returns false when the level set misses it
+__device__ __forceinline__ bool tet_face(const F3 x[4], const float f[4], const bool ab[4],
+                                         F3 &area, F3 &cen)
+{
+    int na = (int)ab[0] + (int)ab[1] + (int)ab[2] + (int)ab[3];
+    if (na == 0 || na == 4) return false;
+    F3 P[4];
+    int np;
+    if (na == 1 || na == 3) {
+        bool want = (na == 1);
+        int lone = 0;
+        for (int i = 0; i < 4; ++i)
+            if (ab[i] == want) lone = i;
+        np = 0;
+        for (int i = 0; i < 4; ++i)
+            if (i != lone) P[np++] = lerp0(x[lone], f[lone], x[i], f[i]);
+        area = cross(P[1] - P[0], P[2] - P[0]);
+    } else {
+        int a0 = -1, a1 = -1, b0 = -1, b1 = -1;
+        for (int i = 0; i < 4; ++i) {
+            if (ab[i]) { if (a0 < 0) a0 = i; else a1 = i; }
+            else { if (b0 < 0) b0 = i; else b1 = i; }
+        }
+        P[0] = lerp0(x[a0], f[a0], x[b0], f[b0]);
+        P[1] = lerp0(x[a0], f[a0], x[b1], f[b1]);
+        P[2] = lerp0(x[a1], f[a1], x[b1], f[b1]);
+        P[3] = lerp0(x[a1], f[a1], x[b0], f[b0]);
+        np = 4;
+        area = cross(P[2] - P[0], P[3] - P[1]);
+    }
+    area.x *= 0.5f; area.y *= 0.5f; area.z *= 0.5f;
+    F3 ca = {0, 0, 0}, cb = {0, 0, 0};
+    for (int i = 0; i < 4; ++i) {
+        if (ab[i]) { ca.x += x[i].x; ca.y += x[i].y; ca.z += x[i].z; }
+        else { cb.x += x[i].x; cb.y += x[i].y; cb.z += x[i].z; }
+    }
+    float ia = 1.f / na, ib = 1.f / (4 - na);
+    F3 dir = {ca.x * ia - cb.x * ib, ca.y * ia - cb.y * ib, ca.z * ia - cb.z * ib};
+    if (area.x * dir.x + area.y * dir.y + area.z * dir.z < 0.f) {
+        area.x = -area.x; area.y = -area.y; area.z = -area.z;
+    }
+    F3 s = {0, 0, 0};
+    for (int i = 0; i < np; ++i) { s.x += P[i].x; s.y += P[i].y; s.z += P[i].z; }
+    float inv = 1.f / np;
+    cen = {s.x * inv, s.y * inv, s.z * inv};
+    return true;
+}
+
+__global__ void __launch_bounds__(256)
+    k_mc_faces(const int *__restrict__ leaf_corners, int64_t nl, const float4 *__restrict__ cpos,
+               const float *__restrict__ wc, IterState *st, float4 *__restrict__ faces,
+               int64_t max_faces, int *err)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double iso = st->iso;
+    F3 area[6], cen[6];
+    int cnt = 0;
+    if (l < nl) {
+        F3 x[8];
+        float f[8];
+        bool ab[8];
+        for (int v = 0; v < 8; ++v) {
+            int ci = leaf_corners[l * 8 + v];
+            x[v] = f3(cpos[ci]);
+            double df = (double)wc[ci] - iso;
+            f[v] = (float)df;
+            ab[v] = df > 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            F3 xt[4];
+            float ft[4];
+            bool at[4];
+            for (int i = 0; i < 4; ++i) {
+                int v = c_tets[t][i];
+                xt[i] = x[v];
+                ft[i] = f[v];
+                at[i] = ab[v];
+            }
+            if (tet_face(xt, ft, at, area[cnt], cen[cnt])) ++cnt;
+        }
+    }
+    // warp-aggregated append
+    const int lane = threadIdx.x & 31;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int total = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(&st->nfaces, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    int64_t o = (int64_t)base + incl - cnt;
+    for (int k = 0; k < cnt; ++k, ++o) {
+        if (o >= max_faces) {
+            atomicOr(err, kErrOverflow);
+            break;
+        }
+        faces[2 * o] = make_float4(area[k].x, area[k].y, area[k].z, 0.f);
+        faces[2 * o + 1] = make_float4(cen[k].x, cen[k].y, cen[k].z, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exact k nearest points over the bucket tree
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float box_d2(float4 lo, float4 hi, F3 q)
+{
+    float dx = fmaxf(fmaxf(lo.x - q.x, q.x - hi.x), 0.f);
+    float dy = fmaxf(fmaxf(lo.y - q.y, q.y - hi.y), 0.f);
+    float dz = fmaxf(fmaxf(lo.z - q.z, q.z - hi.z), 0.f);
+    return fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
+}
+__device__ __forceinline__ float pt_d2(float4 p, F3 q)
+{
+    float dx = __fsub_rn(p.x, q.x), dy = __fsub_rn(p.y, q.y), dz = __fsub_rn(p.z, q.z);
+    return fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
+}
+
+struct KnnTree {
+    const float4 *p4;
+    const int64_t *perm;
+    int64_t n;
+    const float4 *lo, *hi;
+    int levels;
+};
+
+// (d, o) strictly before (e, p): smaller distance, ties to the smaller input index
+__device__ __forceinline__ bool before(float d, int64_t o, float e, int64_t p)
+{
+    return d < e || (d == e && o < p);
+}
+
+template <int KMAX>
+__device__ __forceinline__ int knn_search(const KnnTree &T, F3 q, int k, int *bj, int *err)
+{
+    float bd[KMAX];
+    int64_t bo[KMAX];
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) {
+        bd[t] = INFINITY;
+        bo[t] = INT64_MAX;
+        bj[t] = -1;
+    }
+    const int64_t nleaf = (int64_t)1 << T.levels;
+    int stack[64];
+    int sp = 0;
+    stack[sp++] = 1;
+    while (sp > 0) {
+        int node = stack[--sp];
+        float worst = bd[k - 1];
+        if (box_d2(T.lo[node], T.hi[node], q) > worst) continue;
+        if (node >= nleaf) {
+            int64_t j0 = (int64_t)(node - nleaf) * kBucket;
+            int64_t j1 = min(j0 + kBucket, T.n);
+            for (int64_t j = j0; j < j1; ++j) {
+                float d = pt_d2(T.p4[j], q);
+                int64_t o = T.perm[j];
+                if (!before(d, o, bd[k - 1], bo[k - 1])) continue;
+#pragma unroll
+                for (int t = KMAX - 1; t >= 0; --t) {
+                    if (t >= k) continue;
+                    bool prev = t > 0 && before(d, o, bd[t > 0 ? t - 1 : 0], bo[t > 0 ? t - 1 : 0]);
+                    bool cur = before(d, o, bd[t], bo[t]);
+                    if (prev) {
+                        bd[t] = bd[t - 1];
+                        bo[t] = bo[t - 1];
+                        bj[t] = bj[t - 1];
+                    } else if (cur) {
+                        bd[t] = d;
+                        bo[t] = o;
+                        bj[t] = (int)j;
+                    }
+                }
+            }
+        } else {
+            int a = 2 * node, b = 2 * node + 1;
+            float da = box_d2(T.lo[a], T.hi[a], q), db = box_d2(T.lo[b], T.hi[b], q);
+            float worst2 = bd[k - 1];
+            if (sp + 2 > 64) {
+                atomicOr(err, kErrStack);
+                break;
+            }
+            // push the farther child first so that the nearer one is visited first
+            if (da <= db) {
+                if (db <= worst2) stack[sp++] = b;
+                if (da <= worst2) stack[sp++] = a;
+            } else {
+                if (da <= worst2) stack[sp++] = a;
+                if (db <= worst2) stack[sp++] = b;
+            }
+        }
+    }
+    int found = 0;
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t)
+        if (t < k && bj[t] >= 0) ++found;
+    return found;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(128)
+    k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
+                  KnnTree T, int k, double scale, unsigned long long *acc, int *err)
+{
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nf = min((int64_t)st->nfaces, max_faces);
+    if (f >= nf) return;
+    float4 A = faces[2 * f], C = faces[2 * f + 1];
+    int bj[KMAX];
+    knn_search<KMAX>(T, F3{C.x, C.y, C.z}, k, bj, err);
+    long long vx = llrint((double)A.x * scale);
+    long long vy = llrint((double)A.y * scale);
+    long long vz = llrint((double)A.z * scale);
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) {
+        if (t >= k || bj[t] < 0) continue;
+        unsigned long long *a = acc + 3 * (int64_t)bj[t];
+        atomicAdd(a + 0, (unsigned long long)vx);
+        atomicAdd(a + 1, (unsigned long long)vy);
+        atomicAdd(a + 2, (unsigned long long)vz);
+    }
+}
+
+template <int KMAX>
+__global__ void k_knn_query(const float4 *__restrict__ q, int64_t m, KnnTree T, int k,
+                            int64_t *idx_out, int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    float4 v = q[i];
+    int bj[KMAX];
+    knn_search<KMAX>(T, F3{v.x, v.y, v.z}, k, bj, err);
+    for (int t = 0; t < k; ++t) idx_out[i * k + t] = bj[t] >= 0 ? T.perm[bj[t]] : -1;
+}
+
+// ---------------------------------------------------------------------------
+// normal update (Eq. 7) and per-point change
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    k_normal_update(int mode, int64_t n, unsigned long long *__restrict__ acc, double inv_scale,
+                    const float4 *__restrict__ wg, const float4 *__restrict__ p4,
+                    float4 *__restrict__ nrm, float *__restrict__ src,
+                    float *__restrict__ dtheta, double *__restrict__ dn_blocks)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dn = 0.0;
+    if (i < n) {
+        float4 o = nrm[i];
+        float nx = o.x, ny = o.y, nz = o.z;
+        if (mode == DWG_UPDATE_LEVELSET) {
+            unsigned long long *a = acc + 3 * i;
+            double ax = (double)(long long)a[0] * inv_scale;
+            double ay = (double)(long long)a[1] * inv_scale;
+            double az = (double)(long long)a[2] * inv_scale;
+            a[0] = 0ull; a[1] = 0ull; a[2] = 0ull;
+            double len = sqrt(ax * ax + ay * ay + az * az);
+            if (len > 0.0) {
+                nx = (float)(-ax / len);
+                ny = (float)(-ay / len);
+                nz = (float)(-az / len);
+            }
+        } else {
+            float4 g = wg[i];
+            float len = sqrtf(g.x * g.x + g.y * g.y + g.z * g.z);
+            if (len > 0.f && isfinite(len)) {
+                nx = -g.x / len;
+                ny = -g.y / len;
+                nz = -g.z / len;
+            }
+        }
+        float cx = o.y * nz - o.z * ny, cy = o.z * nx - o.x * nz, cz = o.x * ny - o.y * nx;
+        float sn = sqrtf(cx * cx + cy * cy + cz * cz);
+        float cs = o.x * nx + o.y * ny + o.z * nz;
+        dtheta[i] = atan2f(sn, cs) * (float)(180.0 / kPi);
+        float ex = nx - o.x, ey = ny - o.y, ez = nz - o.z;
+        dn = (double)sqrtf(ex * ex + ey * ey + ez * ez);
+        nrm[i] = make_float4(nx, ny, nz, 0.f);
+        float c = p4[i].w * (float)(1.0 / (4.0 * kPi));
+        float4 *r = reinterpret_cast<float4 *>(src + i * kSrcFloats);
+        float mx = c * nx, my = c * ny, mz = c * nz;
+        r[1] = make_float4(r[1].x, r[1].y, mx, mx);
+        r[2] = make_float4(my, my, mz, mz);
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = dn;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dn_blocks[blockIdx.x] = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// convergence: exact mean of the ceil(n/100) largest changes
+// ---------------------------------------------------------------------------
+constexpr int kSelThreads = 1024;
+
+// exclusive block scan of one unsigned per thread (1024 threads)
+__device__ unsigned block_scan_u(unsigned v, unsigned *warp_sums, unsigned &total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        unsigned s = warp_sums[lane];
+        unsigned si = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned x = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += x;
+        }
+        warp_sums[lane] = si - s;
+        if (lane == 31) warp_sums[32] = si;
+    }
+    __syncthreads();
+    unsigned r = warp_sums[w] + incl - v;
+    total = warp_sums[32];
+    __syncthreads();
+    return r;
+}
+
+// Among the bins of hist (nb bins, 4 per thread), find b with
+// suffix(b) >= k > suffix(b + 1); returns b and the count strictly above.
+__device__ void find_bin(const unsigned *hist, int nb, unsigned k, unsigned *warp_sums,
+                         int *s_bin, unsigned *s_above)
+{
+    unsigned loc[4];
+    unsigned s = 0;
+    int b0 = threadIdx.x * 4;
+    for (int t = 0; t < 4; ++t) {
+        loc[t] = (b0 + t < nb) ? hist[b0 + t] : 0u;
+        s += loc[t];
+    }
+    unsigned total;
+    unsigned ex = block_scan_u(s, warp_sums, total);
+    for (int t = 0; t < 4; ++t) {
+        int b = b0 + t;
+        unsigned suffix = total - ex;  // count in bins >= b
+        if (b < nb && suffix >= k && suffix - loc[t] < k) {
+            *s_bin = b;
+            *s_above = suffix - loc[t];
+        }
+        ex += loc[t];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+    k_select(const float *__restrict__ dtheta, int64_t n, float tol, IterState *st,
+             const double *__restrict__ dn_blocks, int ndn, double *tr_iso, double *tr_stat,
+             double *tr_dn, long long *tr_faces, cudaGraphConditionalHandle cond, int use_cond)
+{
+    __shared__ unsigned hist[kSelBins];
+    __shared__ unsigned warp_sums[33];
+    __shared__ int s_bin;
+    __shared__ unsigned s_above;
+    __shared__ double sh[kSelThreads];
+    const unsigned *bits = reinterpret_cast<const unsigned *>(dtheta);
+    unsigned k = (unsigned)((n + 99) / 100);
+    unsigned krem = k, above_total = 0;
+    unsigned prefix = 0;
+    // level 1: bits 31..20, level 2: bits 19..8, level 3: bits 7..0
+    const int shifts[3] = {20, 8, 0};
+    const int nbins[3] = {4096, 4096, 256};
+    for (int lv = 0; lv < 3; ++lv) {
+        for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        int sh_hi = shifts[lv] + (lv == 2 ? 8 : 12);  // bits above this level's field
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            unsigned v = bits[i];
+            if (lv > 0 && (v >> sh_hi) != prefix) continue;
+            unsigned bin = (v >> shifts[lv]) & (unsigned)(nbins[lv] - 1);
+            atomicAdd(&hist[bin], 1u);
+        }
+        __syncthreads();
+        find_bin(hist, nbins[lv], krem, warp_sums, &s_bin, &s_above);
+        prefix = (prefix << (lv == 2 ? 8 : 12)) | (unsigned)s_bin;
+        above_total += s_above;
+        krem -= s_above;
+        __syncthreads();
+    }
+    const unsigned tbits = prefix;
+    const float tval = __uint_as_float(tbits);
+    // sum of the values strictly above the threshold, FP64, fixed order
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        if (bits[i] > tbits) s += (double)dtheta[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    double sum_above = sh[0];
+    __syncthreads();
+    double dn = 0.0;
+    for (int b = threadIdx.x; b < ndn; b += blockDim.x) dn += dn_blocks[b];
+    sh[threadIdx.x] = dn;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double stat = (sum_above + (double)(k - above_total) * (double)tval) / (double)k;
+        int it = st->iter;
+        st->stat = stat;
+        if (tr_iso && it < st->max_iters) {
+            tr_iso[it] = st->iso;
+            tr_stat[it] = stat;
+            tr_dn[it] = sh[0] / (double)n;
+            tr_faces[it] = st->nfaces;
+        }
+        it += 1;
+        st->iter = it;
+        int done = stat <= (double)tol;
+        st->done = done;
+        if (use_cond) cudaGraphSetConditional(cond, (!done && it < st->max_iters) ? 1u : 0u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// random unit normals from splitmix64 (stream 7)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_random_normals(float4 *nrm, const int64_t *perm, int64_t n, uint64_t key)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t j = (uint64_t)perm[i];
+    const uint64_t G = 0x9E3779B97F4A7C15ull;
+    uint64_t a = mix64(key + (2 * j + 1) * G), b = mix64(key + (2 * j + 2) * G);
+    double u0 = (double)(a >> 11) * 0x1.0p-53, u1 = (double)(b >> 11) * 0x1.0p-53;
+    double z = 1.0 - 2.0 * u0;
+    double phi = 2.0 * kPi * u1;
+    double s = sqrt(fmax(0.0, 1.0 - z * z));
+    nrm[i] = make_float4((float)(s * cos(phi)), (float)(s * sin(phi)), (float)z, 0.f);
+}
+
+cudaError_t launch_random_normals(float4 *nrm, const int64_t *perm, int64_t n, uint64_t seed,
+                                  cudaStream_t s)
+{
+    uint64_t key = mix64(((seed & 0xFFFFFFFFull) << 32) | 7ull);
+    k_random_normals<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(nrm, perm, n, key);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static KnnTree knn_tree(const Ctx *c)
+{
+    KnnTree T;
+    T.p4 = c->d_p4;
+    T.perm = c->d_perm;
+    T.n = c->n;
+    T.lo = c->d_bvh_lo;
+    T.hi = c->d_bvh_hi;
+    T.levels = c->knn_levels;
+    return T;
+}
+
+cudaError_t launch_iso(Ctx *c)
+{
+    k_iso<<<1, 256, 0, c->stream>>>(c->d_wsum_blocks, c->wsum_blocks, c->n, c->d_state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_faces(Ctx *c)
+{
+    k_mc_faces<<<(unsigned)ceil_div(c->nleaves, 256), 256, 0, c->stream>>>(
+        c->d_leaf_corners, c->nleaves, c->d_corner_pos, c->d_wc, c->d_state, c->d_faces,
+        c->max_faces, c->d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn_scatter(Ctx *c)
+{
+    // one thread per possible face; threads past the emitted count exit
+    unsigned blocks = (unsigned)ceil_div(c->max_faces, 128);
+    KnnTree T = knn_tree(c);
+    if (c->knn <= 10)
+        k_knn_scatter<10><<<blocks, 128, 0, c->stream>>>(c->d_faces, c->d_state, c->max_faces, T,
+                                                         c->knn, c->acc_scale, c->d_acc, c->d_err);
+    else
+        k_knn_scatter<32><<<blocks, 128, 0, c->stream>>>(c->d_faces, c->d_state, c->max_faces, T,
+                                                         c->knn, c->acc_scale, c->d_acc, c->d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t *idx_out)
+{
+    KnnTree T = knn_tree(c);
+    unsigned blocks = (unsigned)ceil_div(m, 128);
+    if (k <= 10)
+        k_knn_query<10><<<blocks, 128, 0, c->stream>>>(q, m, T, k, idx_out, c->d_err);
+    else
+        k_knn_query<32><<<blocks, 128, 0, c->stream>>>(q, m, T, k, idx_out, c->d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normal_update(Ctx *c)
+{
+    k_normal_update<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->stream>>>(
+        c->mode, c->n, c->d_acc, 1.0 / c->acc_scale, c->d_wg, c->d_p4, c->d_nrm, c->d_src,
+        c->d_dtheta, c->d_dn_blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(Ctx *c, cudaGraphConditionalHandle cond, int use_cond)
+{
+    k_select<<<1, kSelThreads, 0, c->stream>>>(c->d_dtheta, c->n, c->tol, c->d_state,
+                                               c->d_dn_blocks, (int)ceil_div(c->n, 256),
+                                               c->d_tr_iso, c->d_tr_stat, c->d_tr_dn,
+                                               c->d_tr_faces, cond, use_cond);
+    return cudaGetLastError();
+}
+
+}  // namespace dwg

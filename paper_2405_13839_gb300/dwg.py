@@ -1,0 +1,272 @@
+"""ctypes binding of libdwg.so: the C ABI of include/dwg.h, one Python function
+per C function with the same name.
+
+The binding only marshals arguments: arrays may be numpy arrays (host) or
+torch tensors (host or CUDA); their data pointers are passed straight to the
+library, which tells host from device memory itself.  Every computation runs
+in the library's CUDA kernels.  If libdwg.so is missing, importing this
+module raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DWG_OK = 0
+DWG_NOT_CONVERGED = 1
+DWG_ERR_INVALID = -1
+DWG_ERR_CUDA = -2
+DWG_ERR_OOM = -3
+DWG_ERR_NONFINITE = -4
+DWG_ERR_TIMEOUT = -5
+DWG_ERR_STATE = -6
+DWG_KERNEL_PLAIN = 0
+DWG_KERNEL_SCREENED = 1
+DWG_UPDATE_LEVELSET = 0
+DWG_UPDATE_DIRECT = 1
+DWG_INIT_RANDOM = 0
+DWG_INIT_GIVEN = 1
+
+_NAMES = {v: k for k, v in dict(
+    DWG_ERR_INVALID=-1, DWG_ERR_CUDA=-2, DWG_ERR_OOM=-3, DWG_ERR_NONFINITE=-4,
+    DWG_ERR_TIMEOUT=-5, DWG_ERR_STATE=-6).items()}
+
+
+class DWGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dwg_stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_corners", ctypes.c_int64), ("iters", ctypes.c_int),
+                ("converged", ctypes.c_int), ("faces_last", ctypes.c_int64),
+                ("iso_last", ctypes.c_double), ("stat_last", ctypes.c_double),
+                ("interactions", ctypes.c_double), ("ms_orient", ctypes.c_double)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(_build.LIB):
+        raise ImportError(
+            f"libdwg.so not built ({_build.LIB}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    I = ctypes.c_int
+    F = ctypes.c_float
+    H = ctypes.c_void_p
+    sig = {
+        "dwg_create": ([P, I64, ctypes.POINTER(H)], I),
+        "dwg_destroy": ([H], None),
+        "dwg_last_error": ([H], ctypes.c_char_p),
+        "dwg_set_stream": ([H, P], I),
+        "dwg_set_params": ([H, I, F, F, I, F], I),
+        "dwg_set_update": ([H, I, I, I], I),
+        "dwg_set_weights": ([H, P], I),
+        "dwg_set_init": ([H, I, ctypes.c_uint64, P], I),
+        "dwg_orient": ([H, P, ctypes.POINTER(I)], I),
+        "dwg_step": ([H, P, P, P, ctypes.POINTER(ctypes.c_double),
+                      ctypes.POINTER(ctypes.c_double)], I),
+        "dwg_get_normals": ([H, P], I),
+        "dwg_set_normals": ([H, P], I),
+        "dwg_eval_gwn": ([H, P, I64, P, P], I),
+        "dwg_get_stats": ([H, ctypes.POINTER(dwg_stats)], I),
+        "dwg_get_trace": ([H, P, P, P, P, I, ctypes.POINTER(I)], I),
+        "dwg_get_leaves": ([H, P, I64, ctypes.POINTER(I64)], I),
+        "dwg_get_corners": ([H, P, I64, ctypes.POINTER(I64)], I),
+        "dwg_knn": ([H, P, I64, I, P], I),
+        "dwg_profile_step": ([H, P, I, ctypes.POINTER(I)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+def _ptr(a):
+    """Data pointer of a contiguous numpy array or torch tensor (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check_f32(a, cols=None, name="array"):
+    dt = getattr(a, "dtype", None)
+    ok = dt == np.float32 or str(dt) == "torch.float32"
+    if not ok:
+        raise TypeError(f"{name} must be float32, got {dt}")
+    if cols is not None and (a.ndim != 2 or a.shape[1] != cols):
+        raise ValueError(f"{name} must have shape (n, {cols})")
+
+
+def _raise(h, rc):
+    if rc < 0:
+        msg = _lib.dwg_last_error(h)
+        raise DWGError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _like(ref, shape, dtype=np.float32):
+    """Output buffer on the same side (host/device) as ref."""
+    if isinstance(ref, np.ndarray):
+        return np.empty(shape, dtype=dtype)
+    import torch
+    tdt = {np.float32: torch.float32, np.int64: torch.int64}[dtype]
+    return torch.empty(shape, dtype=tdt, device=ref.device)
+
+
+# ----------------------------------------------------------------------------
+# the ABI, one function per C entry point
+# ----------------------------------------------------------------------------
+def dwg_create(points):
+    """Handle for a float32 (n, 3) cloud (numpy, or torch on host or GPU)."""
+    _check_f32(points, 3, "points")
+    h = ctypes.c_void_p()
+    rc = _lib.dwg_create(_ptr(points), int(points.shape[0]), ctypes.byref(h))
+    _raise(None, rc)
+    return h
+
+
+def dwg_destroy(h):
+    _lib.dwg_destroy(h)
+
+
+def dwg_last_error(h=None):
+    m = _lib.dwg_last_error(h)
+    return m.decode() if m else ""
+
+
+def dwg_set_stream(h, stream):
+    """stream: a cudaStream_t as int (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+    return _raise(h, _lib.dwg_set_stream(h, stream))
+
+
+def dwg_set_params(h, kernel, eps, screening, max_iters, tol):
+    return _raise(h, _lib.dwg_set_params(h, int(kernel), float(eps), float(screening),
+                                         int(max_iters), float(tol)))
+
+
+def dwg_set_update(h, depth, knn=10, mode=DWG_UPDATE_LEVELSET):
+    return _raise(h, _lib.dwg_set_update(h, int(depth), int(knn), int(mode)))
+
+
+def dwg_set_weights(h, a):
+    _check_f32(a, None, "weights")
+    return _raise(h, _lib.dwg_set_weights(h, _ptr(a)))
+
+
+def dwg_set_init(h, mode, seed=1, normals=None):
+    if normals is not None:
+        _check_f32(normals, 3, "normals")
+    return _raise(h, _lib.dwg_set_init(h, int(mode), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                       _ptr(normals)))
+
+
+def dwg_orient(h, normals_out):
+    """Runs Algorithm 1; fills normals_out (float32 (n, 3)).  Returns (rc, iters)."""
+    it = ctypes.c_int()
+    rc = _lib.dwg_orient(h, _ptr(normals_out), ctypes.byref(it))
+    _raise(h, rc)
+    return rc, it.value
+
+
+def dwg_step(h, w_out=None, grad_out=None, dtheta_out=None):
+    """One iteration.  Returns (iso, stat)."""
+    iso = ctypes.c_double()
+    st = ctypes.c_double()
+    rc = _lib.dwg_step(h, _ptr(w_out), _ptr(grad_out), _ptr(dtheta_out), ctypes.byref(iso),
+                       ctypes.byref(st))
+    _raise(h, rc)
+    return iso.value, st.value
+
+
+def dwg_get_normals(h, normals_out):
+    return _raise(h, _lib.dwg_get_normals(h, _ptr(normals_out)))
+
+
+def dwg_set_normals(h, normals):
+    _check_f32(normals, 3, "normals")
+    return _raise(h, _lib.dwg_set_normals(h, _ptr(normals)))
+
+
+def dwg_eval_gwn(h, queries, w_out, grad_out=None):
+    _check_f32(queries, 3, "queries")
+    return _raise(h, _lib.dwg_eval_gwn(h, _ptr(queries), int(queries.shape[0]), _ptr(w_out),
+                                       _ptr(grad_out)))
+
+
+def dwg_get_stats(h):
+    s = dwg_stats()
+    _raise(h, _lib.dwg_get_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in dwg_stats._fields_}
+
+
+def dwg_get_trace(h, cap=100000):
+    cnt = ctypes.c_int()
+    _raise(h, _lib.dwg_get_trace(h, None, None, None, None, 0, ctypes.byref(cnt)))
+    k = cnt.value
+    iso = np.zeros(k)
+    stat = np.zeros(k)
+    dn = np.zeros(k)
+    faces = np.zeros(k, dtype=np.int64)
+    _raise(h, _lib.dwg_get_trace(h, iso.ctypes.data, stat.ctypes.data, dn.ctypes.data,
+                                 faces.ctypes.data, k, ctypes.byref(cnt)))
+    return dict(iso=iso, stat=stat, mean_dn=dn, faces=faces)
+
+
+def dwg_get_leaves(h):
+    cnt = ctypes.c_int64()
+    _raise(h, _lib.dwg_get_leaves(h, None, 0, ctypes.byref(cnt)))
+    out = np.zeros((cnt.value, 5), dtype=np.int64)
+    _raise(h, _lib.dwg_get_leaves(h, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    return out
+
+
+def dwg_get_corners(h):
+    cnt = ctypes.c_int64()
+    _raise(h, _lib.dwg_get_corners(h, None, 0, ctypes.byref(cnt)))
+    out = np.zeros(cnt.value, dtype=np.int64)
+    _raise(h, _lib.dwg_get_corners(h, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    return out
+
+
+def dwg_knn(h, queries, k, idx_out):
+    _check_f32(queries, 3, "queries")
+    return _raise(h, _lib.dwg_knn(h, _ptr(queries), int(queries.shape[0]), int(k),
+                                  _ptr(idx_out)))
+
+
+PROFILE_KERNELS = ["eval_points", "reduce_points", "iso", "eval_corners", "reduce_corners",
+                   "mc_faces", "knn_scatter", "normal_update", "select"]
+
+
+def dwg_profile_step(h):
+    """Per-kernel device milliseconds of one iteration (dict by kernel name)."""
+    ms = np.zeros(16, dtype=np.float32)
+    cnt = ctypes.c_int()
+    _raise(h, _lib.dwg_profile_step(h, ms.ctypes.data, 16, ctypes.byref(cnt)))
+    return {k: float(ms[i]) for i, k in enumerate(PROFILE_KERNELS[:cnt.value])}
