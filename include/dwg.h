@@ -82,8 +82,9 @@ int dwg_create(const float *points, int64_t n, dwg_handle *out);
 /* Release every device resource of the handle.  NULL is ignored. */
 void dwg_destroy(dwg_handle h);
 
-/* Text of the last failure on this handle, or of the last failed
- * dwg_create when h is NULL.  Valid until the next call on the handle. */
+/* Text of the last failure on this handle, or, when h is NULL, of the last
+ * failed call that takes no handle (dwg_create, dwg_eval_w_noalloc).  Valid
+ * until the next call on the handle. */
 const char *dwg_last_error(dwg_handle h);
 
 /* Issue all further work of the handle on this cudaStream_t (NULL: the
@@ -218,6 +219,43 @@ int dwg_profile_step(dwg_handle h, float *ms_out, int cap, int *count);
  * float32 distance go to the smaller input index; -1 when n < k).
  */
 int dwg_knn(dwg_handle h, const float *queries, int64_t m, int k, int64_t *idx_out);
+
+/*
+ * w at m query points for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an engineering entry point.
+ *
+ * Who needs it: a caller that manages all device memory itself -- a
+ * serving process with a fixed, pre-reserved HBM budget, a framework with its
+ * own pool allocator -- or that cannot accept cudaMalloc/cudaFree inside its
+ * work (cudaFree synchronises the whole device; an allocation may fail at any
+ * point of a run).  This call performs no device allocation and calls no
+ * allocating library routine.
+ *
+ * It computes exactly what dwg_eval_gwn computes without grad_out (Eq. 2/3,
+ * or Eq. 5 for DWG_KERNEL_SCREENED, softened by eps, FP32 terms with
+ * compensated sums) for the cloud given here, without a handle:
+ *   points   float32 n x 3, normals float32 n x 3 (normalised here; zero
+ *            vectors rejected), weights float32 n or NULL (a_i = 1),
+ *   queries  float32 m x 3, w_out float32 m,
+ * all in DEVICE memory of the current device (host pointers are rejected
+ * with DWG_ERR_INVALID); kernel, eps, screening as in dwg_set_params;
+ * stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * The call returns after w_out is written (it synchronises the stream).
+ *
+ * Limits: 1 <= n <= 65536 and 1 <= m <= 262144; larger sizes return
+ * DWG_ERR_INVALID with a message naming the limit.  Its scratch (source
+ * records, query records, partial sums, an error word: 15 MiB + 256 bytes)
+ * is a fixed device array in the library, held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents: calls that overlap on the GPU
+ * (other threads, other streams) race and must be serialised by the caller.
+ * Errors are reported by the return code and dwg_last_error(NULL).
+ */
+int dwg_eval_w_noalloc(const float *points, const float *normals, const float *weights,
+                       int64_t n, const float *queries, int64_t m, int kernel, float eps,
+                       float screening, float *w_out, void *stream);
 
 #ifdef __cplusplus
 }

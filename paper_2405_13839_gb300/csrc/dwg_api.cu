@@ -21,6 +21,15 @@ struct dwg_ctx : public Ctx {};
 static std::mutex g_err_mu;
 static std::string g_create_err;
 
+namespace dwg {
+// last error of the calls that have no handle (reported by dwg_last_error(NULL))
+void set_global_error(const std::string &msg)
+{
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_err = msg;
+}
+}  // namespace dwg
+
 static int fail(Ctx *c, int code, const std::string &msg)
 {
     if (c) c->err = msg;

@@ -614,4 +614,36 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// launchers without an engine context (caller-provided buffers)
+// ---------------------------------------------------------------------------
+int gwn_w_chunks_raw(int64_t m, int64_t npad, int device)
+{
+    return pick_chunks(ceil_div(m, kEvalThreads * 2 * kPW), npad / kSrcTile, num_sms(device));
+}
+
+cudaError_t launch_gwn_w_raw(const float *src, int64_t npad, const float4 *q, int64_t m,
+                             int nchunks, float *part, const EvalParams &ep, int *err,
+                             cudaStream_t s)
+{
+    constexpr int QB = kEvalThreads * 2 * kPW;
+    int64_t ntiles = npad / kSrcTile;
+    int tpc = (int)ceil_div(ntiles, nchunks);
+    dim3 grid((unsigned)ceil_div(m, QB), (unsigned)nchunks);
+    if (ep.screened)
+        k_gwn<kPW, false, true><<<grid, kEvalThreads, 0, s>>>(src, ntiles, q, m, tpc, part, m, ep,
+                                                              err);
+    else
+        k_gwn<kPW, false, false><<<grid, kEvalThreads, 0, s>>>(src, ntiles, q, m, tpc, part, m,
+                                                               ep, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_w_raw(const float *part, int nchunks, int64_t m, float *out,
+                                cudaStream_t s)
+{
+    k_reduce_w<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(part, nchunks, m, m, out);
+    return cudaGetLastError();
+}
+
 }  // namespace dwg

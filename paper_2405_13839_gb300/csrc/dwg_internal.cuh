@@ -205,6 +205,15 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
                                  double *wsum_blocks);
 cudaError_t launch_reduce_w(Ctx *c, const float *part, int nchunks, int64_t m, float *out);
 int wsum_block_count(int64_t n);
+int gwn_w_chunks_raw(int64_t m, int64_t npad, int device);
+cudaError_t launch_gwn_w_raw(const float *src, int64_t npad, const float4 *q, int64_t m,
+                             int nchunks, float *part, const EvalParams &ep, int *err,
+                             cudaStream_t s);
+cudaError_t launch_reduce_w_raw(const float *part, int nchunks, int64_t m, float *out,
+                                cudaStream_t s);
+
+// dwg_api.cu
+void set_global_error(const std::string &msg);
 
 // dwg_iter.cu
 cudaError_t launch_iso(Ctx *c);

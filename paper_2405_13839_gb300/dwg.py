@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "dwg_get_corners": ([H, P, I64, ctypes.POINTER(I64)], I),
         "dwg_knn": ([H, P, I64, I, P], I),
         "dwg_profile_step": ([H, P, I, ctypes.POINTER(I)], I),
+        "dwg_eval_w_noalloc": ([P, P, P, I64, P, I64, I, F, F, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -270,3 +271,17 @@ def dwg_profile_step(h):
     cnt = ctypes.c_int()
     _raise(h, _lib.dwg_profile_step(h, ms.ctypes.data, 16, ctypes.byref(cnt)))
     return {k: float(ms[i]) for i, k in enumerate(PROFILE_KERNELS[:cnt.value])}
+
+
+def dwg_eval_w_noalloc(points, normals, weights, queries, w_out, kernel=DWG_KERNEL_PLAIN,
+                       eps=1e-3, screening=0.0, stream=None):
+    """w at queries without any device allocation (all arrays CUDA tensors)."""
+    _check_f32(points, 3, "points")
+    _check_f32(normals, 3, "normals")
+    _check_f32(queries, 3, "queries")
+    if weights is not None:
+        _check_f32(weights, None, "weights")
+    rc = _lib.dwg_eval_w_noalloc(_ptr(points), _ptr(normals), _ptr(weights),
+                                 int(points.shape[0]), _ptr(queries), int(queries.shape[0]),
+                                 int(kernel), float(eps), float(screening), _ptr(w_out), stream)
+    return _raise(None, rc)
