@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0, help="0 plain, 1 screened (lambda 10)")
     ap.add_argument("--depth", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--one-step", action="store_true",
+                    help="run one iteration of the workload and exit (for profiler captures)")
     return ap.parse_args()
 
 
@@ -69,6 +72,17 @@ def workload(args):
     W["kernel"] = args.kernel
     W["lambda"] = 10.0 if args.kernel == 1 else 0.0
     return W
+
+
+def profiled_traffic(kernel_file):
+    """dram bytes per launch recorded in a committed ncu summary (or None)."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", kernel_file)):
+            if line.startswith("dram_bytes_per_launch:"):
+                return int(line.split(":")[1])
+    except OSError:
+        pass
+    return None
 
 
 def measured_peaks():
@@ -214,8 +228,10 @@ def run_ours(args, rank, world, local):
     achieved = work / (kms[dom] / 1e3)
     peak = lanes / ops
     iter_ms = sum(kms.values())
+    traffic = profiled_traffic("eval_corners_torus100k.md") if (
+        dom == "eval_corners" and W["kernel"] == 0 and W["depth"] == 8) else None
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
-            "unit": "Ginteractions/s", "frac": achieved / peak, "traffic": None,
+            "unit": "Ginteractions/s", "frac": achieved / peak, "traffic": traffic,
             "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {fmax/1e6:.0f} MHz"
                           f" / {ops} FP32 ops per interaction",
             "kernel_ms": {k: round(v, 4) for k, v in kms.items()},
@@ -288,9 +304,28 @@ def cpu_baseline(W, nc_hint, budget_s=12.0):
             "extrapolated_s_per_iteration": it_s, "corners": int(len(C))}
 
 
+def one_step(args):
+    """One iteration of the workload: the launch shapes of a bench step."""
+    import torch
+    from paper_2405_13839_gb300 import dwg
+    W = workload(args)
+    h = dwg.dwg_create(W["points"])
+    dwg.dwg_set_weights(h, W["weights"])
+    dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lambda"], W["max_iters"], W["tol"])
+    dwg.dwg_set_update(h, W["depth"], 10, dwg.DWG_UPDATE_LEVELSET)
+    dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
+    iso, stat = dwg.dwg_step(h)
+    torch.cuda.synchronize()
+    dwg.dwg_destroy(h)
+    print(json.dumps({"one_step": W["name"], "iso": iso, "stat": stat}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.one_step:
+        one_step(args)
+        return
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -330,7 +365,7 @@ def main():
     W = r["W"]
     n = len(W["points"])
     cpu = None
-    if world == 1:
+    if world == 1 and not args.no_cpu:
         try:
             cpu = cpu_baseline(W, r["nc"])
         except Exception as e:  # the oracle is a reported baseline only

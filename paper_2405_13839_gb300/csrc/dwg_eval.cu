@@ -425,17 +425,48 @@ static int num_sms(int dev)
     return cached[dev];
 }
 
-// Split the sources into chunks so that the grid covers every SM several
-// times over; each chunk keeps at least 8 tiles.
-static int pick_chunks(int64_t qtiles, int64_t ntiles_src, int sms)
+// Split the sources into chunks so that the grid fills the GPU in whole
+// waves: with `slots` resident CTAs, a grid of qtiles * ch CTAs of
+// ceil(ntiles / ch) tiles each takes ceil(qtiles * ch / slots) waves; pick
+// the chunk count with the smallest waves * tiles-per-chunk (fewest chunks
+// on ties), each chunk keeping at least 8 tiles.
+static int pick_chunks(int64_t qtiles, int64_t ntiles_src, int slots)
 {
-    int64_t target = (int64_t)sms * 8;
-    int64_t ch = ceil_div(target, qtiles > 0 ? qtiles : 1);
+    if (qtiles < 1) qtiles = 1;
+    if (slots < 1) slots = 1;
     int64_t maxch = ntiles_src / 8;
     if (maxch < 1) maxch = 1;
-    if (ch > maxch) ch = maxch;
-    if (ch < 1) ch = 1;
-    return (int)ch;
+    if (maxch > 64) maxch = 64;
+    int best = 1;
+    int64_t best_cost = INT64_MAX;
+    for (int64_t ch = 1; ch <= maxch; ++ch) {
+        int64_t tpc = ceil_div(ntiles_src, ch);
+        int64_t waves = ceil_div(qtiles * ch, slots);
+        int64_t cost = waves * tpc;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = (int)ch;
+        }
+    }
+    return best;
+}
+
+template <int P, bool GRAD, bool SCREENED>
+static int resident_slots(int dev)
+{
+    static int cached[64] = {0};
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gwn<P, GRAD, SCREENED>,
+                                                          kEvalThreads, 0) != cudaSuccess ||
+            nb < 1) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        cached[dev] = nb * num_sms(dev);
+    }
+    return cached[dev];
 }
 
 template <int P, bool GRAD>
@@ -463,7 +494,12 @@ constexpr int kPW = 4;      // query pairs per thread, w-only kernel
 int eval_chunks(const Ctx *c, int64_t m, bool grad)
 {
     int QB = kEvalThreads * 2 * (grad ? kPGrad : kPW);
-    return pick_chunks(ceil_div(m, QB), c->npad / kSrcTile, num_sms(c->device));
+    bool scr = c->kernel == DWG_KERNEL_SCREENED && c->lambda > 0.f;
+    int slots = grad ? (scr ? resident_slots<kPGrad, true, true>(c->device)
+                            : resident_slots<kPGrad, true, false>(c->device))
+                     : (scr ? resident_slots<kPW, false, true>(c->device)
+                            : resident_slots<kPW, false, false>(c->device));
+    return pick_chunks(ceil_div(m, QB), c->npad / kSrcTile, slots);
 }
 
 int eval_launch(Ctx *c, const float4 *q, int64_t m, bool grad, int nchunks, float *part,
@@ -619,7 +655,8 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
 // ---------------------------------------------------------------------------
 int gwn_w_chunks_raw(int64_t m, int64_t npad, int device)
 {
-    return pick_chunks(ceil_div(m, kEvalThreads * 2 * kPW), npad / kSrcTile, num_sms(device));
+    return pick_chunks(ceil_div(m, kEvalThreads * 2 * kPW), npad / kSrcTile,
+                       resident_slots<kPW, false, false>(device));
 }
 
 cudaError_t launch_gwn_w_raw(const float *src, int64_t npad, const float4 *q, int64_t m,

@@ -182,27 +182,68 @@ __device__ __forceinline__ float pt_d2(float4 p, F3 q)
 struct KnnTree {
     const float4 *p4;
     const int64_t *perm;
+    const uint64_t *codes;  // sorted 63-bit Morton codes of the points
     int64_t n;
     const float4 *lo, *hi;
     int levels;
+    double cube_lo[3];
+    double inv_h21;
 };
 
-// (d, o) strictly before (e, p): smaller distance, ties to the smaller input index
-__device__ __forceinline__ bool before(float d, int64_t o, float e, int64_t p)
+// Candidate order: squared float32 distance, ties to the smaller input index,
+// as one 64-bit key (the bits of a non-negative float order like the float).
+__device__ __forceinline__ uint64_t knn_key(float d, int64_t o)
 {
-    return d < e || (d == e && o < p);
+    return ((uint64_t)__float_as_uint(d) << 32) | (uint64_t)(uint32_t)o;
 }
 
-template <int KMAX>
-__device__ __forceinline__ int knn_search(const KnnTree &T, F3 q, int k, int *bj, int *err)
+template <int KMAX, bool FIXED>
+__device__ __forceinline__ void knn_insert(uint64_t key, int j, int k, uint64_t *best, int *bj)
 {
-    float bd[KMAX];
-    int64_t bo[KMAX];
+#pragma unroll
+    for (int t = KMAX - 1; t >= 0; --t) {
+        if (!FIXED && t >= k) continue;
+        bool prev = t > 0 && key < best[t > 0 ? t - 1 : 0];
+        bool cur = key < best[t];
+        if (prev) {
+            best[t] = best[t - 1];
+            bj[t] = bj[t - 1];
+        } else if (cur) {
+            best[t] = key;
+            bj[t] = j;
+        }
+    }
+}
+
+// Exact k nearest points of q.  KMAX is the array size; with FIXED the
+// runtime k equals KMAX and every index is a compile-time constant (the
+// arrays stay in registers).  The list is seeded with the points next to q's
+// Morton code in the sorted order, which bounds the search ball before the
+// depth-first descent (nearer child first) prunes the bucket tree.
+template <int KMAX, bool FIXED>
+__device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *bj, int *err)
+{
+    uint64_t best[KMAX];
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) {
-        bd[t] = INFINITY;
-        bo[t] = INT64_MAX;
+        best[t] = ~0ull;
         bj[t] = -1;
+    }
+    const int kk = FIXED ? KMAX : k;
+    // seed: the sorted neighbours of q's position on the Morton curve
+    uint64_t code = morton3((uint64_t)quant21(q.x, T.cube_lo[0], T.inv_h21),
+                            (uint64_t)quant21(q.y, T.cube_lo[1], T.inv_h21),
+                            (uint64_t)quant21(q.z, T.cube_lo[2], T.inv_h21));
+    int64_t lo = 0, hi = T.n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(&T.codes[mid]) < code) lo = mid + 1; else hi = mid;
+    }
+    const int64_t s0 = max((int64_t)0, lo - kk), s1 = min(T.n, lo + kk);
+    for (int64_t j = s0; j < s1; ++j) {
+        float d = pt_d2(__ldg(&T.p4[j]), q);
+        uint64_t key = knn_key(d, __ldg(&T.perm[j]));
+        if (key < best[kk - 1]) knn_insert<KMAX, FIXED>(key, (int)j, k, best, bj);
     }
     const int64_t nleaf = (int64_t)1 << T.levels;
     int stack[64];
@@ -210,57 +251,39 @@ __device__ __forceinline__ int knn_search(const KnnTree &T, F3 q, int k, int *bj
     stack[sp++] = 1;
     while (sp > 0) {
         int node = stack[--sp];
-        float worst = bd[k - 1];
-        if (box_d2(T.lo[node], T.hi[node], q) > worst) continue;
+        const float worst = best[kk - 1] == ~0ull ? INFINITY : __uint_as_float((uint32_t)(best[kk - 1] >> 32));
+        if (box_d2(__ldg(&T.lo[node]), __ldg(&T.hi[node]), q) > worst) continue;
         if (node >= nleaf) {
             int64_t j0 = (int64_t)(node - nleaf) * kBucket;
             int64_t j1 = min(j0 + kBucket, T.n);
             for (int64_t j = j0; j < j1; ++j) {
-                float d = pt_d2(T.p4[j], q);
-                int64_t o = T.perm[j];
-                if (!before(d, o, bd[k - 1], bo[k - 1])) continue;
-#pragma unroll
-                for (int t = KMAX - 1; t >= 0; --t) {
-                    if (t >= k) continue;
-                    bool prev = t > 0 && before(d, o, bd[t > 0 ? t - 1 : 0], bo[t > 0 ? t - 1 : 0]);
-                    bool cur = before(d, o, bd[t], bo[t]);
-                    if (prev) {
-                        bd[t] = bd[t - 1];
-                        bo[t] = bo[t - 1];
-                        bj[t] = bj[t - 1];
-                    } else if (cur) {
-                        bd[t] = d;
-                        bo[t] = o;
-                        bj[t] = (int)j;
-                    }
-                }
+                if (j >= s0 && j < s1) continue;  // already seeded
+                float d = pt_d2(__ldg(&T.p4[j]), q);
+                if (d > worst) continue;
+                uint64_t key = knn_key(d, __ldg(&T.perm[j]));
+                if (key < best[kk - 1]) knn_insert<KMAX, FIXED>(key, (int)j, k, best, bj);
             }
         } else {
             int a = 2 * node, b = 2 * node + 1;
-            float da = box_d2(T.lo[a], T.hi[a], q), db = box_d2(T.lo[b], T.hi[b], q);
-            float worst2 = bd[k - 1];
+            float da = box_d2(__ldg(&T.lo[a]), __ldg(&T.hi[a]), q);
+            float db = box_d2(__ldg(&T.lo[b]), __ldg(&T.hi[b]), q);
             if (sp + 2 > 64) {
                 atomicOr(err, kErrStack);
                 break;
             }
             // push the farther child first so that the nearer one is visited first
             if (da <= db) {
-                if (db <= worst2) stack[sp++] = b;
-                if (da <= worst2) stack[sp++] = a;
+                if (db <= worst) stack[sp++] = b;
+                if (da <= worst) stack[sp++] = a;
             } else {
-                if (da <= worst2) stack[sp++] = a;
-                if (db <= worst2) stack[sp++] = b;
+                if (da <= worst) stack[sp++] = a;
+                if (db <= worst) stack[sp++] = b;
             }
         }
     }
-    int found = 0;
-#pragma unroll
-    for (int t = 0; t < KMAX; ++t)
-        if (t < k && bj[t] >= 0) ++found;
-    return found;
 }
 
-template <int KMAX>
+template <int KMAX, bool FIXED>
 __global__ void __launch_bounds__(128)
     k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
                   KnnTree T, int k, double scale, unsigned long long *acc, int *err)
@@ -270,7 +293,7 @@ __global__ void __launch_bounds__(128)
     if (f >= nf) return;
     float4 A = faces[2 * f], C = faces[2 * f + 1];
     int bj[KMAX];
-    knn_search<KMAX>(T, F3{C.x, C.y, C.z}, k, bj, err);
+    knn_search<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, bj, err);
     long long vx = llrint((double)A.x * scale);
     long long vy = llrint((double)A.y * scale);
     long long vz = llrint((double)A.z * scale);
@@ -284,7 +307,7 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-template <int KMAX>
+template <int KMAX, bool FIXED>
 __global__ void k_knn_query(const float4 *__restrict__ q, int64_t m, KnnTree T, int k,
                             int64_t *idx_out, int *err)
 {
@@ -292,7 +315,7 @@ __global__ void k_knn_query(const float4 *__restrict__ q, int64_t m, KnnTree T, 
     if (i >= m) return;
     float4 v = q[i];
     int bj[KMAX];
-    knn_search<KMAX>(T, F3{v.x, v.y, v.z}, k, bj, err);
+    knn_search<KMAX, FIXED>(T, F3{v.x, v.y, v.z}, k, bj, err);
     for (int t = 0; t < k; ++t) idx_out[i * k + t] = bj[t] >= 0 ? T.perm[bj[t]] : -1;
 }
 
@@ -531,6 +554,9 @@ static KnnTree knn_tree(const Ctx *c)
     T.lo = c->d_bvh_lo;
     T.hi = c->d_bvh_hi;
     T.levels = c->knn_levels;
+    T.codes = c->d_codes;
+    for (int k = 0; k < 3; ++k) T.cube_lo[k] = c->cube_lo[k];
+    T.inv_h21 = (double)(1 << kMortonBits) / c->cube_L;
     return T;
 }
 
@@ -553,12 +579,12 @@ cudaError_t launch_knn_scatter(Ctx *c)
     // one thread per possible face; threads past the emitted count exit
     unsigned blocks = (unsigned)ceil_div(c->max_faces, 128);
     KnnTree T = knn_tree(c);
-    if (c->knn <= 10)
-        k_knn_scatter<10><<<blocks, 128, 0, c->stream>>>(c->d_faces, c->d_state, c->max_faces, T,
-                                                         c->knn, c->acc_scale, c->d_acc, c->d_err);
+    if (c->knn == 10)
+        k_knn_scatter<10, true><<<blocks, 128, 0, c->stream>>>(
+            c->d_faces, c->d_state, c->max_faces, T, c->knn, c->acc_scale, c->d_acc, c->d_err);
     else
-        k_knn_scatter<32><<<blocks, 128, 0, c->stream>>>(c->d_faces, c->d_state, c->max_faces, T,
-                                                         c->knn, c->acc_scale, c->d_acc, c->d_err);
+        k_knn_scatter<32, false><<<blocks, 128, 0, c->stream>>>(
+            c->d_faces, c->d_state, c->max_faces, T, c->knn, c->acc_scale, c->d_acc, c->d_err);
     return cudaGetLastError();
 }
 
@@ -566,10 +592,10 @@ cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t 
 {
     KnnTree T = knn_tree(c);
     unsigned blocks = (unsigned)ceil_div(m, 128);
-    if (k <= 10)
-        k_knn_query<10><<<blocks, 128, 0, c->stream>>>(q, m, T, k, idx_out, c->d_err);
+    if (k == 10)
+        k_knn_query<10, true><<<blocks, 128, 0, c->stream>>>(q, m, T, k, idx_out, c->d_err);
     else
-        k_knn_query<32><<<blocks, 128, 0, c->stream>>>(q, m, T, k, idx_out, c->d_err);
+        k_knn_query<32, false><<<blocks, 128, 0, c->stream>>>(q, m, T, k, idx_out, c->d_err);
     return cudaGetLastError();
 }
 
