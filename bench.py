@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", type=int, default=0, help="0 plain, 1 screened (lambda 10)")
-    ap.add_argument("--depth", type=int, default=8)
+    ap.add_argument("--depth", type=int, default=None)
+    ap.add_argument("--workload", default="torus-100k", choices=["torus-100k", "metaballs-1m"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--one-step", action="store_true",
@@ -67,8 +68,15 @@ def dist_env():
 
 
 def workload(args):
-    W = synth.workload_torus100k()
-    W["depth"] = args.depth
+    if args.workload == "metaballs-1m":
+        W = synth.workload_metaballs1m()
+        W["path"] = 2     # Barnes-Hut
+    else:
+        W = synth.workload_torus100k()
+        W["path"] = 1     # exact all-pairs
+        W["theta"] = 0.5
+    if args.depth:
+        W["depth"] = args.depth
     W["kernel"] = args.kernel
     W["lambda"] = 10.0 if args.kernel == 1 else 0.0
     return W
@@ -160,6 +168,7 @@ def run_ours(args, rank, world, local):
     dwg.dwg_set_weights(h, a_dev)
     dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lambda"], W["max_iters"], W["tol"])
     dwg.dwg_set_update(h, W["depth"], 10, dwg.DWG_UPDATE_LEVELSET)
+    dwg.dwg_set_tree(h, W["path"], W["theta"])
     dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
     out = torch.empty((n, 3), dtype=torch.float32, device=dev)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -252,6 +261,7 @@ def run_ours(args, rank, world, local):
             dwg.dwg_set_weights(h2, ah)
             dwg.dwg_set_params(h2, W["kernel"], W["eps"], W["lambda"], W["max_iters"], W["tol"])
             dwg.dwg_set_update(h2, W["depth"], 10, dwg.DWG_UPDATE_LEVELSET)
+            dwg.dwg_set_tree(h2, W["path"], W["theta"])
             dwg.dwg_set_init(h2, dwg.DWG_INIT_RANDOM, 1)
             dwg.dwg_orient(h2, oh)
             e2e_inter += dwg.dwg_get_stats(h2)["interactions"]
@@ -313,6 +323,7 @@ def one_step(args):
     dwg.dwg_set_weights(h, W["weights"])
     dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lambda"], W["max_iters"], W["tol"])
     dwg.dwg_set_update(h, W["depth"], 10, dwg.DWG_UPDATE_LEVELSET)
+    dwg.dwg_set_tree(h, W["path"], W["theta"])
     dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
     iso, stat = dwg.dwg_step(h)
     torch.cuda.synchronize()

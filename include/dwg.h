@@ -64,6 +64,12 @@ extern "C" {
 #define DWG_INIT_RANDOM 0
 #define DWG_INIT_GIVEN 1
 
+/* Evaluation path: exact all-pairs sums, or the Barnes-Hut far field of
+ * Sec. 5.2; AUTO takes all-pairs up to 262,144 points and the tree above. */
+#define DWG_PATH_AUTO 0
+#define DWG_PATH_ALLPAIRS 1
+#define DWG_PATH_TREE 2
+
 typedef struct dwg_ctx *dwg_handle;
 
 /*
@@ -112,6 +118,18 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
  *   mode:  DWG_UPDATE_LEVELSET or DWG_UPDATE_DIRECT.
  */
 int dwg_set_update(dwg_handle h, int depth, int knn, int mode);
+
+/*
+ * Evaluation path and opening angle (Sec. 5.2 "Octree Traversal").
+ *   path:  DWG_PATH_AUTO, DWG_PATH_ALLPAIRS or DWG_PATH_TREE.
+ *   theta: opening angle in (0, 1]: a node of area-weighted centre c and
+ *          radius r stands for its points as one dipole (its area-weighted
+ *          normal sum at c) for a query q with |q - c| > r / theta, else it
+ *          opens; leaves (16 Morton-consecutive points) are summed exactly.
+ *          The paper opens when |q - c| <= 2.3 r, i.e. theta = 1 / 2.3.
+ * Default: AUTO, theta = 0.5.
+ */
+int dwg_set_tree(dwg_handle h, int path, float theta);
 
 /* Area weights a_i > 0 (float32, n, input order, host or device). */
 int dwg_set_weights(dwg_handle h, const float *a);
@@ -173,6 +191,7 @@ typedef struct {
     double stat_last;        /* convergence statistic of the last iteration */
     double interactions;     /* kernel evaluations of the last dwg_orient */
     double ms_orient;        /* device time of the last dwg_orient */
+    double interactions_eval; /* kernel evaluations of the last dwg_eval_gwn */
 } dwg_stats;
 
 int dwg_get_stats(dwg_handle h, dwg_stats *out);

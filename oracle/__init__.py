@@ -84,6 +84,10 @@ def _load():
             lib.dwgo_orient.argtypes = [i64, P, P, P, ctypes.POINTER(_Params), P,
                                         ctypes.POINTER(ctypes.c_int), P, P]
             lib.dwgo_orient.restype = ctypes.c_int
+            lib.dwgo_morton_order.argtypes = [i64, P, P]
+            lib.dwgo_tree_gwn.argtypes = [i64, P, P, P, i64, P, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P,
+                                          P, P]
             _lib = lib
     return _lib
 
@@ -235,3 +239,39 @@ def orient(points, weights, n0, prm):
     k = it.value
     return dict(normals=out, iters=k, converged=bool(conv), iso=ti[:k].copy(),
                 stat=ts[:k].copy())
+
+
+def morton_order(points):
+    """Input indices in Morton order of the root cube (21 bits per axis)."""
+    lib = _load()
+    p = _d(points, 3)
+    out = np.zeros(len(p), dtype=np.int64)
+    lib.dwgo_morton_order(len(p), _ptr(p), _ptr(out))
+    return out
+
+
+def tree_gwn(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0.0, lam=0.0,
+             beta=2.0, bucket=16, grad=True, want_count=False, want_bound=False):
+    """Barnes-Hut w (and grad w) at queries (Sec. 5.2); optional per-query
+    evaluation counts and first-order error bounds."""
+    lib = _load()
+    p = _d(points, 3)
+    nn = _d(normals, 3)
+    a = _d(weights).ravel()
+    q = _d(queries, 3)
+    w = np.zeros(len(q))
+    g = np.zeros((len(q), 3)) if grad else None
+    cnt = np.zeros(len(q)) if want_count else None
+    bnd = np.zeros(len(q)) if want_bound else None
+    lib.dwgo_tree_gwn(len(p), _ptr(p), _ptr(nn), _ptr(a), len(q), _ptr(q), int(kernel),
+                      float(eps), float(lam), float(beta), int(bucket), _ptr(w),
+                      _ptr(g) if grad else None, _ptr(cnt) if want_count else None,
+                      _ptr(bnd) if want_bound else None)
+    out = [w]
+    if grad:
+        out.append(g)
+    if want_count:
+        out.append(cnt)
+    if want_bound:
+        out.append(bnd)
+    return tuple(out) if len(out) > 1 else w

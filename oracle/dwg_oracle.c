@@ -627,3 +627,245 @@ int dwgo_orient(int64_t n, const double *p, const double *a, const double *n0,
     free(wp); free(dth); free(nxt); free(cur);
     return conv;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Barnes-Hut far field (Sec. 5.2 "Octree Traversal")                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The hierarchy: the input points sorted along the Morton curve of the root
+ * cube (21 bits per axis, stable, ties in input order), cut into buckets of
+ * `bucket` consecutive points; a complete binary tree over the buckets (heap
+ * order: node 1 is the root, node k has children 2k and 2k+1, the 2^L leaves
+ * are the buckets, the last ones possibly empty).  Each node is a contiguous
+ * Morton range, like an octree node refined at bucket granularity.
+ *
+ * Node data, all sums in double, leaves summed sequentially in sorted order
+ * and internal nodes as (left + right):
+ *   A = sum a_i,  c = sum a_i p_i / A  ("mass center", area weighted),
+ *   r = max |p_i - c| over a leaf's points, and for an internal node
+ *       max over its non-empty children of |c_child - c| + r_child (an upper
+ *       bound of the largest distance, so the opening test is conservative),
+ *   M = sum a_i n_i  (the node's area-weighted normal, Sec. 5.2).
+ * A query q uses node as one dipole at c with moment M when it is far:
+ *   |q - c|^2 > (beta r)^2, evaluated in float32 as
+ *   dx = q - c_f (each axis), d2 = fma(dz, dz, fma(dy, dy, dx * dx)),
+ *   far iff d2 > br2_f, with c_f = (float)c and br2_f = (float)((beta r)^2);
+ * otherwise it descends, and a leaf's points are summed exactly.  beta is the
+ * inverse opening angle (Sec. 5.2 uses 2.3).
+ */
+typedef struct {
+    int L;               /* leaves = 2^L */
+    int64_t nleaf, n;
+    int bucket;
+    int64_t *order;      /* sorted index -> input index */
+    double *A, *c, *r;   /* per node */
+    double *M;           /* per node, 3 */
+    float *cf, *br2;     /* per node */
+} bh_tree;
+
+typedef struct { uint64_t key; int64_t idx; } key_idx;
+
+static int cmp_key_idx(const void *a, const void *b)
+{
+    const key_idx *x = (const key_idx *)a, *y = (const key_idx *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+static uint64_t spread21(uint64_t v)
+{
+    uint64_t out = 0;
+    for (int b = 0; b < 21; ++b) out |= ((v >> b) & 1ull) << (3 * b);
+    return out;
+}
+
+/* Morton order of the points in the root cube (21 bits per axis) */
+void dwgo_morton_order(int64_t n, const double *p, int64_t *order)
+{
+    double cube[6];
+    dwgo_cube(n, p, 21, cube);
+    key_idx *ki = (key_idx *)malloc(sizeof(key_idx) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t cx = (uint64_t)cell_of(p[3 * i + 0], cube[0], cube[5], 21);
+        uint64_t cy = (uint64_t)cell_of(p[3 * i + 1], cube[1], cube[5], 21);
+        uint64_t cz = (uint64_t)cell_of(p[3 * i + 2], cube[2], cube[5], 21);
+        ki[i].key = spread21(cx) | (spread21(cy) << 1) | (spread21(cz) << 2);
+        ki[i].idx = i;
+    }
+    qsort(ki, (size_t)n, sizeof(key_idx), cmp_key_idx);
+    for (int64_t i = 0; i < n; ++i) order[i] = ki[i].idx;
+    free(ki);
+}
+
+static void bh_build(bh_tree *T, int64_t n, const double *p, const double *nrm, const double *a,
+                     int bucket, double beta)
+{
+    T->n = n;
+    T->bucket = bucket;
+    int64_t nb = (n + bucket - 1) / bucket;
+    int L = 0;
+    while (((int64_t)1 << L) < nb) ++L;
+    T->L = L;
+    T->nleaf = (int64_t)1 << L;
+    int64_t nn = 2 * T->nleaf;
+    T->order = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    dwgo_morton_order(n, p, T->order);
+    T->A = (double *)calloc((size_t)nn, sizeof(double));
+    T->c = (double *)calloc(3 * (size_t)nn, sizeof(double));
+    T->r = (double *)calloc((size_t)nn, sizeof(double));
+    T->M = (double *)calloc(3 * (size_t)nn, sizeof(double));
+    T->cf = (float *)calloc(3 * (size_t)nn, sizeof(float));
+    T->br2 = (float *)calloc((size_t)nn, sizeof(float));
+    double *Sp = (double *)calloc(3 * (size_t)nn, sizeof(double));
+    /* leaves */
+    for (int64_t b = 0; b < T->nleaf; ++b) {
+        int64_t node = T->nleaf + b, j0 = b * bucket, j1 = j0 + bucket < n ? j0 + bucket : n;
+        double sa = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+        for (int64_t j = j0; j < j1; ++j) {
+            int64_t i = T->order[j];
+            sa = sa + a[i];
+            sx = sx + a[i] * p[3 * i]; sy = sy + a[i] * p[3 * i + 1]; sz = sz + a[i] * p[3 * i + 2];
+            mx = mx + a[i] * nrm[3 * i]; my = my + a[i] * nrm[3 * i + 1]; mz = mz + a[i] * nrm[3 * i + 2];
+        }
+        T->A[node] = sa;
+        Sp[3 * node] = sx; Sp[3 * node + 1] = sy; Sp[3 * node + 2] = sz;
+        T->M[3 * node] = mx; T->M[3 * node + 1] = my; T->M[3 * node + 2] = mz;
+    }
+    for (int64_t node = T->nleaf - 1; node >= 1; --node) {
+        int64_t l = 2 * node, rr = 2 * node + 1;
+        T->A[node] = T->A[l] + T->A[rr];
+        for (int k = 0; k < 3; ++k) {
+            Sp[3 * node + k] = Sp[3 * l + k] + Sp[3 * rr + k];
+            T->M[3 * node + k] = T->M[3 * l + k] + T->M[3 * rr + k];
+        }
+    }
+    for (int64_t node = 1; node < nn; ++node)
+        if (T->A[node] > 0.0)
+            for (int k = 0; k < 3; ++k) T->c[3 * node + k] = Sp[3 * node + k] / T->A[node];
+    /* radii: leaves exact, internal nodes bounded through the children */
+    for (int64_t b = 0; b < T->nleaf; ++b) {
+        int64_t node = T->nleaf + b, j0 = b * bucket, j1 = j0 + bucket < n ? j0 + bucket : n;
+        double rm = 0.0;
+        for (int64_t j = j0; j < j1; ++j) {
+            int64_t i = T->order[j];
+            double dx = p[3 * i] - T->c[3 * node], dy = p[3 * i + 1] - T->c[3 * node + 1],
+                   dz = p[3 * i + 2] - T->c[3 * node + 2];
+            double d = sqrt(dx * dx + dy * dy + dz * dz);
+            if (d > rm) rm = d;
+        }
+        T->r[node] = rm;
+    }
+    for (int64_t node = T->nleaf - 1; node >= 1; --node) {
+        double rm = 0.0;
+        for (int64_t ch = 2 * node; ch <= 2 * node + 1; ++ch) {
+            if (!(T->A[ch] > 0.0)) continue;
+            double dx = T->c[3 * ch] - T->c[3 * node], dy = T->c[3 * ch + 1] - T->c[3 * node + 1],
+                   dz = T->c[3 * ch + 2] - T->c[3 * node + 2];
+            double d = sqrt(dx * dx + dy * dy + dz * dz) + T->r[ch];
+            if (d > rm) rm = d;
+        }
+        T->r[node] = rm;
+    }
+    for (int64_t node = 1; node < nn; ++node) {
+        for (int k = 0; k < 3; ++k) T->cf[3 * node + k] = (float)T->c[3 * node + k];
+        double br = beta * T->r[node];
+        T->br2[node] = (float)(br * br);
+    }
+    free(Sp);
+}
+
+static void bh_free(bh_tree *T)
+{
+    free(T->order); free(T->A); free(T->c); free(T->r); free(T->M); free(T->cf); free(T->br2);
+}
+
+/* far-field term of a node: a dipole of moment M at c_f (float-rounded
+ * position and moment M / (4 pi) rounded to float, as the library stores
+ * them), kernel evaluated in double */
+static void dipole_term(const float *cf, const double *M, const double *q, int screened, double eps,
+                        double s, double *t, double g[3])
+{
+    double pc[3] = {(double)cf[0], (double)cf[1], (double)cf[2]};
+    double m[3], one[3];
+    for (int k = 0; k < 3; ++k) m[k] = (double)(float)(M[k] / (4.0 * DWGO_PI));
+    /* term() builds m = a n / (4 pi); pass a = 4 pi and n = m so that it
+     * rebuilds exactly m up to one rounding of (4 pi m) / (4 pi) */
+    double nrm_len = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    if (nrm_len == 0.0) { *t = 0.0; g[0] = g[1] = g[2] = 0.0; return; }
+    for (int k = 0; k < 3; ++k) one[k] = m[k] / nrm_len;
+    term(pc, one, nrm_len * 4.0 * DWGO_PI, q, screened, eps, s, t, g);
+}
+
+static int far_test(const bh_tree *T, int64_t node, const double *q)
+{
+    float qx = (float)q[0], qy = (float)q[1], qz = (float)q[2];
+    float dx = qx - T->cf[3 * node], dy = qy - T->cf[3 * node + 1], dz = qz - T->cf[3 * node + 2];
+    float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    return d2 > T->br2[node];
+}
+
+static void bh_query(const bh_tree *T, int64_t node, const double *p, const double *nrm,
+                     const double *a, const double *q, int screened, double eps, double s,
+                     double *w, double g[3], double *count, double *bound)
+{
+    if (!(T->A[node] > 0.0)) return; /* empty */
+    if (far_test(T, node, q)) {
+        double t, gt[3];
+        dipole_term(T->cf + 3 * node, T->M + 3 * node, q, screened, eps, s, &t, gt);
+        *w += t;
+        g[0] += gt[0]; g[1] += gt[1]; g[2] += gt[2];
+        *count += 1.0;
+        if (bound) {
+            double dx = q[0] - T->c[3 * node], dy = q[1] - T->c[3 * node + 1],
+                   dz = q[2] - T->c[3 * node + 2];
+            double d = sqrt(dx * dx + dy * dy + dz * dz) - T->r[node];
+            *bound += T->A[node] * T->r[node] / (2.0 * DWGO_PI * d * d * d);
+        }
+        return;
+    }
+    if (node >= T->nleaf) {
+        int64_t b = node - T->nleaf, j0 = b * T->bucket;
+        int64_t j1 = j0 + T->bucket < T->n ? j0 + T->bucket : T->n;
+        for (int64_t j = j0; j < j1; ++j) {
+            int64_t i = T->order[j];
+            const double *pi = p + 3 * i;
+            if (pi[0] == q[0] && pi[1] == q[1] && pi[2] == q[2]) continue;
+            double t, gt[3];
+            term(pi, nrm + 3 * i, a[i], q, screened, eps, s, &t, gt);
+            *w += t;
+            g[0] += gt[0]; g[1] += gt[1]; g[2] += gt[2];
+            *count += 1.0;
+        }
+        return;
+    }
+    bh_query(T, 2 * node, p, nrm, a, q, screened, eps, s, w, g, count, bound);
+    bh_query(T, 2 * node + 1, p, nrm, a, q, screened, eps, s, w, g, count, bound);
+}
+
+/*
+ * Barnes-Hut w and grad w at m queries (Sec. 5.2) with buckets of `bucket`
+ * points and opening factor beta = 1 / theta.  count (m, may be NULL):
+ * kernel evaluations per query (points plus far nodes).  bound (m, may be
+ * NULL): sum over far nodes of A r / (2 pi (|q - c| - r)^3), a bound of the
+ * plain kernel's first-order far-field error for eps -> 0.
+ */
+void dwgo_tree_gwn(int64_t n, const double *p, const double *nrm, const double *a, int64_t m,
+                   const double *q, int kernel, double eps, double lambda, double beta,
+                   int bucket, double *w, double *g, double *count, double *bound)
+{
+    bh_tree T;
+    bh_build(&T, n, p, nrm, a, bucket, beta);
+    double s = sqrt(lambda > 0 ? lambda : 0.0);
+    int screened = (kernel == 1);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < m; ++i) {
+        double wi = 0.0, gi[3] = {0, 0, 0}, ci = 0.0, bi = 0.0;
+        bh_query(&T, 1, p, nrm, a, q + 3 * i, screened, eps, s, &wi, gi, &ci, bound ? &bi : NULL);
+        w[i] = wi;
+        if (g) { g[3 * i] = gi[0]; g[3 * i + 1] = gi[1]; g[3 * i + 2] = gi[2]; }
+        if (count) count[i] = ci;
+        if (bound) bound[i] = bi;
+    }
+    bh_free(&T);
+}

@@ -30,6 +30,15 @@ void set_global_error(const std::string &msg)
 }
 }  // namespace dwg
 
+namespace dwg {
+bool use_tree(const Ctx *c)
+{
+    if (c->path == DWG_PATH_TREE) return true;
+    if (c->path == DWG_PATH_ALLPAIRS) return false;
+    return c->n > 262144;
+}
+}  // namespace dwg
+
 static int fail(Ctx *c, int code, const std::string &msg)
 {
     if (c) c->err = msg;
@@ -126,8 +135,9 @@ __global__ void k_weights_in(const float *__restrict__ a, const int64_t *__restr
     if (!(v > 0.f) || !isfinite(v)) atomicOr(err, kErrNonfinite);
     p4[i].w = v;
 }
-__global__ void k_iter_reset(IterState *st, int max_iters)
+__global__ void k_iter_reset(IterState *st, int max_iters, unsigned long long *counter)
 {
+    if (counter) *counter = 0ull;
     st->iter = 0;
     st->done = 0;
     st->max_iters = max_iters;
@@ -149,8 +159,14 @@ static unsigned nblk(int64_t n, int b = 256) { return (unsigned)ceil_div(n, b); 
 // ---------------------------------------------------------------------------
 static int ensure_iter_buffers(Ctx *c)
 {
+    const bool tree = use_tree(c);
+    if (tree) {
+        int rc = build_tree(c);
+        if (!rc) rc = tree_records(c);
+        if (rc) return rc;
+    }
     // partial sums for the point evaluation
-    c->nchunks_p = eval_chunks(c, c->n, true);
+    c->nchunks_p = tree ? 1 : eval_chunks(c, c->n, true);
     size_t need_p = (size_t)c->nchunks_p * 8 * (size_t)c->n;
     if (need_p > c->part_p_cap) {
         cudaFree(c->d_part_p);
@@ -161,7 +177,7 @@ static int ensure_iter_buffers(Ctx *c)
     if (c->mode == DWG_UPDATE_LEVELSET) {
         int rc = build_discretization(c, c->depth);
         if (rc) return rc;
-        c->nchunks_c = eval_chunks(c, c->ncorners, false);
+        c->nchunks_c = tree ? 1 : eval_chunks(c, c->ncorners, false);
         size_t need_c = (size_t)c->nchunks_c * 2 * (size_t)c->ncorners;
         if (need_c > c->part_c_cap) {
             cudaFree(c->d_part_c);
@@ -205,9 +221,16 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], c->stream);
     };
+    const bool tree = use_tree(c);
     // w and grad w at the input points
     mark(0);
-    if ((rc = eval_launch(c, c->d_p4, c->n, true, c->nchunks_p, c->d_part_p, c->n))) return rc;
+    if (tree) {
+        if (launch_tree_moments(c) != cudaSuccess ||
+            launch_tree_gwn(c, c->d_p4, c->n, true, c->d_part_p, c->n) != cudaSuccess)
+            return fail(c, DWG_ERR_CUDA, "tree launch failed");
+    } else if ((rc = eval_launch(c, c->d_p4, c->n, true, c->nchunks_p, c->d_part_p, c->n))) {
+        return rc;
+    }
     mark(1);
     if (launch_reduce_points(c, c->d_part_p, c->nchunks_p, c->n, c->d_p4, 1, true, c->d_wg,
                              c->d_wsum_blocks) != cudaSuccess)
@@ -217,9 +240,14 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
     mark(3);
     if (c->mode == DWG_UPDATE_LEVELSET) {
         // w at the octree leaf corners, level set, face gradients to the k nearest points
-        if ((rc = eval_launch(c, c->d_corner_pos, c->ncorners, false, c->nchunks_c, c->d_part_c,
-                              c->ncorners)))
+        if (tree) {
+            if (launch_tree_gwn(c, c->d_corner_pos, c->ncorners, false, c->d_part_c, c->ncorners) !=
+                cudaSuccess)
+                return fail(c, DWG_ERR_CUDA, "tree launch failed");
+        } else if ((rc = eval_launch(c, c->d_corner_pos, c->ncorners, false, c->nchunks_c,
+                                     c->d_part_c, c->ncorners))) {
             return rc;
+        }
         mark(4);
         if (launch_reduce_w(c, c->d_part_c, c->nchunks_c, c->ncorners, c->d_wc) != cudaSuccess)
             return fail(c, DWG_ERR_CUDA, "reduce_w launch failed");
@@ -330,6 +358,7 @@ static int prepare_normals(Ctx *c)
 
 static double interactions_per_iter(const Ctx *c)
 {
+    // (the tree path counts its evaluations on the device instead)
     double n = (double)c->n;
     double it = n * n;
     if (c->mode == DWG_UPDATE_LEVELSET) it += (double)c->ncorners * n;
@@ -358,7 +387,9 @@ void dwg_destroy(dwg_handle h)
                     h->d_dtheta, h->d_wg, h->d_bvh_lo, h->d_bvh_hi, h->d_leaves,
                     h->d_leaf_corners, h->d_corner_keys, h->d_corner_pos, h->d_wc, h->d_faces,
                     h->d_acc, h->d_part_p, h->d_part_c, h->d_wsum_blocks, h->d_dn_blocks,
-                    h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err};
+                    h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err,
+                    h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
+                    h->d_tree_mrec, h->d_counter};
     for (void *p : bufs) cudaFree(p);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -431,6 +462,8 @@ static int create_impl(dwg_ctx *c, const float *points, int64_t n)
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_wsum_blocks, c->wsum_blocks * sizeof(double)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_dn_blocks, ceil_div(n, 256) * sizeof(double)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_state, sizeof(IterState)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_counter, sizeof(unsigned long long)));
+        DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         c->stats.n_points = n;
         return DWG_OK;
@@ -522,6 +555,18 @@ int dwg_set_update(dwg_handle h, int depth, int knn, int mode)
     return DWG_OK;
 }
 
+int dwg_set_tree(dwg_handle h, int path, float theta)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (path != DWG_PATH_AUTO && path != DWG_PATH_ALLPAIRS && path != DWG_PATH_TREE)
+        return fail(h, DWG_ERR_INVALID, "unknown path");
+    if (!(theta > 0.f) || !(theta <= 1.f)) return fail(h, DWG_ERR_INVALID, "theta must be in (0, 1]");
+    h->path = path;
+    h->tree_beta = 1.0f / theta;
+    invalidate_graph(h);
+    return DWG_OK;
+}
+
 int dwg_set_weights(dwg_handle h, const float *a)
 {
     if (!h || !a) return DWG_ERR_INVALID;
@@ -532,6 +577,7 @@ int dwg_set_weights(dwg_handle h, const float *a)
     if (!rc) {
         k_weights_in<<<nblk(h->n), 256, 0, h->stream>>>(d, h->d_perm, h->n, h->d_p4, h->d_err);
         rc = check_device_err(h);
+        h->tree_built = false;  // node centres depend on the weights
         if (rc == DWG_ERR_NONFINITE) h->err = "weights must be finite and > 0";
     }
     cudaFree(d);
@@ -615,7 +661,7 @@ int dwg_orient(dwg_handle h, float *normals_out, int *iters_out)
     if (rc) return rc;
     h->normals_pending = true;  // orient always starts from the initial normals
     if ((rc = prepare_normals(h))) return rc;
-    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters);
+    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters, h->d_counter);
     LAUNCH_CHECK(h);
     if (!h->graph_valid && (rc = build_graph(h))) return rc;
     cudaEvent_t e0, e1;
@@ -663,6 +709,11 @@ int dwg_orient(dwg_handle h, float *normals_out, int *iters_out)
     h->stats.n_leaves = h->nleaves;
     h->stats.n_corners = h->ncorners;
     h->stats.interactions = interactions_per_iter(h) * it;
+    if (use_tree(h)) {
+        unsigned long long cnt = 0;
+        DWG_CUDA_TRY(h, cudaMemcpy(&cnt, h->d_counter, sizeof(cnt), cudaMemcpyDeviceToHost));
+        h->stats.interactions = (double)cnt;
+    }
     h->stats.ms_orient = ms;
     if (iters_out) *iters_out = it;
     if (normals_out && (rc = dwg_get_normals(h, normals_out))) return rc;
@@ -677,7 +728,7 @@ int dwg_step(dwg_handle h, float *w_out, float *grad_out, float *dtheta_out, dou
     int rc = ensure_iter_buffers(h);
     if (rc) return rc;
     if ((rc = prepare_normals(h))) return rc;
-    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters);
+    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters, h->d_counter);
     LAUNCH_CHECK(h);
     cudaGraphConditionalHandle none = 0;
     if ((rc = enqueue_body(h, none, 0))) return rc;
@@ -711,7 +762,7 @@ int dwg_profile_step(dwg_handle h, float *ms_out, int cap, int *count)
     int rc = ensure_iter_buffers(h);
     if (rc) return rc;
     if ((rc = prepare_normals(h))) return rc;
-    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters);
+    k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters, h->d_counter);
     LAUNCH_CHECK(h);
     cudaEvent_t ev[10];
     for (int k = 0; k < 10; ++k) DWG_CUDA_TRY(h, cudaEventCreate(&ev[k]));
@@ -747,9 +798,18 @@ int dwg_eval_gwn(dwg_handle h, const float *queries, int64_t m, float *w_out, fl
         if ((rc = check_device_err(h))) return rc;
         DWG_CUDA_TRY(h, cudaMalloc(&q4, m * sizeof(float4)));
         k_xyz_to_f4<<<nblk(m), 256, 0, h->stream>>>(qx, m, q4);
-        int nch = eval_chunks(h, m, grad);
+        const bool tree = use_tree(h);
+        int nch = tree ? 1 : eval_chunks(h, m, grad);
         DWG_CUDA_TRY(h, cudaMalloc(&part, (size_t)nch * (grad ? 8 : 2) * m * sizeof(float)));
-        if ((rc = eval_launch(h, q4, m, grad, nch, part, m))) return rc;
+        if (tree) {
+            if ((rc = build_tree(h)) || (rc = tree_records(h))) return rc;
+            DWG_CUDA_TRY(h, cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), h->stream));
+            if (launch_tree_moments(h) != cudaSuccess ||
+                launch_tree_gwn(h, q4, m, grad, part, m) != cudaSuccess)
+                return fail(h, DWG_ERR_CUDA, "tree launch failed");
+        } else if ((rc = eval_launch(h, q4, m, grad, nch, part, m))) {
+            return rc;
+        }
         DWG_CUDA_TRY(h, cudaMalloc(&wg, m * sizeof(float4)));
         if (launch_reduce_points(h, part, nch, m, q4, grad ? 2 : 0, grad, wg, nullptr) !=
             cudaSuccess)
@@ -759,6 +819,14 @@ int dwg_eval_gwn(dwg_handle h, const float *queries, int64_t m, float *w_out, fl
         if ((rc = download(h, w_out, o, m * sizeof(float)))) return rc;
         if (grad && (rc = download(h, grad_out, o + m, 3 * m * sizeof(float)))) return rc;
         DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        h->stats.interactions_eval = (double)m * (double)h->n;
+        if (tree) {
+            unsigned long long cnt = 0;
+            DWG_CUDA_TRY(h, cudaMemcpyAsync(&cnt, h->d_counter, sizeof(cnt), cudaMemcpyDeviceToHost,
+                                            h->stream));
+            DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            h->stats.interactions_eval = (double)cnt;
+        }
         return check_device_err(h);
     };
     rc = body();

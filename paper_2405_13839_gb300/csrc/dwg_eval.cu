@@ -400,7 +400,7 @@ cudaError_t launch_pack_sources(const float4 *p4, const float4 *nrm, int64_t n, 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static EvalParams make_params(const Ctx *c)
+EvalParams make_eval_params(const Ctx *c)
 {
     EvalParams ep;
     ep.eps2 = c->eps * c->eps;
@@ -473,7 +473,7 @@ template <int P, bool GRAD>
 static cudaError_t launch_gwn_t(const Ctx *c, const float4 *q, int64_t m, int nchunks,
                                 float *part, int64_t stride)
 {
-    EvalParams ep = make_params(c);
+    EvalParams ep = make_eval_params(c);
     constexpr int QB = kEvalThreads * 2 * P;
     int64_t qtiles = ceil_div(m, QB);
     int64_t ntiles = c->npad / kSrcTile;
@@ -637,7 +637,7 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
     CubeQ cq;
     for (int k = 0; k < 3; ++k) cq.lo[k] = c->cube_lo[k];
     cq.inv_h21 = (double)(1 << kMortonBits) / c->cube_L;
-    EvalParams ep = make_params(c);
+    EvalParams ep = make_eval_params(c);
     unsigned blocks = (unsigned)ceil_div(m, 256);
     if (grad)
         k_reduce_points<true><<<blocks, 256, 0, c->stream>>>(part, nchunks, m, m, queries,

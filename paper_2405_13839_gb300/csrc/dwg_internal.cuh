@@ -115,6 +115,15 @@ struct Ctx {
     int trace_cap = 0;
     int *d_err = nullptr;
 
+    // Barnes-Hut far field over the bucket tree
+    int path = DWG_PATH_AUTO;
+    float tree_beta = 2.0f;            // 1 / opening angle
+    bool tree_built = false;
+    double tree_beta_set = -1.0;
+    double *d_tree_A = nullptr, *d_tree_C = nullptr, *d_tree_R = nullptr, *d_tree_M = nullptr;
+    float4 *d_tree_rec = nullptr, *d_tree_mrec = nullptr;
+    unsigned long long *d_counter = nullptr;  // kernel evaluations of the tree path
+
     // graph
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_valid = false;
@@ -195,6 +204,7 @@ int build_knn_tree(Ctx *c);
 int build_discretization(Ctx *c, int depth);
 
 // dwg_eval.cu
+EvalParams make_eval_params(const Ctx *c);
 int eval_chunks(const Ctx *c, int64_t m, bool grad);
 int eval_launch(Ctx *c, const float4 *q, int64_t m, bool grad, int nchunks, float *part,
                 int64_t stride);
@@ -214,6 +224,14 @@ cudaError_t launch_reduce_w_raw(const float *part, int nchunks, int64_t m, float
 
 // dwg_api.cu
 void set_global_error(const std::string &msg);
+bool use_tree(const Ctx *c);
+
+// dwg_tree.cu
+int build_tree(Ctx *c);
+int tree_records(Ctx *c);
+cudaError_t launch_tree_moments(Ctx *c);
+cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float *part,
+                            int64_t stride);
 
 // dwg_iter.cu
 cudaError_t launch_iso(Ctx *c);

@@ -30,6 +30,9 @@ DWG_UPDATE_LEVELSET = 0
 DWG_UPDATE_DIRECT = 1
 DWG_INIT_RANDOM = 0
 DWG_INIT_GIVEN = 1
+DWG_PATH_AUTO = 0
+DWG_PATH_ALLPAIRS = 1
+DWG_PATH_TREE = 2
 
 _NAMES = {v: k for k, v in dict(
     DWG_ERR_INVALID=-1, DWG_ERR_CUDA=-2, DWG_ERR_OOM=-3, DWG_ERR_NONFINITE=-4,
@@ -47,7 +50,8 @@ class dwg_stats(ctypes.Structure):
                 ("n_corners", ctypes.c_int64), ("iters", ctypes.c_int),
                 ("converged", ctypes.c_int), ("faces_last", ctypes.c_int64),
                 ("iso_last", ctypes.c_double), ("stat_last", ctypes.c_double),
-                ("interactions", ctypes.c_double), ("ms_orient", ctypes.c_double)]
+                ("interactions", ctypes.c_double), ("ms_orient", ctypes.c_double),
+                ("interactions_eval", ctypes.c_double)]
 
 
 def lib_path() -> str:
@@ -72,6 +76,7 @@ def _load() -> ctypes.CDLL:
         "dwg_set_params": ([H, I, F, F, I, F], I),
         "dwg_set_update": ([H, I, I, I], I),
         "dwg_set_weights": ([H, P], I),
+        "dwg_set_tree": ([H, I, F], I),
         "dwg_set_init": ([H, I, ctypes.c_uint64, P], I),
         "dwg_orient": ([H, P, ctypes.POINTER(I)], I),
         "dwg_step": ([H, P, P, P, ctypes.POINTER(ctypes.c_double),
@@ -173,6 +178,10 @@ def dwg_set_params(h, kernel, eps, screening, max_iters, tol):
 
 def dwg_set_update(h, depth, knn=10, mode=DWG_UPDATE_LEVELSET):
     return _raise(h, _lib.dwg_set_update(h, int(depth), int(knn), int(mode)))
+
+
+def dwg_set_tree(h, path, theta=0.5):
+    return _raise(h, _lib.dwg_set_tree(h, int(path), float(theta)))
 
 
 def dwg_set_weights(h, a):

@@ -1,0 +1,92 @@
+"""Barnes-Hut path of the CUDA library against the oracle's Barnes-Hut
+(Sec. 5.2): same bucket tree (bit-exact Morton order), same node data
+(double sums in the same order), same float32 opening test, so the two make
+identical far/near decisions (checked through the evaluation counts); values
+agree to the exact path's tolerances."""
+import numpy as np
+import pytest
+
+import synth
+from test_gpu_parity import check_wg, s_g, agreement
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def handle(dwglib):
+    made = []
+
+    def make(points):
+        h = dwglib.dwg_create(points)
+        made.append(h)
+        return h
+
+    yield make
+    for h in made:
+        dwglib.dwg_destroy(h)
+
+
+@pytest.mark.parametrize("n", [1, 33, 1000, 5000, 40000])
+@pytest.mark.parametrize("kernel,lam,theta", [(0, 0.0, 0.5), (0, 0.0, 1 / 2.3), (1, 10.0, 0.5)])
+def test_tree_eval_matches_oracle_tree(dwglib, oracle_mod, handle, n, kernel, lam, theta):
+    p, _ = synth.torus(n, seed=n + 3, noise=0.004)
+    a = np.full(n, 4 * np.pi ** 2 * 0.3 / n, np.float32)
+    nrm = synth.random_unit_normals(n, seed=n).astype(np.float32)
+    eps = synth.default_eps(4 * np.pi ** 2 * 0.3, n)
+    h = handle(p)
+    dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_params(h, kernel, eps, lam, 30, 0.1)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, theta)
+    dwglib.dwg_set_normals(h, nrm)
+    sel = np.unique((synth.uniform(7, n, min(n, 1500)) * n).astype(np.int64))
+    q = np.vstack([p[sel], synth.uniform_box(500, [-1.5, -1.5, -0.6], [1.5, 1.5, 0.6],
+                                             seed=n)]).astype(np.float32)
+    w = np.zeros(len(q), np.float32)
+    g = np.zeros((len(q), 3), np.float32)
+    dwglib.dwg_eval_gwn(h, q, w, g)
+    cnt_gpu = dwglib.dwg_get_stats(h)["interactions_eval"]
+    wo, go, cnt = oracle_mod.tree_gwn(p, nrm, a, q, kernel=kernel, eps=eps, lam=lam,
+                                      beta=float(np.float32(1) / np.float32(theta)),
+                                      want_count=True)
+    check_wg(w, g, wo, go, s_g(p, nrm, a, q, eps))
+    # identical opening decisions; the library also counts the query's own
+    # point (it adds zero and is removed from the gradient afterwards)
+    own = len(sel)
+    assert cnt_gpu == cnt.sum() + own
+
+
+def test_tree_with_tiny_opening_angle_is_exact(dwglib, oracle_mod, handle):
+    n = 20000
+    p, _ = synth.torus(n, seed=1, noise=0.003)
+    a = np.full(n, 4 * np.pi ** 2 * 0.3 / n, np.float32)
+    nrm = synth.random_unit_normals(n, seed=2).astype(np.float32)
+    eps = synth.default_eps(4 * np.pi ** 2 * 0.3, n)
+    h = handle(p)
+    dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_params(h, 0, eps, 0.0, 30, 0.1)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 1e-3)
+    dwglib.dwg_set_normals(h, nrm)
+    q = p[::40].copy()
+    w = np.zeros(len(q), np.float32)
+    g = np.zeros((len(q), 3), np.float32)
+    dwglib.dwg_eval_gwn(h, q, w, g)
+    wo, go = oracle_mod.gwn(p, nrm, a, q, eps=eps)
+    check_wg(w, g, wo, go, s_g(p, nrm, a, q, eps))
+
+
+def test_tree_orientation_torus(dwglib, handle):
+    n = 60000
+    p, nt = synth.torus(n, seed=0)
+    area = 4 * np.pi ** 2 * 0.3
+    h = handle(p)
+    dwglib.dwg_set_weights(h, np.full(n, area / n, np.float32))
+    dwglib.dwg_set_params(h, 1, synth.default_eps(area, n), 10.0, 40, 0.1)
+    dwglib.dwg_set_update(h, 7, 10, dwglib.DWG_UPDATE_LEVELSET)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+    dwglib.dwg_set_init(h, dwglib.DWG_INIT_RANDOM, 1)
+    out = np.zeros((n, 3), np.float32)
+    rc, iters = dwglib.dwg_orient(h, out)
+    assert agreement(out, nt) >= 0.999, (agreement(out, nt), iters)
+    st = dwglib.dwg_get_stats(h)
+    # the far field does the work of many points
+    assert st["interactions"] < 0.5 * iters * (n * n + st["n_corners"] * n)
