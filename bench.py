@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", type=int, default=0, help="0 plain, 1 screened (lambda 10)")
     ap.add_argument("--depth", type=int, default=None)
-    ap.add_argument("--workload", default="torus-100k", choices=["torus-100k", "metaballs-1m"])
+    ap.add_argument("--workload", default="torus-100k",
+                    choices=["torus-100k", "metaballs-1m", "batch-64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--one-step", action="store_true",

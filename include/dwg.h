@@ -215,6 +215,28 @@ int dwg_get_leaves(dwg_handle h, int64_t *leaves_out, int64_t cap, int64_t *coun
 int dwg_get_corners(dwg_handle h, int64_t *keys_out, int64_t cap, int64_t *count);
 
 /*
+ * Many clouds in one handle (the batched form of Alg. 1).
+ * dwg_create_batch: points float32 (total x 3, host or device) with the
+ *   clouds concatenated; offsets int64 (n_clouds + 1, host or device),
+ *   offsets[0] = 0, offsets[n_clouds] = total, every cloud non-empty.  Each
+ *   cloud gets its own root cube, octree, kNN tree, iso-value and
+ *   convergence test; its default softening is its own (0.5 L / sqrt(n)) and
+ *   its default octree depth is round(log2(n) / 2) clamped to [5, 10].
+ *   dwg_set_params / dwg_set_update / dwg_set_tree on the batch handle apply
+ *   to every cloud; dwg_set_init takes DWG_INIT_RANDOM (cloud c uses seed + c).
+ * dwg_orient_batch: runs every cloud until it converges (or max_iters); a
+ *   converged cloud stops iterating while the others go on.  The whole loop
+ *   is one CUDA graph launch; per iteration the all-pairs sums of every
+ *   cloud on that path are one kernel launch.  normals_out (total x 3, host
+ *   or device, may be NULL) in the input layout; iters_out (host, n_clouds,
+ *   may be NULL).  Returns DWG_NOT_CONVERGED if any cloud reached the cap.
+ * dwg_orient and dwg_step return DWG_ERR_STATE on a batch handle.
+ */
+int dwg_create_batch(const float *points, const int64_t *offsets, int n_clouds,
+                     dwg_handle *out);
+int dwg_orient_batch(dwg_handle h, float *normals_out, int *iters_out);
+
+/*
  * Per-kernel device times of one iteration, for profiling.  Runs one
  * iteration exactly like dwg_step (same kernels, same launch shapes, on the
  * handle's stream) with a CUDA event pair around each launch, and writes the

@@ -16,7 +16,17 @@
 
 using namespace dwg;
 
-struct dwg_ctx : public Ctx {};
+struct dwg_ctx : public Ctx {
+    // batch handles (dwg_create_batch): one sub-handle per cloud
+    bool is_batch = false;
+    std::vector<dwg_ctx *> clouds;
+    std::vector<int64_t> offsets;
+    GwnCloud *d_bcl_p = nullptr, *d_bcl_c = nullptr;
+    GwnItem *d_bit_p = nullptr, *d_bit_c = nullptr;
+    int64_t nit_p = 0, nit_c = 0;
+    IterState **d_states = nullptr;
+    bool eps_given = false;
+};
 
 static std::mutex g_err_mu;
 static std::string g_create_err;
@@ -226,7 +236,7 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
     mark(0);
     if (tree) {
         if (launch_tree_moments(c) != cudaSuccess ||
-            launch_tree_gwn(c, c->d_p4, c->n, true, c->d_part_p, c->n) != cudaSuccess)
+            launch_tree_gwn(c, c->d_p4, c->n, true, c->d_part_p, c->n, c->d_state) != cudaSuccess)
             return fail(c, DWG_ERR_CUDA, "tree launch failed");
     } else if ((rc = eval_launch(c, c->d_p4, c->n, true, c->nchunks_p, c->d_part_p, c->n))) {
         return rc;
@@ -241,8 +251,8 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
     if (c->mode == DWG_UPDATE_LEVELSET) {
         // w at the octree leaf corners, level set, face gradients to the k nearest points
         if (tree) {
-            if (launch_tree_gwn(c, c->d_corner_pos, c->ncorners, false, c->d_part_c, c->ncorners) !=
-                cudaSuccess)
+            if (launch_tree_gwn(c, c->d_corner_pos, c->ncorners, false, c->d_part_c, c->ncorners,
+                                c->d_state) != cudaSuccess)
                 return fail(c, DWG_ERR_CUDA, "tree launch failed");
         } else if ((rc = eval_launch(c, c->d_corner_pos, c->ncorners, false, c->nchunks_c,
                                      c->d_part_c, c->ncorners))) {
@@ -380,6 +390,13 @@ const char *dwg_last_error(dwg_handle h)
 void dwg_destroy(dwg_handle h)
 {
     if (!h) return;
+    for (dwg_ctx *c : h->clouds) dwg_destroy(c);
+    h->clouds.clear();
+    cudaFree(h->d_bcl_p);
+    cudaFree(h->d_bcl_c);
+    cudaFree(h->d_bit_p);
+    cudaFree(h->d_bit_c);
+    cudaFree(h->d_states);
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     invalidate_graph(h);
@@ -463,6 +480,7 @@ static int create_impl(dwg_ctx *c, const float *points, int64_t n)
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_dn_blocks, ceil_div(n, 256) * sizeof(double)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_state, sizeof(IterState)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_counter, sizeof(unsigned long long)));
+        k_iter_reset<<<1, 1, 0, c->stream>>>(c->d_state, c->max_iters, nullptr);
         DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
         DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         c->stats.n_points = n;
@@ -537,7 +555,9 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
     h->lambda = screening;
     h->max_iters = max_iters;
     h->tol = tol;
+    h->eps_given = true;
     invalidate_graph(h);
+    for (dwg_ctx *c : h->clouds) dwg_set_params(c, kernel, eps, screening, max_iters, tol);
     return DWG_OK;
 }
 
@@ -552,6 +572,7 @@ int dwg_set_update(dwg_handle h, int depth, int knn, int mode)
     h->knn = knn;
     h->mode = mode;
     invalidate_graph(h);
+    for (dwg_ctx *c : h->clouds) dwg_set_update(c, depth, knn, mode);
     return DWG_OK;
 }
 
@@ -564,6 +585,7 @@ int dwg_set_tree(dwg_handle h, int path, float theta)
     h->path = path;
     h->tree_beta = 1.0f / theta;
     invalidate_graph(h);
+    for (dwg_ctx *c : h->clouds) dwg_set_tree(c, path, theta);
     return DWG_OK;
 }
 
@@ -602,6 +624,16 @@ int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals)
 {
     if (!h) return DWG_ERR_INVALID;
     cudaSetDevice(h->device);
+    if (h->is_batch) {
+        if (mode != DWG_INIT_RANDOM)
+            return fail(h, DWG_ERR_STATE, "batch handles take DWG_INIT_RANDOM only");
+        // cloud c draws from seed + c
+        for (size_t c = 0; c < h->clouds.size(); ++c)
+            dwg_set_init(h->clouds[c], mode, seed + c, nullptr);
+        h->init_mode = mode;
+        h->seed = seed;
+        return DWG_OK;
+    }
     if (mode == DWG_INIT_RANDOM) {
         h->init_mode = mode;
         h->seed = seed;
@@ -656,6 +688,7 @@ static int read_state(dwg_handle h, IterState *st)
 int dwg_orient(dwg_handle h, float *normals_out, int *iters_out)
 {
     if (!h) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "use dwg_orient_batch on a batch handle");
     cudaSetDevice(h->device);
     int rc = ensure_iter_buffers(h);
     if (rc) return rc;
@@ -724,6 +757,7 @@ int dwg_step(dwg_handle h, float *w_out, float *grad_out, float *dtheta_out, dou
              double *stat_out)
 {
     if (!h) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "use dwg_orient_batch on a batch handle");
     cudaSetDevice(h->device);
     int rc = ensure_iter_buffers(h);
     if (rc) return rc;
@@ -805,7 +839,7 @@ int dwg_eval_gwn(dwg_handle h, const float *queries, int64_t m, float *w_out, fl
             if ((rc = build_tree(h)) || (rc = tree_records(h))) return rc;
             DWG_CUDA_TRY(h, cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), h->stream));
             if (launch_tree_moments(h) != cudaSuccess ||
-                launch_tree_gwn(h, q4, m, grad, part, m) != cudaSuccess)
+                launch_tree_gwn(h, q4, m, grad, part, m, nullptr) != cudaSuccess)
                 return fail(h, DWG_ERR_CUDA, "tree launch failed");
         } else if ((rc = eval_launch(h, q4, m, grad, nch, part, m))) {
             return rc;
@@ -952,6 +986,308 @@ int dwg_knn(dwg_handle h, const float *queries, int64_t m, int k, int64_t *idx_o
     cudaFree(q4);
     cudaFree(idx);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// batches: many clouds, one launch per iteration for the all-pairs sums
+// ---------------------------------------------------------------------------
+__global__ void k_batch_cond(IterState *const *states, int nc, int max_iters,
+                             cudaGraphConditionalHandle cond)
+{
+    __shared__ int s_more;
+    if (threadIdx.x == 0) s_more = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const IterState *st = states[c];
+        if (!st->done && st->iter < max_iters) s_more = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, s_more ? 1u : 0u);
+}
+
+// per-cloud octree depth when none is set: about half the bits of n
+static int auto_depth(int64_t n)
+{
+    int d = (int)lround(0.5 * log2((double)std::max<int64_t>(n, 2)));
+    return std::min(10, std::max(5, d));
+}
+
+static int batch_prepare(dwg_ctx *h)
+{
+    for (dwg_ctx *c : h->clouds) {
+        c->stream = h->stream;
+        int rc = ensure_iter_buffers(c);
+        if (rc) return fail(h, rc, "cloud: " + c->err);
+        c->normals_pending = true;
+        if ((rc = prepare_normals(c))) return fail(h, rc, "cloud: " + c->err);
+        k_iter_reset<<<1, 1, 0, h->stream>>>(c->d_state, c->max_iters, c->d_counter);
+    }
+    LAUNCH_CHECK(h);
+    return DWG_OK;
+}
+
+static int batch_tables(dwg_ctx *h)
+{
+    std::vector<GwnCloud> cp, cc;
+    std::vector<GwnItem> ip, ic;
+    for (dwg_ctx *c : h->clouds) {
+        if (use_tree(c)) continue;
+        EvalParams ep = make_eval_params(c);
+        int64_t ntiles = c->npad / kSrcTile;
+        for (int pass = 0; pass < 2; ++pass) {
+            bool grad = pass == 0;
+            if (!grad && c->mode != DWG_UPDATE_LEVELSET) continue;
+            int64_t m = grad ? c->n : c->ncorners;
+            int nch = grad ? c->nchunks_p : c->nchunks_c;
+            GwnCloud g;
+            g.src = c->d_src;
+            g.ntiles = ntiles;
+            g.q = grad ? c->d_p4 : c->d_corner_pos;
+            g.m = m;
+            g.tpc = (int)ceil_div(ntiles, nch);
+            g.part = grad ? c->d_part_p : c->d_part_c;
+            g.stride = m;
+            g.ep = ep;
+            g.st = c->d_state;
+            auto &tab = grad ? cp : cc;
+            auto &its = grad ? ip : ic;
+            int id = (int)tab.size();
+            tab.push_back(g);
+            int64_t qt = ceil_div(m, batch_query_tile(grad));
+            for (int ch = 0; ch < nch; ++ch)
+                for (int64_t t = 0; t < qt; ++t) its.push_back(GwnItem{id, (int)t, ch, 0});
+        }
+    }
+    auto put = [&](auto &vec, auto **dptr) -> int {
+        cudaFree(*dptr);
+        *dptr = nullptr;
+        if (vec.empty()) return DWG_OK;
+        DWG_CUDA_TRY(h, cudaMalloc(dptr, vec.size() * sizeof(vec[0])));
+        DWG_CUDA_TRY(h, cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(vec[0]),
+                                   cudaMemcpyHostToDevice));
+        return DWG_OK;
+    };
+    int rc;
+    if ((rc = put(cp, &h->d_bcl_p)) || (rc = put(cc, &h->d_bcl_c)) || (rc = put(ip, &h->d_bit_p)) ||
+        (rc = put(ic, &h->d_bit_c)))
+        return rc;
+    h->nit_p = (int64_t)ip.size();
+    h->nit_c = (int64_t)ic.size();
+    std::vector<IterState *> st;
+    for (dwg_ctx *c : h->clouds) st.push_back(c->d_state);
+    cudaFree(h->d_states);
+    h->d_states = nullptr;
+    DWG_CUDA_TRY(h, cudaMalloc(&h->d_states, st.size() * sizeof(IterState *)));
+    DWG_CUDA_TRY(h, cudaMemcpy(h->d_states, st.data(), st.size() * sizeof(IterState *),
+                               cudaMemcpyHostToDevice));
+    return DWG_OK;
+}
+
+// one iteration of every cloud
+static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
+{
+    bool scr = h->kernel == DWG_KERNEL_SCREENED && h->lambda > 0.f;
+    if (launch_gwn_batch(h->d_bcl_p, h->d_bit_p, h->nit_p, true, scr, h->d_err, h->stream) !=
+            cudaSuccess ||
+        launch_gwn_batch(h->d_bcl_c, h->d_bit_c, h->nit_c, false, scr, h->d_err, h->stream) !=
+            cudaSuccess)
+        return fail(h, DWG_ERR_CUDA, "batched gwn launch failed");
+    for (dwg_ctx *c : h->clouds) {
+        c->stream = h->stream;
+        if (use_tree(c)) {
+            if (launch_tree_moments(c) != cudaSuccess ||
+                launch_tree_gwn(c, c->d_p4, c->n, true, c->d_part_p, c->n, c->d_state) !=
+                    cudaSuccess ||
+                (c->mode == DWG_UPDATE_LEVELSET &&
+                 launch_tree_gwn(c, c->d_corner_pos, c->ncorners, false, c->d_part_c, c->ncorners,
+                                 c->d_state) != cudaSuccess))
+                return fail(h, DWG_ERR_CUDA, "tree launch failed");
+        }
+        if (launch_reduce_points(c, c->d_part_p, c->nchunks_p, c->n, c->d_p4, 1, true, c->d_wg,
+                                 c->d_wsum_blocks) != cudaSuccess ||
+            launch_iso(c) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "reduce launch failed");
+        if (c->mode == DWG_UPDATE_LEVELSET &&
+            (launch_reduce_w(c, c->d_part_c, c->nchunks_c, c->ncorners, c->d_wc) != cudaSuccess ||
+             launch_mc_faces(c) != cudaSuccess || launch_knn_scatter(c) != cudaSuccess))
+            return fail(h, DWG_ERR_CUDA, "level-set launch failed");
+        if (launch_normal_update(c) != cudaSuccess || launch_select(c, cond, 0) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "update launch failed");
+    }
+    k_batch_cond<<<1, 256, 0, h->stream>>>(h->d_states, (int)h->clouds.size(), h->max_iters, cond);
+    LAUNCH_CHECK(h);
+    return DWG_OK;
+}
+
+static int batch_build_graph(dwg_ctx *h)
+{
+    invalidate_graph(h);
+    int rc = batch_tables(h);
+    if (rc) return rc;
+    cudaGraph_t g = nullptr;
+    DWG_CUDA_TRY(h, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(h, DWG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    cudaStream_t saved = h->stream;
+    h->stream = h->own_stream;
+    e = cudaStreamBeginCaptureToGraph(h->stream, cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                      0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        h->stream = saved;
+        cudaGraphDestroy(g);
+        return fail(h, DWG_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    }
+    rc = batch_body(h, cond);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(h->stream, &captured);
+    h->stream = saved;
+    for (dwg_ctx *c : h->clouds) c->stream = saved;
+    if (rc || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (rc) return rc;
+        return fail(h, DWG_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph_exec = nullptr;
+        return fail(h, DWG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    h->graph_valid = true;
+    return DWG_OK;
+}
+
+int dwg_create_batch(const float *points, const int64_t *offsets, int n_clouds, dwg_handle *out)
+{
+    if (out) *out = nullptr;
+    if (!out || !points || !offsets || n_clouds < 1) {
+        set_global_error("dwg_create_batch: null argument or n_clouds < 1");
+        return DWG_ERR_INVALID;
+    }
+    std::vector<int64_t> off(n_clouds + 1);
+    if (is_device_ptr(offsets)) {
+        if (cudaMemcpy(off.data(), offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            set_global_error("dwg_create_batch: cannot read offsets");
+            return DWG_ERR_CUDA;
+        }
+    } else {
+        memcpy(off.data(), offsets, off.size() * sizeof(int64_t));
+    }
+    if (off[0] != 0) {
+        set_global_error("dwg_create_batch: offsets[0] must be 0");
+        return DWG_ERR_INVALID;
+    }
+    for (int c = 0; c < n_clouds; ++c)
+        if (off[c + 1] <= off[c]) {
+            set_global_error("dwg_create_batch: every cloud needs at least one point");
+            return DWG_ERR_INVALID;
+        }
+    const int64_t total = off[n_clouds];
+    dwg_ctx *h = new (std::nothrow) dwg_ctx();
+    if (!h) return DWG_ERR_OOM;
+    h->is_batch = true;
+    h->offsets = off;
+    float *dpts = nullptr;
+    bool own = false;
+    auto body = [&]() -> int {
+        DWG_CUDA_TRY(h, cudaGetDevice(&h->device));
+        DWG_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+        h->stream = h->own_stream;
+        DWG_CUDA_TRY(h, cudaMalloc(&h->d_err, sizeof(int)));
+        DWG_CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+        if (is_device_ptr(points)) {
+            dpts = const_cast<float *>(points);
+        } else {
+            DWG_CUDA_TRY(h, cudaMalloc(&dpts, total * 3 * sizeof(float)));
+            own = true;
+            DWG_CUDA_TRY(h, cudaMemcpy(dpts, points, total * 3 * sizeof(float),
+                                       cudaMemcpyHostToDevice));
+        }
+        h->n = total;
+        for (int c = 0; c < n_clouds; ++c) {
+            dwg_ctx *s = new (std::nothrow) dwg_ctx();
+            if (!s) return DWG_ERR_OOM;
+            h->clouds.push_back(s);
+            int rc = create_impl(s, dpts + 3 * off[c], off[c + 1] - off[c]);
+            if (rc) return fail(h, rc, "cloud " + std::to_string(c) + ": " + s->err);
+            s->depth = auto_depth(s->n);
+            s->seed = h->seed + (uint64_t)c;
+        }
+        return DWG_OK;
+    };
+    int rc = body();
+    if (own) cudaFree(dpts);
+    if (rc) {
+        set_global_error("dwg_create_batch: " + h->err);
+        dwg_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return DWG_OK;
+}
+
+int dwg_orient_batch(dwg_handle h, float *normals_out, int *iters_out)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (!h->is_batch) return fail(h, DWG_ERR_STATE, "not a batch handle");
+    cudaSetDevice(h->device);
+    int rc = batch_prepare(h);
+    if (rc) return rc;
+    if (!h->graph_valid && (rc = batch_build_graph(h))) return rc;
+    cudaEvent_t e0, e1;
+    DWG_CUDA_TRY(h, cudaEventCreate(&e0));
+    DWG_CUDA_TRY(h, cudaEventCreate(&e1));
+    cudaEventRecord(e0, h->stream);
+    cudaError_t e = cudaGraphLaunch(h->graph_exec, h->stream);
+    cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(h, DWG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    if ((rc = check_device_err(h))) return rc;
+    bool all = true;
+    double inter = 0.0;
+    int maxit = 0;
+    for (size_t c = 0; c < h->clouds.size(); ++c) {
+        dwg_ctx *s = h->clouds[c];
+        IterState st;
+        if ((rc = read_state(s, &st))) return fail(h, rc, s->err);
+        if ((rc = check_device_err(s))) return fail(h, rc, s->err);
+        int it = std::min(st.iter, s->max_iters);
+        if (iters_out) iters_out[c] = it;
+        all = all && st.done;
+        maxit = std::max(maxit, it);
+        double per = (double)s->n * (double)s->n +
+                     (s->mode == DWG_UPDATE_LEVELSET ? (double)s->ncorners * (double)s->n : 0.0);
+        if (use_tree(s)) {
+            unsigned long long cnt = 0;
+            DWG_CUDA_TRY(h, cudaMemcpy(&cnt, s->d_counter, sizeof(cnt), cudaMemcpyDeviceToHost));
+            inter += (double)cnt;
+        } else {
+            inter += per * it;
+        }
+        if (normals_out && (rc = dwg_get_normals(s, normals_out + 3 * h->offsets[c])))
+            return fail(h, rc, s->err);
+    }
+    h->stats.iters = maxit;
+    h->stats.converged = all;
+    h->stats.interactions = inter;
+    h->stats.ms_orient = ms;
+    return all ? DWG_OK : DWG_NOT_CONVERGED;
 }
 
 }  // extern "C"

@@ -169,11 +169,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 constexpr int kEvalThreads = 128;
 constexpr int kStages = 4;
 
+// One CTA's work: query tile `qtile` against source chunk `chunk`.
 template <int P, bool GRAD, bool SCREENED>
-__global__ void __launch_bounds__(kEvalThreads)
-    k_gwn(const float *__restrict__ src, int64_t ntiles_total, const float4 *__restrict__ q,
-          int64_t m, int tiles_per_chunk, float *__restrict__ part, int64_t stride,
-          EvalParams ep, int *__restrict__ err)
+__device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t ntiles_total,
+                                          const float4 *__restrict__ q, int64_t m,
+                                          int tiles_per_chunk, float *__restrict__ part,
+                                          int64_t stride, const EvalParams &ep,
+                                          int *__restrict__ err, int64_t qtile, int chunk)
 {
     constexpr int T = kSrcTile;
     constexpr int TILE_FLOATS = T * kSrcFloats;
@@ -186,8 +188,7 @@ __global__ void __launch_bounds__(kEvalThreads)
     __shared__ int s_abort;
 
     const int tid = threadIdx.x;
-    const int64_t qbase = (int64_t)blockIdx.x * QB + tid;
-    const int chunk = blockIdx.y;
+    const int64_t qbase = qtile * QB + tid;
     const int64_t tile0 = (int64_t)chunk * tiles_per_chunk;
     int ntiles = (int)min((int64_t)tiles_per_chunk, ntiles_total - tile0);
     if (ntiles < 0) ntiles = 0;
@@ -364,6 +365,30 @@ __global__ void __launch_bounds__(kEvalThreads)
                     part[((int64_t)(chunk * NA + aa) * 2 + h) * stride + i] = vals[aa][h];
         }
     }
+}
+
+template <int P, bool GRAD, bool SCREENED>
+__global__ void __launch_bounds__(kEvalThreads)
+    k_gwn(const float *__restrict__ src, int64_t ntiles_total, const float4 *__restrict__ q,
+          int64_t m, int tiles_per_chunk, float *__restrict__ part, int64_t stride,
+          EvalParams ep, int *__restrict__ err)
+{
+    gwn_block<P, GRAD, SCREENED>(src, ntiles_total, q, m, tiles_per_chunk, part, stride, ep, err,
+                                 (int64_t)blockIdx.x, (int)blockIdx.y);
+}
+
+// Many clouds in one launch: CTA b runs work item items[b] of its cloud;
+// clouds that have converged are skipped.
+template <int P, bool GRAD, bool SCREENED>
+__global__ void __launch_bounds__(kEvalThreads)
+    k_gwn_batch(const GwnCloud *__restrict__ clouds, const GwnItem *__restrict__ items,
+                int *__restrict__ err)
+{
+    const GwnItem it = items[blockIdx.x];
+    const GwnCloud &C = clouds[it.cloud];
+    if (C.st && cloud_idle(C.st)) return;
+    gwn_block<P, GRAD, SCREENED>(C.src, C.ntiles, C.q, C.m, C.tpc, C.part, C.stride, C.ep, err,
+                                 (int64_t)it.qtile, it.chunk);
 }
 
 // ---------------------------------------------------------------------------
@@ -680,6 +705,23 @@ cudaError_t launch_reduce_w_raw(const float *part, int nchunks, int64_t m, float
                                 cudaStream_t s)
 {
     k_reduce_w<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(part, nchunks, m, m, out);
+    return cudaGetLastError();
+}
+
+int batch_query_tile(bool grad) { return kEvalThreads * 2 * (grad ? kPGrad : kPW); }
+
+cudaError_t launch_gwn_batch(const GwnCloud *clouds, const GwnItem *items, int64_t nitems,
+                             bool grad, bool screened, int *err, cudaStream_t s)
+{
+    if (nitems <= 0) return cudaSuccess;
+    unsigned g = (unsigned)nitems;
+    if (grad) {
+        if (screened) k_gwn_batch<kPGrad, true, true><<<g, kEvalThreads, 0, s>>>(clouds, items, err);
+        else k_gwn_batch<kPGrad, true, false><<<g, kEvalThreads, 0, s>>>(clouds, items, err);
+    } else {
+        if (screened) k_gwn_batch<kPW, false, true><<<g, kEvalThreads, 0, s>>>(clouds, items, err);
+        else k_gwn_batch<kPW, false, false><<<g, kEvalThreads, 0, s>>>(clouds, items, err);
+    }
     return cudaGetLastError();
 }
 

@@ -42,12 +42,37 @@ struct IterState {
     double stat;         // convergence statistic of the current iteration
 };
 
+#ifdef __CUDACC__
+// a cloud whose loop has ended (converged, or at its iteration cap) skips
+// the rest of a batched iteration
+__device__ __forceinline__ bool cloud_idle(const IterState *st)
+{
+    return st->done || st->iter >= st->max_iters;
+}
+#endif
+
 struct EvalParams {
     float eps2;        // eps^2
     float s;           // sqrt(lambda)
     float s2;          // lambda
     float nl2e_s;      // -sqrt(lambda) * log2(e)
     int screened;
+};
+
+// one cloud of a batched evaluation launch
+struct GwnCloud {
+    const float *src;
+    int64_t ntiles;
+    const float4 *q;
+    int64_t m;
+    int tpc;           // source tiles per chunk
+    float *part;
+    int64_t stride;
+    EvalParams ep;
+    const IterState *st;
+};
+struct GwnItem {
+    int cloud, qtile, chunk, pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -214,6 +239,9 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
                                  const float4 *queries, int self_mode, bool grad, float4 *out,
                                  double *wsum_blocks);
 cudaError_t launch_reduce_w(Ctx *c, const float *part, int nchunks, int64_t m, float *out);
+int batch_query_tile(bool grad);
+cudaError_t launch_gwn_batch(const GwnCloud *clouds, const GwnItem *items, int64_t nitems,
+                             bool grad, bool screened, int *err, cudaStream_t s);
 int wsum_block_count(int64_t n);
 int gwn_w_chunks_raw(int64_t m, int64_t npad, int device);
 cudaError_t launch_gwn_w_raw(const float *src, int64_t npad, const float4 *q, int64_t m,
@@ -230,8 +258,9 @@ bool use_tree(const Ctx *c);
 int build_tree(Ctx *c);
 int tree_records(Ctx *c);
 cudaError_t launch_tree_moments(Ctx *c);
+// st: loop state whose end makes the kernel skip its work (NULL: always run)
 cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float *part,
-                            int64_t stride);
+                            int64_t stride, const IterState *st);
 
 // dwg_iter.cu
 cudaError_t launch_iso(Ctx *c);

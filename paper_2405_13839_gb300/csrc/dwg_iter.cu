@@ -23,6 +23,7 @@ namespace dwg {
 // ---------------------------------------------------------------------------
 __global__ void k_iso(const double *__restrict__ wsum_blocks, int nb, int64_t n, IterState *st)
 {
+    if (cloud_idle(st)) return;  // finished cloud of a batch
     __shared__ double sh[256];
     double s = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) s += wsum_blocks[b];
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(256)
                const float *__restrict__ wc, IterState *st, float4 *__restrict__ faces,
                int64_t max_faces, int *err)
 {
+    if (cloud_idle(st)) return;  // finished cloud of a batch
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double iso = st->iso;
     F3 area[6], cen[6];
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(128)
     k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
                   KnnTree T, int k, double scale, unsigned long long *acc, int *err)
 {
+    if (cloud_idle(st)) return;  // finished cloud of a batch
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nf = min((int64_t)st->nfaces, max_faces);
     if (f >= nf) return;
@@ -326,8 +329,10 @@ __global__ void __launch_bounds__(256)
     k_normal_update(int mode, int64_t n, unsigned long long *__restrict__ acc, double inv_scale,
                     const float4 *__restrict__ wg, const float4 *__restrict__ p4,
                     float4 *__restrict__ nrm, float *__restrict__ src,
-                    float *__restrict__ dtheta, double *__restrict__ dn_blocks)
+                    float *__restrict__ dtheta, double *__restrict__ dn_blocks,
+                    const IterState *st)
 {
+    if (cloud_idle(st)) return;  // finished cloud of a batch: normals stay
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dn = 0.0;
     if (i < n) {
@@ -441,6 +446,7 @@ __global__ void __launch_bounds__(kSelThreads)
              const double *__restrict__ dn_blocks, int ndn, double *tr_iso, double *tr_stat,
              double *tr_dn, long long *tr_faces, cudaGraphConditionalHandle cond, int use_cond)
 {
+    if (cloud_idle(st)) return;  // finished cloud of a batch
     __shared__ unsigned hist[kSelBins];
     __shared__ unsigned warp_sums[33];
     __shared__ int s_bin;
@@ -603,7 +609,7 @@ cudaError_t launch_normal_update(Ctx *c)
 {
     k_normal_update<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->stream>>>(
         c->mode, c->n, c->d_acc, 1.0 / c->acc_scale, c->d_wg, c->d_p4, c->d_nrm, c->d_src,
-        c->d_dtheta, c->d_dn_blocks);
+        c->d_dtheta, c->d_dn_blocks, c->d_state);
     return cudaGetLastError();
 }
 

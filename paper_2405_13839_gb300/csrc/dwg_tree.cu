@@ -247,8 +247,9 @@ __global__ void __launch_bounds__(kTreeThreads)
     k_tree_gwn(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ rec,
                const float4 *__restrict__ mrec, const float *__restrict__ src, int64_t n,
                int levels, EvalParams ep, float *__restrict__ part, int64_t stride,
-               unsigned long long *__restrict__ counter, int *err)
+               unsigned long long *__restrict__ counter, int *err, const IterState *st)
 {
+    if (st && cloud_idle(st)) return;  // finished cloud of a batch
     __shared__ int s_node[kTreeThreads / 32][kTreeStack];
     __shared__ unsigned s_mask[kTreeThreads / 32][kTreeStack];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -398,7 +399,7 @@ cudaError_t launch_tree_moments(Ctx *c)
 }
 
 cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float *part,
-                            int64_t stride)
+                            int64_t stride, const IterState *st)
 {
     EvalParams ep = make_eval_params(c);
     unsigned blocks = (unsigned)ceil_div(m, kTreeThreads);
@@ -406,20 +407,20 @@ cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float
         if (ep.screened)
             k_tree_gwn<true, true><<<blocks, kTreeThreads, 0, c->stream>>>(
                 q, m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->knn_levels, ep, part, stride,
-                c->d_counter, c->d_err);
+                c->d_counter, c->d_err, st);
         else
             k_tree_gwn<true, false><<<blocks, kTreeThreads, 0, c->stream>>>(
                 q, m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->knn_levels, ep, part, stride,
-                c->d_counter, c->d_err);
+                c->d_counter, c->d_err, st);
     } else {
         if (ep.screened)
             k_tree_gwn<false, true><<<blocks, kTreeThreads, 0, c->stream>>>(
                 q, m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->knn_levels, ep, part, stride,
-                c->d_counter, c->d_err);
+                c->d_counter, c->d_err, st);
         else
             k_tree_gwn<false, false><<<blocks, kTreeThreads, 0, c->stream>>>(
                 q, m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->knn_levels, ep, part, stride,
-                c->d_counter, c->d_err);
+                c->d_counter, c->d_err, st);
     }
     return cudaGetLastError();
 }

@@ -77,6 +77,8 @@ def _load() -> ctypes.CDLL:
         "dwg_set_update": ([H, I, I, I], I),
         "dwg_set_weights": ([H, P], I),
         "dwg_set_tree": ([H, I, F], I),
+        "dwg_create_batch": ([P, P, I, ctypes.POINTER(H)], I),
+        "dwg_orient_batch": ([H, P, P], I),
         "dwg_set_init": ([H, I, ctypes.c_uint64, P], I),
         "dwg_orient": ([H, P, ctypes.POINTER(I)], I),
         "dwg_step": ([H, P, P, P, ctypes.POINTER(ctypes.c_double),
@@ -155,6 +157,24 @@ def dwg_create(points):
     rc = _lib.dwg_create(_ptr(points), int(points.shape[0]), ctypes.byref(h))
     _raise(None, rc)
     return h
+
+
+def dwg_create_batch(points, offsets):
+    """Batch handle for concatenated clouds; offsets int64 (n_clouds + 1)."""
+    _check_f32(points, 3, "points")
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    h = ctypes.c_void_p()
+    rc = _lib.dwg_create_batch(_ptr(points), off.ctypes.data, len(off) - 1, ctypes.byref(h))
+    _raise(None, rc)
+    return h
+
+
+def dwg_orient_batch(h, normals_out, n_clouds):
+    """Orients every cloud; returns (rc, iterations per cloud)."""
+    it = np.zeros(n_clouds, dtype=np.int32)
+    rc = _lib.dwg_orient_batch(h, _ptr(normals_out), it.ctypes.data)
+    _raise(h, rc)
+    return rc, it
 
 
 def dwg_destroy(h):

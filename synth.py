@@ -333,3 +333,31 @@ def workload_metaballs1m():
     return dict(name="metaballs-1m", points=p, normals_true=nt,
                 weights=np.ones(n, np.float32), eps=0.5 * ext / np.sqrt(n), depth=10,
                 max_iters=30, tol=0.1, theta=0.5)
+
+
+def workload_batch64(seed=0, n_clouds=64, lo=5_000, hi=500_000):
+    """64 clouds with sizes log-uniform in [5,000, 500,000]: spheres, tori
+    and metaball surfaces (uniform choice), Gaussian noise U[0, 1 %] of each
+    cloud's diagonal, each placed in its own region of space (clouds never
+    interact: each has its own octree and iso-value)."""
+    u = uniform(seed, 700, n_clouds)
+    sizes = np.round(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
+    kind = (uniform(seed, 701, n_clouds) * 3).astype(int)
+    noise = 0.01 * uniform(seed, 702, n_clouds)
+    pts, nrms, offs = [], [], [0]
+    for c in range(n_clouds):
+        n = int(sizes[c])
+        if kind[c] == 0:
+            p, nt = sphere(n, seed=seed * 1000 + c)
+        elif kind[c] == 1:
+            p, nt = torus(n, seed=seed * 1000 + c)
+        else:
+            p, nt = metaballs(n, 0, seed=seed * 1000 + c, blobs=6, res=72)
+        if noise[c] > 0:
+            p = add_noise(p, float(noise[c]), seed=seed * 1000 + c)
+        pts.append(p)
+        nrms.append(nt)
+        offs.append(offs[-1] + n)
+    return dict(name="batch-64", points=np.ascontiguousarray(np.vstack(pts), dtype=np.float32),
+                normals_true=np.vstack(nrms), offsets=np.array(offs, dtype=np.int64),
+                kinds=kind, sizes=sizes, max_iters=30, tol=0.1)

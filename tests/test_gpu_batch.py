@@ -1,0 +1,83 @@
+"""Batched orientation (one handle, many clouds): every cloud's result must be
+bit-identical to orienting that cloud alone with the same parameters."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _clouds():
+    specs = [("sphere", 1500, 0), ("torus", 4000, 1), ("sphere", 700, 2), ("torus", 9000, 3),
+             ("sphere", 33, 4)]
+    pts, offs = [], [0]
+    for kind, n, s in specs:
+        p = synth.sphere(n, seed=s)[0] if kind == "sphere" else synth.torus(n, seed=s)[0]
+        pts.append(p)
+        offs.append(offs[-1] + n)
+    return np.ascontiguousarray(np.vstack(pts)), np.array(offs, np.int64)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_batch_equals_singles(dwglib, path):
+    P, off = _clouds()
+    nc = len(off) - 1
+    hb = dwglib.dwg_create_batch(P, off)
+    try:
+        dwglib.dwg_set_tree(hb, path, 0.5)
+        dwglib.dwg_set_init(hb, dwglib.DWG_INIT_RANDOM, 11)
+        out = np.zeros_like(P)
+        rc, iters = dwglib.dwg_orient_batch(hb, out, nc)
+        st = dwglib.dwg_get_stats(hb)
+    finally:
+        dwglib.dwg_destroy(hb)
+    assert st["n_points"] == len(P)
+    for c in range(nc):
+        p = np.ascontiguousarray(P[off[c]:off[c + 1]])
+        n = len(p)
+        h = dwglib.dwg_create(p)
+        try:
+            depth = min(10, max(5, int(round(0.5 * np.log2(max(n, 2))))))
+            dwglib.dwg_set_update(h, depth, 10, dwglib.DWG_UPDATE_LEVELSET)
+            dwglib.dwg_set_tree(h, path, 0.5)
+            dwglib.dwg_set_init(h, dwglib.DWG_INIT_RANDOM, 11 + c)
+            o = np.zeros_like(p)
+            rc1, it1 = dwglib.dwg_orient(h, o)
+        finally:
+            dwglib.dwg_destroy(h)
+        assert it1 == iters[c], (c, it1, iters[c])
+        assert np.array_equal(o, out[off[c]:off[c + 1]]), c
+
+
+def test_batch_orients_every_cloud(dwglib):
+    P, off = _clouds()
+    nts = []
+    for kind, n, s in [("sphere", 1500, 0), ("torus", 4000, 1), ("sphere", 700, 2),
+                       ("torus", 9000, 3), ("sphere", 33, 4)]:
+        nts.append(synth.sphere(n, seed=s)[1] if kind == "sphere" else synth.torus(n, seed=s)[1])
+    hb = dwglib.dwg_create_batch(P, off)
+    try:
+        dwglib.dwg_set_params(hb, 1, 0.01, 10.0, 40, 0.1)   # screened, one eps for all
+        out = np.zeros_like(P)
+        rc, iters = dwglib.dwg_orient_batch(hb, out, len(off) - 1)
+    finally:
+        dwglib.dwg_destroy(hb)
+    for c in range(4):  # the 33-point cloud is too sparse to judge
+        o = out[off[c]:off[c + 1]]
+        d = np.sum(o * nts[c], axis=1)
+        s = 1.0 if d.sum() >= 0 else -1.0
+        assert np.mean(s * d > 0) >= 0.99, (c, np.mean(s * d > 0), iters)
+
+
+def test_batch_handle_rejects_single_calls(dwglib):
+    P, off = _clouds()
+    hb = dwglib.dwg_create_batch(P, off)
+    try:
+        with pytest.raises(dwglib.DWGError) as e:
+            dwglib.dwg_orient(hb, np.zeros_like(P))
+        assert e.value.code == dwglib.DWG_ERR_STATE
+    finally:
+        dwglib.dwg_destroy(hb)
+    with pytest.raises(dwglib.DWGError):
+        dwglib.dwg_create_batch(P, np.array([0, 10, 10, len(P)], np.int64))
