@@ -63,6 +63,7 @@ extern "C" {
  * device from a seed, or caller-given normals. */
 #define DWG_INIT_RANDOM 0
 #define DWG_INIT_GIVEN 1
+#define DWG_INIT_LEARNED 2
 
 /* Evaluation path: exact all-pairs sums, or the Barnes-Hut far field of
  * Sec. 5.2; AUTO takes all-pairs up to 262,144 points and the tree above. */
@@ -141,6 +142,11 @@ int dwg_set_weights(dwg_handle h, const float *a);
  * phi = 2 pi u1, n = (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z);
  * normals is ignored.  DWG_INIT_GIVEN copies normals (float32 n x 3, input
  * order, host or device; each is normalised, zero vectors rejected).
+ * DWG_INIT_LEARNED (a project extension, not in the paper): `normals` points
+ * to the 12,675 float32 parameters of the kNN-patch network (layout in
+ * dwg_mlp_forward); the initial normal of each point is the normalised
+ * network output for its patch features (dwg_mlp_features); where the output
+ * is zero or not finite the random normal from `seed` is kept.
  */
 int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals);
 
@@ -253,6 +259,35 @@ int dwg_orient_batch(dwg_handle h, float *normals_out, int *iters_out);
  * Entries 3-6 are 0 for DWG_UPDATE_DIRECT.  *count receives 9.
  */
 int dwg_profile_step(dwg_handle h, float *ms_out, int cap, int *count);
+
+/*
+ * Learned warm start (a project extension; the paper initialises with
+ * random, PCA or Gauss-map normals, Sec. 5.1).  The network maps a 64-value
+ * patch feature row to 3 outputs: three hidden layers of 64 with ReLU,
+ * bfloat16 weights and activations on the tensor cores, fp32 accumulation.
+ * Parameters (float32, 12,675): W1[64][64] (out, in), b1[64], W2[64][64],
+ * b2[64], W3[64][64], b3[64], W4[3][64], b4[3].
+ *
+ * dwg_mlp_features: feature rows of the handle's points (float32 n x 64,
+ *   input order, host or device): offsets to the 16 nearest other points
+ *   (exact, ascending, ties to the smaller index) divided by their RMS
+ *   length, then (p - c) / R with c the centroid and R the RMS radius of
+ *   the cloud, zero padding.
+ * dwg_mlp_forward: Y (B x 3) = network(X) for B rows of X (B x 64).
+ * dwg_mlp_grad: mean squared error (1/B) sum |network(X) - T|^2 of B rows
+ *   against targets T (B x 3) into *loss (host) and its gradient with
+ *   respect to every parameter into grad (12,675).
+ * dwg_mlp_adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step >= 1)
+ *   of params with grad, moments m and v (12,675 each, updated in place).
+ * The last three take DEVICE pointers only and run on `stream` (NULL: the
+ * legacy default stream); they return after the results are written.
+ */
+int dwg_mlp_features(dwg_handle h, float *X_out);
+int dwg_mlp_forward(const float *params, const float *X, int64_t B, float *Y, void *stream);
+int dwg_mlp_grad(const float *params, const float *X, const float *T, int64_t B, float *grad,
+                 double *loss, void *stream);
+int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
+                 void *stream);
 
 /*
  * k nearest input points (1 <= k <= 32) of m query points (float32 m x 3):

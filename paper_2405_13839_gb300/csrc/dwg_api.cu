@@ -351,10 +351,30 @@ static int check_device_err(Ctx *c)
 static int prepare_normals(Ctx *c)
 {
     if (c->normals_pending) {
-        if (c->init_mode == DWG_INIT_RANDOM) {
+        if (c->init_mode == DWG_INIT_RANDOM || c->init_mode == DWG_INIT_LEARNED) {
             if (launch_random_normals(c->d_nrm, c->d_perm, c->n, c->seed, c->stream) !=
                 cudaSuccess)
                 return fail(c, DWG_ERR_CUDA, "random normals launch failed");
+            if (c->init_mode == DWG_INIT_LEARNED) {
+                float *X = nullptr, *Y = nullptr;
+                double *cR = nullptr;
+                auto run = [&]() -> int {
+                    DWG_CUDA_TRY(c, cudaMalloc(&X, c->n * 64 * sizeof(float)));
+                    DWG_CUDA_TRY(c, cudaMalloc(&Y, c->n * 3 * sizeof(float)));
+                    DWG_CUDA_TRY(c, cudaMalloc(&cR, 4 * sizeof(double)));
+                    if (launch_features(c, X, false, cR) != cudaSuccess ||
+                        launch_mlp_forward(c->d_mlp_params, X, c->n, Y, c->stream) != cudaSuccess ||
+                        launch_normals_from_y(c, Y) != cudaSuccess)
+                        return fail(c, DWG_ERR_CUDA, "learned init launch failed");
+                    DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+                    return DWG_OK;
+                };
+                int rc = run();
+                cudaFree(X);
+                cudaFree(Y);
+                cudaFree(cR);
+                if (rc) return rc;
+            }
         } else {
             DWG_CUDA_TRY(c, cudaMemcpyAsync(c->d_nrm, c->d_nrm_init, c->n * sizeof(float4),
                                             cudaMemcpyDeviceToDevice, c->stream));
@@ -406,7 +426,7 @@ void dwg_destroy(dwg_handle h)
                     h->d_acc, h->d_part_p, h->d_part_c, h->d_wsum_blocks, h->d_dn_blocks,
                     h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err,
                     h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
-                    h->d_tree_mrec, h->d_counter};
+                    h->d_tree_mrec, h->d_counter, h->d_mlp_params};
     for (void *p : bufs) cudaFree(p);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -625,16 +645,27 @@ int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals)
     if (!h) return DWG_ERR_INVALID;
     cudaSetDevice(h->device);
     if (h->is_batch) {
-        if (mode != DWG_INIT_RANDOM)
-            return fail(h, DWG_ERR_STATE, "batch handles take DWG_INIT_RANDOM only");
+        if (mode == DWG_INIT_GIVEN)
+            return fail(h, DWG_ERR_STATE, "batch handles take DWG_INIT_RANDOM or DWG_INIT_LEARNED");
         // cloud c draws from seed + c
-        for (size_t c = 0; c < h->clouds.size(); ++c)
-            dwg_set_init(h->clouds[c], mode, seed + c, nullptr);
+        for (size_t c = 0; c < h->clouds.size(); ++c) {
+            int rc = dwg_set_init(h->clouds[c], mode, seed + c, normals);
+            if (rc) return fail(h, rc, h->clouds[c]->err);
+        }
         h->init_mode = mode;
         h->seed = seed;
         return DWG_OK;
     }
     if (mode == DWG_INIT_RANDOM) {
+        h->init_mode = mode;
+        h->seed = seed;
+    } else if (mode == DWG_INIT_LEARNED) {
+        if (!normals) return fail(h, DWG_ERR_INVALID, "DWG_INIT_LEARNED needs the parameters");
+        if (!h->d_mlp_params)
+            DWG_CUDA_TRY(h, cudaMalloc(&h->d_mlp_params, kMlpParamCount * sizeof(float)));
+        int rc = upload(h, h->d_mlp_params, normals, kMlpParamCount * sizeof(float));
+        if (rc) return rc;
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         h->init_mode = mode;
         h->seed = seed;
     } else if (mode == DWG_INIT_GIVEN) {
@@ -957,6 +988,92 @@ int dwg_get_corners(dwg_handle h, int64_t *keys_out, int64_t cap, int64_t *count
                    cudaStreamSynchronize(h->stream)
                ? DWG_ERR_CUDA
                : DWG_OK;
+}
+
+int dwg_mlp_features(dwg_handle h, float *X_out)
+{
+    if (!h || !X_out) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "not on a batch handle");
+    cudaSetDevice(h->device);
+    float *X = nullptr;
+    double *cR = nullptr;
+    auto run = [&]() -> int {
+        DWG_CUDA_TRY(h, cudaMalloc(&X, h->n * 64 * sizeof(float)));
+        DWG_CUDA_TRY(h, cudaMalloc(&cR, 4 * sizeof(double)));
+        if (launch_features(h, X, true, cR) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "features launch failed");
+        int rc = download(h, X_out, X, h->n * 64 * sizeof(float));
+        if (rc) return rc;
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return check_device_err(h);
+    };
+    int rc = run();
+    cudaFree(X);
+    cudaFree(cR);
+    return rc;
+}
+
+static int mlp_check(std::initializer_list<const void *> ptrs, int64_t B)
+{
+    for (const void *p : ptrs)
+        if (!p || !is_device_ptr(p)) {
+            set_global_error("dwg_mlp_*: every array must be device memory");
+            return DWG_ERR_INVALID;
+        }
+    if (B < 1) {
+        set_global_error("dwg_mlp_*: B must be >= 1");
+        return DWG_ERR_INVALID;
+    }
+    return DWG_OK;
+}
+
+static int mlp_finish(cudaError_t e, cudaStream_t s)
+{
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_global_error(std::string("dwg_mlp_*: ") + cudaGetErrorString(e));
+        return DWG_ERR_CUDA;
+    }
+    return DWG_OK;
+}
+
+int dwg_mlp_forward(const float *params, const float *X, int64_t B, float *Y, void *stream)
+{
+    int rc = mlp_check({params, X, Y}, B);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    return mlp_finish(launch_mlp_forward(params, X, B, Y, s), s);
+}
+
+int dwg_mlp_grad(const float *params, const float *X, const float *T, int64_t B, float *grad,
+                 double *loss, void *stream)
+{
+    int rc = mlp_check({params, X, T, grad}, B);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dl = nullptr;
+    cudaError_t e = cudaMallocAsync(&dl, sizeof(double), s);
+    if (e == cudaSuccess) e = launch_mlp_grad(params, X, T, B, grad, dl, s);
+    double hl = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hl, dl, sizeof(double), cudaMemcpyDeviceToHost, s);
+    rc = mlp_finish(e, s);
+    cudaFreeAsync(dl, s);
+    cudaStreamSynchronize(s);
+    if (loss) *loss = hl;
+    return rc;
+}
+
+int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
+                 void *stream)
+{
+    int rc = mlp_check({params, grad, m, v}, 1);
+    if (rc) return rc;
+    if (step < 1 || !(lr > 0.f)) {
+        set_global_error("dwg_mlp_adam: need step >= 1 and lr > 0");
+        return DWG_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return mlp_finish(launch_adam(params, grad, m, v, step, lr, s), s);
 }
 
 int dwg_knn(dwg_handle h, const float *queries, int64_t m, int k, int64_t *idx_out)

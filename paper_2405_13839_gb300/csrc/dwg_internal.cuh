@@ -94,6 +94,7 @@ struct Ctx {
     int init_mode = DWG_INIT_RANDOM;
     uint64_t seed = 1;
     bool normals_pending = true;   // initial normals must be (re)generated
+    float *d_mlp_params = nullptr; // learned warm start (12,675 fp32 parameters)
 
     // geometry (sorted along the Morton curve)
     double cube_lo[3] = {0, 0, 0};
@@ -271,5 +272,15 @@ cudaError_t launch_select(Ctx *c, cudaGraphConditionalHandle cond, int use_cond)
 cudaError_t launch_random_normals(float4 *nrm, const int64_t *perm, int64_t n, uint64_t seed,
                                   cudaStream_t s);
 cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t *idx_out);
+cudaError_t launch_features(Ctx *c, float *X, bool by_input, double *cR);
+cudaError_t launch_normals_from_y(Ctx *c, const float *Y);
+
+// dwg_mlp.cu
+constexpr int kMlpParamCount = 12675;
+cudaError_t launch_mlp_forward(const float *P, const float *X, int64_t B, float *Y, cudaStream_t s);
+cudaError_t launch_mlp_grad(const float *P, const float *X, const float *T, int64_t B, float *grad,
+                            double *loss, cudaStream_t s);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int step, float lr,
+                        cudaStream_t s);
 
 }  // namespace dwg

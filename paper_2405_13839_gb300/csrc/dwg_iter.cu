@@ -285,6 +285,8 @@ __device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *b
     }
 }
 
+static KnnTree knn_tree(const Ctx *c);
+
 template <int KMAX, bool FIXED>
 __global__ void __launch_bounds__(128)
     k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
@@ -320,6 +322,109 @@ __global__ void k_knn_query(const float4 *__restrict__ q, int64_t m, KnnTree T, 
     int bj[KMAX];
     knn_search<KMAX, FIXED>(T, F3{v.x, v.y, v.z}, k, bj, err);
     for (int t = 0; t < k; ++t) idx_out[i * k + t] = bj[t] >= 0 ? T.perm[bj[t]] : -1;
+}
+
+// ---------------------------------------------------------------------------
+// learned warm start: patch features from the 16 nearest other points
+// ---------------------------------------------------------------------------
+__global__ void k_centroid(const float4 *__restrict__ p4, int64_t n, double *out /* cx,cy,cz,R */)
+{
+    __shared__ double sh[256][3];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        float4 p = p4[i];
+        s[0] += p.x; s[1] += p.y; s[2] += p.z;
+    }
+    for (int k = 0; k < 3; ++k) sh[threadIdx.x][k] = s[k];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + o][k];
+        __syncthreads();
+    }
+    const double cx = sh[0][0] / n, cy = sh[0][1] / n, cz = sh[0][2] / n;
+    __syncthreads();
+    double r = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        float4 p = p4[i];
+        double dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
+        r += dx * dx + dy * dy + dz * dz;
+    }
+    sh[threadIdx.x][0] = r;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x][0] += sh[threadIdx.x + o][0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = cx;
+        out[1] = cy;
+        out[2] = cz;
+        out[3] = sqrt(sh[0][0] / n);
+    }
+}
+
+// Feature row of sorted point i: offsets to its 16 nearest other points (in
+// ascending order) divided by their RMS length, then (p - c) / R, zero
+// padding to 64.  Rows go to row index perm[i] when by_input is set.
+__global__ void __launch_bounds__(128)
+    k_features(KnnTree T, const double *__restrict__ cR, float *__restrict__ X, int by_input,
+               int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T.n) return;
+    const float4 pi = T.p4[i];
+    int bj[17];
+    knn_search<17, true>(T, F3{pi.x, pi.y, pi.z}, 17, bj, err);
+    float o[48];
+    int cnt = 0;
+    float ss = 0.f;
+#pragma unroll
+    for (int t = 0; t < 17; ++t) {
+        int j = bj[t];
+        if (j < 0 || j == (int)i || cnt == 16) continue;
+        float4 pj = T.p4[j];
+        float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        o[3 * cnt] = dx;
+        o[3 * cnt + 1] = dy;
+        o[3 * cnt + 2] = dz;
+        ss += dx * dx + dy * dy + dz * dz;
+        ++cnt;
+    }
+    float s = cnt > 0 ? sqrtf(ss / cnt) : 0.f;
+    float inv = s > 0.f ? 1.f / s : 0.f;
+    float *row = X + (by_input ? T.perm[i] : i) * 64;
+    for (int k = 0; k < 48; ++k) row[k] = k < 3 * cnt ? o[k] * inv : 0.f;
+    double R = cR[3];
+    row[48] = R > 0.0 ? (float)((pi.x - cR[0]) / R) : 0.f;
+    row[49] = R > 0.0 ? (float)((pi.y - cR[1]) / R) : 0.f;
+    row[50] = R > 0.0 ? (float)((pi.z - cR[2]) / R) : 0.f;
+    for (int k = 51; k < 64; ++k) row[k] = 0.f;
+}
+
+// network outputs (sorted order) -> unit initial normals; an output that is
+// zero or not finite keeps the random normal already in nrm
+__global__ void k_normals_from_y(const float *__restrict__ Y, int64_t n, float4 *nrm)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x = Y[3 * i], y = Y[3 * i + 1], z = Y[3 * i + 2];
+    float l = sqrtf(x * x + y * y + z * z);
+    if (l > 1e-12f && isfinite(l)) nrm[i] = make_float4(x / l, y / l, z / l, 0.f);
+}
+
+cudaError_t launch_features(Ctx *c, float *X, bool by_input, double *cR)
+{
+    k_centroid<<<1, 256, 0, c->stream>>>(c->d_p4, c->n, cR);
+    k_features<<<(unsigned)ceil_div(c->n, 128), 128, 0, c->stream>>>(knn_tree(c), cR, X,
+                                                                      by_input ? 1 : 0, c->d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normals_from_y(Ctx *c, const float *Y)
+{
+    k_normals_from_y<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->stream>>>(Y, c->n, c->d_nrm);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

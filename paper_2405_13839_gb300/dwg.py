@@ -30,6 +30,8 @@ DWG_UPDATE_LEVELSET = 0
 DWG_UPDATE_DIRECT = 1
 DWG_INIT_RANDOM = 0
 DWG_INIT_GIVEN = 1
+DWG_INIT_LEARNED = 2
+MLP_PARAMS = 12675
 DWG_PATH_AUTO = 0
 DWG_PATH_ALLPAIRS = 1
 DWG_PATH_TREE = 2
@@ -93,6 +95,10 @@ def _load() -> ctypes.CDLL:
         "dwg_knn": ([H, P, I64, I, P], I),
         "dwg_profile_step": ([H, P, I, ctypes.POINTER(I)], I),
         "dwg_eval_w_noalloc": ([P, P, P, I64, P, I64, I, F, F, P, P], I),
+        "dwg_mlp_features": ([H, P], I),
+        "dwg_mlp_forward": ([P, P, I64, P, P], I),
+        "dwg_mlp_grad": ([P, P, P, I64, P, ctypes.POINTER(ctypes.c_double), P], I),
+        "dwg_mlp_adam": ([P, P, P, P, I, F, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -210,8 +216,10 @@ def dwg_set_weights(h, a):
 
 
 def dwg_set_init(h, mode, seed=1, normals=None):
+    """normals: (n, 3) initial normals for DWG_INIT_GIVEN, or the flat float32
+    network parameters (12,675) for DWG_INIT_LEARNED."""
     if normals is not None:
-        _check_f32(normals, 3, "normals")
+        _check_f32(normals, 3 if mode == DWG_INIT_GIVEN else None, "normals")
     return _raise(h, _lib.dwg_set_init(h, int(mode), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                        _ptr(normals)))
 
@@ -314,3 +322,26 @@ def dwg_eval_w_noalloc(points, normals, weights, queries, w_out, kernel=DWG_KERN
                                  int(points.shape[0]), _ptr(queries), int(queries.shape[0]),
                                  int(kernel), float(eps), float(screening), _ptr(w_out), stream)
     return _raise(None, rc)
+
+
+def dwg_mlp_features(h, X_out):
+    """Patch feature rows (n, 64) of the handle's points, input order."""
+    return _raise(h, _lib.dwg_mlp_features(h, _ptr(X_out)))
+
+
+def dwg_mlp_forward(params, X, Y, stream=None):
+    return _raise(None, _lib.dwg_mlp_forward(_ptr(params), _ptr(X), int(X.shape[0]), _ptr(Y),
+                                              stream))
+
+
+def dwg_mlp_grad(params, X, T, grad, stream=None):
+    """Fills grad (12,675) with the gradient of the mean squared error; returns the loss."""
+    loss = ctypes.c_double()
+    _raise(None, _lib.dwg_mlp_grad(_ptr(params), _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grad),
+                                   ctypes.byref(loss), stream))
+    return loss.value
+
+
+def dwg_mlp_adam(params, grad, m, v, step, lr, stream=None):
+    return _raise(None, _lib.dwg_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step),
+                                          float(lr), stream))

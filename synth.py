@@ -361,3 +361,81 @@ def workload_batch64(seed=0, n_clouds=64, lo=5_000, hi=500_000):
     return dict(name="batch-64", points=np.ascontiguousarray(np.vstack(pts), dtype=np.float32),
                 normals_true=np.vstack(nrms), offsets=np.array(offs, dtype=np.int64),
                 kinds=kind, sizes=sizes, max_iters=30, tol=0.1)
+
+
+def _rotation(seed, stream):
+    q = normal(seed, stream, 4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def union_of_shapes(n, n_tori=20, n_ellipsoids=20, seed=0, noise=0.0025):
+    """Samples of the boundary of a union of randomly posed tori (R ~ U[0.08,
+    0.2], r ~ U[0.2 R, 0.4 R]) and ellipsoids (semi-axes ~ U[0.04, 0.15]) with
+    centres ~ U[0, 1]^3: area-uniform samples of each primitive, those inside
+    another primitive dropped, subsampled to exactly n; Gaussian noise sigma
+    = noise x bounding-box diagonal; analytic outward normals."""
+    prims = []
+    for k in range(n_tori + n_ellipsoids):
+        c = uniform(seed, 1000 + k, 3)
+        Rm = _rotation(seed, 2000 + k)
+        if k < n_tori:
+            R = 0.08 + 0.12 * uniform(seed, 3000 + k, 1)[0]
+            r = R * (0.2 + 0.2 * uniform(seed, 4000 + k, 1)[0])
+            prims.append(("t", c, Rm, (R, r), 4 * np.pi ** 2 * R * r))
+        else:
+            ax = 0.04 + 0.11 * uniform(seed, 5000 + k, 3)
+            p_ = 1.6075
+            area = 4 * np.pi * ((ax[0] ** p_ * ax[1] ** p_ + ax[0] ** p_ * ax[2] ** p_ +
+                                 ax[1] ** p_ * ax[2] ** p_) / 3) ** (1 / p_)
+            prims.append(("e", c, Rm, ax, area))
+
+    def inside(x, k):
+        kind, c, Rm, prm, _ = prims[k]
+        y = (x - c) @ Rm          # local frame
+        if kind == "t":
+            R, r = prm
+            return (np.sqrt(y[:, 0] ** 2 + y[:, 1] ** 2) - R) ** 2 + y[:, 2] ** 2 < r * r
+        return ((y / prm) ** 2).sum(1) < 1.0
+
+    total_area = sum(p[4] for p in prims)
+    pts, nrms = [], []
+    for k, (kind, c, Rm, prm, area) in enumerate(prims):
+        m = int(np.ceil(1.25 * n * area / total_area)) + 16
+        if kind == "t":
+            R, r = prm
+            q, nt = torus(m, seed=seed * 100 + k, R=R, r=r)
+            q = q.astype(np.float64)
+        else:
+            q, nt = ellipsoid_points(m, prm, seed=seed * 100 + k, stream=60 + k)
+        x = q @ Rm.T + c
+        nn = nt @ Rm.T
+        keep = np.ones(len(x), bool)
+        for j in range(len(prims)):
+            if j != k:
+                keep &= ~inside(x, j)
+        pts.append(x[keep])
+        nrms.append(nn[keep])
+    P = np.vstack(pts)
+    N = np.vstack(nrms)
+    if len(P) < n:
+        raise ValueError("not enough samples; raise the oversampling factor")
+    sel = np.sort(np.argsort(uniform(seed, 6000, len(P)), kind="stable")[:n])
+    P, N = P[sel], N[sel]
+    if noise > 0:
+        diag = bbox_diag(P)
+        P = P + noise * diag * normal(seed, 6001, P.size).reshape(P.shape)
+    return _as_f32(P), N
+
+
+def workload_union15m():
+    """15,000,000 points on a union of 20 tori and 20 ellipsoids, 0.25 % noise;
+    Barnes-Hut path; random initial normals versus the learned warm start."""
+    p, nt = union_of_shapes(15_000_000, seed=0)
+    ext = float((p.max(0) - p.min(0)).max())
+    return dict(name="union-15m", points=p, normals_true=nt,
+                weights=np.ones(len(p), np.float32), eps=0.5 * ext / np.sqrt(len(p)),
+                depth=11, max_iters=30, tol=0.1, theta=0.5)
