@@ -88,6 +88,10 @@ def _load():
             lib.dwgo_tree_gwn.argtypes = [i64, P, P, P, i64, P, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P,
                                           P, P]
+            lib.dwgo_tree_gwn_group.argtypes = [i64, P, P, P, i64, P, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int, ctypes.c_int, P,
+                                                P, P]
             _lib = lib
     return _lib
 
@@ -274,4 +278,29 @@ def tree_gwn(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0.0, la
         out.append(cnt)
     if want_bound:
         out.append(bnd)
+    return tuple(out) if len(out) > 1 else w
+
+
+def tree_gwn_group(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0.0, lam=0.0,
+                   beta=2.0, bucket=16, group=64, grad=True, want_count=False):
+    """Barnes-Hut w (and grad w) with the opening test applied to groups of
+    `group` consecutive queries (a conservative form of Sec. 5.2's test);
+    optional per-query evaluation counts."""
+    lib = _load()
+    p = _d(points, 3)
+    nn = _d(normals, 3)
+    a = _d(weights).ravel()
+    q = _d(queries, 3)
+    w = np.zeros(len(q))
+    g = np.zeros((len(q), 3)) if grad else None
+    cnt = np.zeros(len(q)) if want_count else None
+    lib.dwgo_tree_gwn_group(len(p), _ptr(p), _ptr(nn), _ptr(a), len(q), _ptr(q), int(kernel),
+                            float(eps), float(lam), float(beta), int(bucket), int(group),
+                            _ptr(w), _ptr(g) if grad else None,
+                            _ptr(cnt) if want_count else None)
+    out = [w]
+    if grad:
+        out.append(g)
+    if want_count:
+        out.append(cnt)
     return tuple(out) if len(out) > 1 else w

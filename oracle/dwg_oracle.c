@@ -869,3 +869,110 @@ void dwgo_tree_gwn(int64_t n, const double *p, const double *nrm, const double *
     }
     bh_free(&T);
 }
+
+/*
+ * The same far field with the opening test applied to groups of queries (a
+ * conservative form of the test of Sec. 5.2).  The queries are cut into
+ * groups of `group` consecutive queries in the given order.  A node is far
+ * for a whole group when the squared distance from its float centre c_f to
+ * the group's bounding box (of the float32 query coordinates) exceeds
+ * br2_f, in float32:
+ *   e_x = max(max(lo_x - c_x, c_x - hi_x), 0) for each axis,
+ *   d2 = fma(e_z, e_z, fma(e_y, e_y, e_x * e_x)),  far iff d2 > br2_f.
+ * Far for the box implies far for every query in it, so every far node a
+ * query uses is one the per-query test would accept, or a descendant of one;
+ * since a node's first-order bound A r / (2 pi (d - r)^3) is at least the sum
+ * of its children's, each query's error bound is at most its per-query bound.
+ * Every query of a group sums the same far nodes and the same leaves; a leaf
+ * point equal to the query is skipped as in the exact sum.
+ */
+typedef struct {
+    int64_t *far, *near;
+    int64_t nfar, nnear, cap_far, cap_near;
+} group_lists;
+
+static void push_id(int64_t **v, int64_t *cnt, int64_t *cap, int64_t id)
+{
+    if (*cnt == *cap) {
+        *cap = *cap ? 2 * *cap : 256;
+        *v = (int64_t *)realloc(*v, sizeof(int64_t) * (size_t)*cap);
+    }
+    (*v)[(*cnt)++] = id;
+}
+
+static void bh_group_lists(const bh_tree *T, int64_t node, const float lo[3], const float hi[3],
+                           group_lists *L)
+{
+    if (!(T->A[node] > 0.0)) return; /* empty */
+    const float *c = T->cf + 3 * node;
+    float ex = fmaxf(fmaxf(lo[0] - c[0], c[0] - hi[0]), 0.0f);
+    float ey = fmaxf(fmaxf(lo[1] - c[1], c[1] - hi[1]), 0.0f);
+    float ez = fmaxf(fmaxf(lo[2] - c[2], c[2] - hi[2]), 0.0f);
+    float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+    if (d2 > T->br2[node]) {
+        push_id(&L->far, &L->nfar, &L->cap_far, node);
+        return;
+    }
+    if (node >= T->nleaf) {
+        push_id(&L->near, &L->nnear, &L->cap_near, node);
+        return;
+    }
+    bh_group_lists(T, 2 * node, lo, hi, L);
+    bh_group_lists(T, 2 * node + 1, lo, hi, L);
+}
+
+void dwgo_tree_gwn_group(int64_t n, const double *p, const double *nrm, const double *a,
+                         int64_t m, const double *q, int kernel, double eps, double lambda,
+                         double beta, int bucket, int group, double *w, double *g,
+                         double *count)
+{
+    bh_tree T;
+    bh_build(&T, n, p, nrm, a, bucket, beta);
+    double s = sqrt(lambda > 0 ? lambda : 0.0);
+    int screened = (kernel == 1);
+    int64_t ngroups = (m + group - 1) / group;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t gi = 0; gi < ngroups; ++gi) {
+        int64_t i0 = gi * group, i1 = i0 + group < m ? i0 + group : m;
+        float lo[3], hi[3];
+        for (int k = 0; k < 3; ++k) lo[k] = hi[k] = (float)q[3 * i0 + k];
+        for (int64_t i = i0; i < i1; ++i)
+            for (int k = 0; k < 3; ++k) {
+                float v = (float)q[3 * i + k];
+                if (v < lo[k]) lo[k] = v;
+                if (v > hi[k]) hi[k] = v;
+            }
+        group_lists L = {NULL, NULL, 0, 0, 0, 0};
+        bh_group_lists(&T, 1, lo, hi, &L);
+        for (int64_t i = i0; i < i1; ++i) {
+            const double *qi = q + 3 * i;
+            double wi = 0.0, gq[3] = {0, 0, 0}, ci = 0.0, t, gt[3];
+            for (int64_t f = 0; f < L.nfar; ++f) {
+                int64_t node = L.far[f];
+                dipole_term(T.cf + 3 * node, T.M + 3 * node, qi, screened, eps, s, &t, gt);
+                wi += t;
+                gq[0] += gt[0]; gq[1] += gt[1]; gq[2] += gt[2];
+                ci += 1.0;
+            }
+            for (int64_t e = 0; e < L.nnear; ++e) {
+                int64_t b = L.near[e] - T.nleaf, j0 = b * T.bucket;
+                int64_t j1 = j0 + T.bucket < T.n ? j0 + T.bucket : T.n;
+                for (int64_t j = j0; j < j1; ++j) {
+                    int64_t k = T.order[j];
+                    const double *pk = p + 3 * k;
+                    if (pk[0] == qi[0] && pk[1] == qi[1] && pk[2] == qi[2]) continue;
+                    term(pk, nrm + 3 * k, a[k], qi, screened, eps, s, &t, gt);
+                    wi += t;
+                    gq[0] += gt[0]; gq[1] += gt[1]; gq[2] += gt[2];
+                    ci += 1.0;
+                }
+            }
+            w[i] = wi;
+            if (g) { g[3 * i] = gq[0]; g[3 * i + 1] = gq[1]; g[3 * i + 2] = gq[2]; }
+            if (count) count[i] = ci;
+        }
+        free(L.far);
+        free(L.near);
+    }
+    bh_free(&T);
+}
