@@ -112,6 +112,21 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
                    float tol);
 
 /*
+ * Convergence rule of dwg_orient (tol from dwg_set_params, in degrees).
+ *   DWG_CONV_TOP1 (default): the mean of the ceil(n / 100) largest per-point
+ *     changes of the normal (angles) is at most tol (Sec. 5.1,
+ *     "Model-independent Parameters").
+ *   DWG_CONV_MEAN: the mean over all points of |n_new - n_old| is at most
+ *     2 sin(tol / 2), the chord of an angle of tol (the measure the paper
+ *     plots in Fig. 6).  Noise and outliers keep a few points moving by
+ *     degrees long after the rest has settled, so the top-1 % rule may not
+ *     be met within max_iters on such clouds.
+ */
+#define DWG_CONV_TOP1 0
+#define DWG_CONV_MEAN 1
+int dwg_set_convergence(dwg_handle h, int rule);
+
+/*
  * Discretisation and update rule.
  *   depth: octree depth d in [1, 14] (Sec. 5.1 recommends 8-10 up to 1M
  *          points, 11-13 beyond).
@@ -126,7 +141,8 @@ int dwg_set_update(dwg_handle h, int depth, int knn, int mode);
  *   theta: opening angle in (0, 1]: a node of area-weighted centre c and
  *          radius r stands for its points as one dipole (its area-weighted
  *          normal sum at c) for a query q with |q - c| > r / theta, else it
- *          opens; leaves (16 Morton-consecutive points) are summed exactly.
+ *          opens; leaves (16 Morton-consecutive points by default, see
+ *          dwg_set_tuning) are summed exactly.
  *          The paper opens when |q - c| <= 2.3 r, i.e. theta = 1 / 2.3.
  * Default: AUTO, theta = 0.5.
  */
@@ -288,6 +304,68 @@ int dwg_mlp_grad(const float *params, const float *X, const float *T, int64_t B,
                  double *loss, void *stream);
 int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
                  void *stream);
+
+/*
+ * Autotuner (a project extension; the paper sets its parameters by hand,
+ * Sec. 5.1, and fixes the opening test at 2.3 r, Sec. 5.2).
+ *
+ * dwg_tuning: the performance settings of a handle.
+ *   path:            DWG_PATH_ALLPAIRS or DWG_PATH_TREE (AUTO resolved);
+ *   points_pairs, points_threads:   shape of the exact evaluator of w and
+ *                    grad w at the points (query pairs per thread, CTA size);
+ *   corners_pairs, corners_threads: shape of the exact evaluator of w at the
+ *                    octree-leaf corners;
+ *   tree_leaf:       points per Barnes-Hut leaf (16, 32, 64 or 128);
+ *   theta:           opening angle of the Barnes-Hut path (as dwg_set_tree);
+ *   tree_group:      0: the opening test per query (Sec. 5.2 as printed);
+ *                    1: per group of 64 consecutive queries, against the
+ *                    group's bounding box -- conservative (far for the box is
+ *                    far for each query), so every query's error stays within
+ *                    its per-query bound, and the group shares one walk;
+ *   w_err:           largest |w_tree - w_exact| the tuner saw on its sample
+ *                    (0 for the exact path);
+ *   ms_points, ms_corners: device time of one evaluation at the points and
+ *                    at the corners with these settings (milliseconds);
+ *   from_cache:      1 when dwg_autotune took the settings from its cache.
+ *
+ * dwg_autotune(h, what, w_budget, cache_path, out): measures on the handle's
+ *   own cloud, current normals and stream.  what = DWG_TUNE_SHAPES (every
+ *   compiled evaluator shape, timed with CUDA events, median of three) and/or
+ *   DWG_TUNE_TREE (per leaf size and test form, the largest opening angle in
+ *   {0.9, 0.8, ..., 0.2} whose w differs from the exact all-pairs w by at most
+ *   w_budget (absolute) on a sample of up to 2,048 points and 2,048 corners;
+ *   then the fastest of those).  With path DWG_PATH_AUTO the faster path that meets
+ *   the budget is chosen; with DWG_PATH_TREE and no angle meeting the budget
+ *   the call fails with DWG_ERR_INVALID.  The chosen settings are applied to
+ *   the handle and written to *out (may be NULL).  cache_path (may be NULL):
+ *   a text file with one JSON object per line, keyed by the GPU's name and SM
+ *   count and the problem (sizes, kernel, screening, update rule, requested
+ *   path, budget, what); a matching line is applied without measuring, a new
+ *   result is appended.  Not valid on batch handles (DWG_ERR_STATE).
+ * dwg_get_tuning / dwg_set_tuning: read or apply settings (dwg_set_tuning
+ *   fails with DWG_ERR_INVALID for a shape that is not compiled, a leaf size
+ *   outside the list or theta outside (0, 1]).  Settings change the order of
+ *   floating-point additions, not the definition of the sums.
+ */
+#define DWG_TUNE_SHAPES 1
+#define DWG_TUNE_TREE 2
+
+typedef struct {
+    int path;
+    int points_pairs, points_threads;
+    int corners_pairs, corners_threads;
+    int tree_leaf;
+    float theta;
+    int tree_group;
+    double w_err;
+    double ms_points, ms_corners;
+    int from_cache;
+} dwg_tuning;
+
+int dwg_autotune(dwg_handle h, int what, double w_budget, const char *cache_path,
+                 dwg_tuning *out);
+int dwg_get_tuning(dwg_handle h, dwg_tuning *out);
+int dwg_set_tuning(dwg_handle h, const dwg_tuning *t);
 
 /*
  * k nearest input points (1 <= k <= 32) of m query points (float32 m x 3):

@@ -53,7 +53,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("eps", ctypes.c_double),
                 ("lmbda", ctypes.c_double), ("depth", ctypes.c_int),
                 ("knn", ctypes.c_int), ("mode", ctypes.c_int),
-                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("rule", ctypes.c_int)]
 
 
 def _load():
@@ -207,9 +207,9 @@ def scatter_normals(points, face_rows, k, n_old):
 
 
 def params(kernel=KERNEL_PLAIN, eps=0.0, lam=0.0, depth=6, knn=10, mode=MODE_LEVELSET,
-           max_iters=30, tol=0.1):
+           max_iters=30, tol=0.1, rule=0):
     return _Params(int(kernel), float(eps), float(lam), int(depth), int(knn), int(mode),
-                   int(max_iters), float(tol))
+                   int(max_iters), float(tol), int(rule))
 
 
 def iterate(points, weights, n_old, prm):

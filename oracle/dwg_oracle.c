@@ -509,6 +509,7 @@ typedef struct {
     int mode;        /* 0 level-set update (Eq. 7), 1 point-gradient update */
     int max_iters;
     double tol;      /* degrees */
+    int rule;        /* 0: top-1 % mean change (Sec. 5.1); 1: mean |n_new - n_old| (Fig. 6) */
 } dwgo_params;
 
 /*
@@ -597,7 +598,10 @@ int64_t dwgo_iterate(int64_t n, const double *p, const double *a, const double *
 
 /*
  * Algorithm 1: iterate from n0 until the mean of the largest 1% of the
- * normal changes is <= tol degrees, or max_iters iterations.  Writes the
+ * normal changes is <= tol degrees (rule 0, Sec. 5.1) -- or, with rule 1,
+ * until the mean over all points of |n_new - n_old| (the quantity plotted in
+ * Fig. 6) is <= 2 sin(tol / 2), the chord of tol degrees -- or max_iters
+ * iterations.  Writes the
  * final normals, the number of iterations performed, and per-iteration
  * traces of the iso-value and of the convergence statistic (max_iters
  * entries each, may be NULL).  Returns 1 if converged, 0 otherwise.
@@ -616,11 +620,20 @@ int dwgo_orient(int64_t n, const double *p, const double *a, const double *n0,
         double iso;
         dwgo_iterate(n, p, a, cur, prm, nxt, dth, wp, NULL, &iso);
         double stat = dwgo_top1_mean(n, dth);
+        double mean_dn = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double dx = nxt[3 * i] - cur[3 * i], dy = nxt[3 * i + 1] - cur[3 * i + 1],
+                   dz = nxt[3 * i + 2] - cur[3 * i + 2];
+            mean_dn += sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        mean_dn /= (double)n;
         if (trace_iso) trace_iso[t] = iso;
         if (trace_stat) trace_stat[t] = stat;
         double *sw = cur; cur = nxt; nxt = sw;
         ++t;
-        if (stat <= prm->tol) { conv = 1; break; }
+        int met = prm->rule == 1 ? mean_dn <= 2.0 * sin(prm->tol * DWGO_PI / 360.0)
+                                 : stat <= prm->tol;
+        if (met) { conv = 1; break; }
     }
     memcpy(n_out, cur, sizeof(double) * 3 * (size_t)n);
     *iters = t;

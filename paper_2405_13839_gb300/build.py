@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libdwg.so")
 SOURCES = ["dwg_eval.cu", "dwg_build.cu", "dwg_iter.cu", "dwg_api.cu", "dwg_noalloc.cu", "dwg_tree.cu",
-           "dwg_mlp.cu"]
+           "dwg_mlp.cu", "dwg_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]

@@ -176,27 +176,35 @@ static int ensure_iter_buffers(Ctx *c)
         if (rc) return rc;
     }
     // partial sums for the point evaluation
-    c->nchunks_p = tree ? 1 : eval_chunks(c, c->n, true);
+    const int nch_p = tree ? 1 : eval_chunks(c, c->n, true);
+    if (nch_p != c->nchunks_p) ++c->bufgen;
+    c->nchunks_p = nch_p;
     size_t need_p = (size_t)c->nchunks_p * 8 * (size_t)c->n;
     if (need_p > c->part_p_cap) {
         cudaFree(c->d_part_p);
         c->d_part_p = nullptr;
+        ++c->bufgen;
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_part_p, need_p * sizeof(float)));
         c->part_p_cap = need_p;
     }
     if (c->mode == DWG_UPDATE_LEVELSET) {
+        if (c->built_depth != c->depth) ++c->bufgen;
         int rc = build_discretization(c, c->depth);
         if (rc) return rc;
-        c->nchunks_c = tree ? 1 : eval_chunks(c, c->ncorners, false);
+        const int nch_c = tree ? 1 : eval_chunks(c, c->ncorners, false);
+        if (nch_c != c->nchunks_c) ++c->bufgen;
+        c->nchunks_c = nch_c;
         size_t need_c = (size_t)c->nchunks_c * 2 * (size_t)c->ncorners;
         if (need_c > c->part_c_cap) {
             cudaFree(c->d_part_c);
             c->d_part_c = nullptr;
+            ++c->bufgen;
             DWG_CUDA_TRY(c, cudaMalloc(&c->d_part_c, need_c * sizeof(float)));
             c->part_c_cap = need_c;
         }
     }
     if (c->trace_cap < c->max_iters) {
+        ++c->bufgen;
         cudaFree(c->d_tr_iso);
         cudaFree(c->d_tr_stat);
         cudaFree(c->d_tr_dn);
@@ -327,6 +335,7 @@ static int build_graph(Ctx *c)
         return fail(c, DWG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
     }
     c->graph_valid = true;
+    c->graph_gen = c->bufgen;
     return DWG_OK;
 }
 
@@ -385,6 +394,15 @@ static int prepare_normals(Ctx *c)
         return fail(c, DWG_ERR_CUDA, "pack launch failed");
     return DWG_OK;
 }
+
+namespace dwg {
+int engine_prepare(Ctx *c)
+{
+    int rc = ensure_iter_buffers(c);
+    if (!rc) rc = prepare_normals(c);
+    return rc;
+}
+}  // namespace dwg
 
 static double interactions_per_iter(const Ctx *c)
 {
@@ -581,6 +599,17 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
     return DWG_OK;
 }
 
+int dwg_set_convergence(dwg_handle h, int rule)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (rule != DWG_CONV_TOP1 && rule != DWG_CONV_MEAN)
+        return fail(h, DWG_ERR_INVALID, "rule must be DWG_CONV_TOP1 or DWG_CONV_MEAN");
+    h->conv_rule = rule;
+    invalidate_graph(h);
+    for (dwg_ctx *c : h->clouds) dwg_set_convergence(c, rule);
+    return DWG_OK;
+}
+
 int dwg_set_update(dwg_handle h, int depth, int knn, int mode)
 {
     if (!h) return DWG_ERR_INVALID;
@@ -727,7 +756,7 @@ int dwg_orient(dwg_handle h, float *normals_out, int *iters_out)
     if ((rc = prepare_normals(h))) return rc;
     k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters, h->d_counter);
     LAUNCH_CHECK(h);
-    if (!h->graph_valid && (rc = build_graph(h))) return rc;
+    if ((!h->graph_valid || h->graph_gen != h->bufgen) && (rc = build_graph(h))) return rc;
     cudaEvent_t e0, e1;
     DWG_CUDA_TRY(h, cudaEventCreate(&e0));
     DWG_CUDA_TRY(h, cudaEventCreate(&e1));
@@ -901,6 +930,35 @@ int dwg_eval_gwn(dwg_handle h, const float *queries, int64_t m, float *w_out, fl
     cudaFree(part);
     cudaFree(wg);
     cudaFree(o);
+    return rc;
+}
+
+int dwg_autotune(dwg_handle h, int what, double w_budget, const char *cache_path,
+                 dwg_tuning *out)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "autotune a single-cloud handle");
+    if (what & ~(DWG_TUNE_SHAPES | DWG_TUNE_TREE) || !what)
+        return fail(h, DWG_ERR_INVALID, "what: DWG_TUNE_SHAPES and/or DWG_TUNE_TREE");
+    cudaSetDevice(h->device);
+    int rc = autotune(h, what, w_budget, cache_path, out);
+    invalidate_graph(h);
+    return rc;
+}
+
+int dwg_get_tuning(dwg_handle h, dwg_tuning *out)
+{
+    if (!h || !out) return DWG_ERR_INVALID;
+    tuning_of(h, out);
+    return DWG_OK;
+}
+
+int dwg_set_tuning(dwg_handle h, const dwg_tuning *t)
+{
+    if (!h || !t) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "set the tuning of a single-cloud handle");
+    int rc = apply_tuning(h, t);
+    invalidate_graph(h);
     return rc;
 }
 
@@ -1236,6 +1294,14 @@ static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
     return DWG_OK;
 }
 
+// buffers of every cloud that the batch graph refers to
+static uint64_t batch_gen(const dwg_ctx *h)
+{
+    uint64_t g = h->bufgen;
+    for (const dwg_ctx *c : h->clouds) g = g * 1000003ull + c->bufgen;
+    return g;
+}
+
 static int batch_build_graph(dwg_ctx *h)
 {
     invalidate_graph(h);
@@ -1282,6 +1348,7 @@ static int batch_build_graph(dwg_ctx *h)
         return fail(h, DWG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
     }
     h->graph_valid = true;
+    h->graph_gen = batch_gen(h);
     return DWG_OK;
 }
 
@@ -1362,7 +1429,8 @@ int dwg_orient_batch(dwg_handle h, float *normals_out, int *iters_out)
     cudaSetDevice(h->device);
     int rc = batch_prepare(h);
     if (rc) return rc;
-    if (!h->graph_valid && (rc = batch_build_graph(h))) return rc;
+    if ((!h->graph_valid || h->graph_gen != batch_gen(h)) && (rc = batch_build_graph(h)))
+        return rc;
     cudaEvent_t e0, e1;
     DWG_CUDA_TRY(h, cudaEventCreate(&e0));
     DWG_CUDA_TRY(h, cudaEventCreate(&e1));

@@ -2,9 +2,10 @@
 // number and its gradient (paper Sec. 3, Eq. 2/3; screened variant Sec. 4.2,
 // Eq. 5) on sm_103a.
 //
-// Work decomposition: a CTA of 128 threads owns a tile of 128 * 2P queries
-// (each thread holds P query pairs in registers) and one contiguous chunk of
-// the sources.  Source records (48 bytes: x, y, z, mx, my, mz, each stored
+// Work decomposition: a CTA of NT threads (128 or 256) owns a tile of
+// NT * 2P queries (each thread holds P query pairs in registers) and one
+// contiguous chunk of the sources; (P, NT) is a tuning choice (one
+// instantiation per shape, picked at run time).  Source records (48 bytes: x, y, z, mx, my, mz, each stored
 // twice so that one 64-bit register pair feeds both lanes of a packed
 // f32x2 instruction) stream through a 4-stage shared-memory ring filled by
 // the bulk-copy (TMA) engine with mbarrier completion.  Every thread reads
@@ -29,89 +30,9 @@
 // subtracted after the sum (reduce kernel), which skips it exactly as the
 // definition requires without a per-term test.
 #include "dwg_internal.cuh"
+#include "dwg_packed.cuh"
 
 namespace dwg {
-
-// ---------------------------------------------------------------------------
-// packed FP32x2 arithmetic (PTX ISA 8.6, sm_100 family and later)
-// ---------------------------------------------------------------------------
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float lo, float hi)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b)
-{
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ float rsqrt_mufu(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float ex2_mufu(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ f2 rsqrt2(f2 v)
-{
-    float a, b;
-    upk(v, a, b);
-    return pk(rsqrt_mufu(a), rsqrt_mufu(b));
-}
-__device__ __forceinline__ f2 ex22(f2 v)
-{
-    float a, b;
-    upk(v, a, b);
-    return pk(ex2_mufu(a), ex2_mufu(b));
-}
-// (hi, lo) += t with Knuth's two-sum, both lanes at once
-__device__ __forceinline__ void two_sum_acc(f2 &hi, f2 &lo, f2 t)
-{
-    f2 s = add2(hi, t);
-    f2 bb = sub2(s, hi);
-    f2 e = add2(sub2(hi, sub2(s, bb)), sub2(t, bb));
-    lo = add2(lo, e);
-    hi = s;
-}
-__device__ __forceinline__ void two_sum1(float &hi, float &lo, float t)
-{
-    float s = __fadd_rn(hi, t);
-    float bb = __fsub_rn(s, hi);
-    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
-    lo = __fadd_rn(lo, e);
-    hi = s;
-}
 
 // ---------------------------------------------------------------------------
 // mbarrier + bulk copy (inline PTX), with bounded waits
@@ -166,11 +87,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // ---------------------------------------------------------------------------
 // the evaluation kernel
 // ---------------------------------------------------------------------------
-constexpr int kEvalThreads = 128;
+constexpr int kEvalThreads = 128;  // CTA size of the default shapes
 constexpr int kStages = 4;
 
 // One CTA's work: query tile `qtile` against source chunk `chunk`.
-template <int P, bool GRAD, bool SCREENED>
+template <int P, int NT, bool GRAD, bool SCREENED>
 __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t ntiles_total,
                                           const float4 *__restrict__ q, int64_t m,
                                           int tiles_per_chunk, float *__restrict__ part,
@@ -180,7 +101,7 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
     constexpr int T = kSrcTile;
     constexpr int TILE_FLOATS = T * kSrcFloats;
     constexpr uint32_t TILE_BYTES = TILE_FLOATS * 4;
-    constexpr int QB = kEvalThreads * 2 * P;
+    constexpr int QB = NT * 2 * P;
     constexpr int NA = GRAD ? 4 : 1;
 
     __shared__ __align__(128) float sbuf[kStages][TILE_FLOATS];
@@ -210,8 +131,8 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
     f2 qx[P], qy[P], qz[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        int64_t i0 = min(qbase + (int64_t)(2 * p) * kEvalThreads, m - 1);
-        int64_t i1 = min(qbase + (int64_t)(2 * p + 1) * kEvalThreads, m - 1);
+        int64_t i0 = min(qbase + (int64_t)(2 * p) * NT, m - 1);
+        int64_t i1 = min(qbase + (int64_t)(2 * p + 1) * NT, m - 1);
         float4 a = q[i0], b = q[i1];
         qx[p] = pk(a.x, b.x);
         qy[p] = pk(a.y, b.y);
@@ -342,7 +263,7 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
     for (int p = 0; p < P; ++p) {
 #pragma unroll
         for (int lane = 0; lane < 2; ++lane) {
-            int64_t i = qbase + (int64_t)(2 * p + lane) * kEvalThreads;
+            int64_t i = qbase + (int64_t)(2 * p + lane) * NT;
             if (i >= m) continue;
             float vals[NA][2];
             float a, b;
@@ -367,14 +288,14 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
     }
 }
 
-template <int P, bool GRAD, bool SCREENED>
-__global__ void __launch_bounds__(kEvalThreads)
+template <int P, int NT, bool GRAD, bool SCREENED>
+__global__ void __launch_bounds__(NT)
     k_gwn(const float *__restrict__ src, int64_t ntiles_total, const float4 *__restrict__ q,
           int64_t m, int tiles_per_chunk, float *__restrict__ part, int64_t stride,
           EvalParams ep, int *__restrict__ err)
 {
-    gwn_block<P, GRAD, SCREENED>(src, ntiles_total, q, m, tiles_per_chunk, part, stride, ep, err,
-                                 (int64_t)blockIdx.x, (int)blockIdx.y);
+    gwn_block<P, NT, GRAD, SCREENED>(src, ntiles_total, q, m, tiles_per_chunk, part, stride, ep,
+                                     err, (int64_t)blockIdx.x, (int)blockIdx.y);
 }
 
 // Many clouds in one launch: CTA b runs work item items[b] of its cloud;
@@ -387,8 +308,8 @@ __global__ void __launch_bounds__(kEvalThreads)
     const GwnItem it = items[blockIdx.x];
     const GwnCloud &C = clouds[it.cloud];
     if (C.st && cloud_idle(C.st)) return;
-    gwn_block<P, GRAD, SCREENED>(C.src, C.ntiles, C.q, C.m, C.tpc, C.part, C.stride, C.ep, err,
-                                 (int64_t)it.qtile, it.chunk);
+    gwn_block<P, kEvalThreads, GRAD, SCREENED>(C.src, C.ntiles, C.q, C.m, C.tpc, C.part, C.stride,
+                                               C.ep, err, (int64_t)it.qtile, it.chunk);
 }
 
 // ---------------------------------------------------------------------------
@@ -476,68 +397,109 @@ static int pick_chunks(int64_t qtiles, int64_t ntiles_src, int slots)
     return best;
 }
 
-template <int P, bool GRAD, bool SCREENED>
-static int resident_slots(int dev)
+// ---------------------------------------------------------------------------
+// evaluator shapes: (query pairs per thread P, CTA size NT); the tuner picks
+// one per kind (w and gradient at the points, w only at the corners)
+// ---------------------------------------------------------------------------
+typedef void (*GwnKernel)(const float *, int64_t, const float4 *, int64_t, int, float *, int64_t,
+                          EvalParams, int *);
+struct GwnVariant {
+    int p, nt;
+    GwnKernel k[2];  // plain, screened
+};
+#define DWG_GWN_VARIANT(P, NT, G) \
+    {P, NT, {k_gwn<P, NT, G, false>, k_gwn<P, NT, G, true>}}
+static const GwnVariant kVarGrad[] = {
+    DWG_GWN_VARIANT(2, 128, true), DWG_GWN_VARIANT(1, 128, true), DWG_GWN_VARIANT(3, 128, true),
+    DWG_GWN_VARIANT(1, 256, true), DWG_GWN_VARIANT(2, 256, true)};
+static const GwnVariant kVarW[] = {
+    DWG_GWN_VARIANT(4, 128, false), DWG_GWN_VARIANT(2, 128, false), DWG_GWN_VARIANT(3, 128, false),
+    DWG_GWN_VARIANT(6, 128, false), DWG_GWN_VARIANT(2, 256, false), DWG_GWN_VARIANT(3, 256, false),
+    DWG_GWN_VARIANT(4, 256, false)};
+#undef DWG_GWN_VARIANT
+constexpr int kNumVarGrad = (int)(sizeof(kVarGrad) / sizeof(kVarGrad[0]));
+constexpr int kNumVarW = (int)(sizeof(kVarW) / sizeof(kVarW[0]));
+
+int eval_variant_count(bool grad) { return grad ? kNumVarGrad : kNumVarW; }
+
+void eval_variant_shape(bool grad, int v, int *p, int *nt)
 {
-    static int cached[64] = {0};
+    const GwnVariant &V = grad ? kVarGrad[v] : kVarW[v];
+    *p = V.p;
+    *nt = V.nt;
+}
+
+static const GwnVariant &variant(bool grad, int v)
+{
+    if (grad) return kVarGrad[(v >= 0 && v < kNumVarGrad) ? v : 0];
+    return kVarW[(v >= 0 && v < kNumVarW) ? v : 0];
+}
+
+// resident CTAs of a variant on the whole device (cached per device)
+static int variant_slots(bool grad, int v, bool scr, int dev)
+{
+    static int cached[2][2][8][64] = {};
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!cached[dev]) {
+    if (v < 0 || v >= 8) v = 0;
+    int &slot = cached[grad][scr][v][dev];
+    if (!slot) {
+        const GwnVariant &V = variant(grad, v);
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gwn<P, GRAD, SCREENED>,
-                                                          kEvalThreads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.k[scr ? 1 : 0], V.nt, 0) !=
+                cudaSuccess ||
             nb < 1) {
             cudaGetLastError();
             nb = 1;
         }
-        cached[dev] = nb * num_sms(dev);
+        slot = nb * num_sms(dev);
     }
-    return cached[dev];
+    return slot;
 }
 
-template <int P, bool GRAD>
-static cudaError_t launch_gwn_t(const Ctx *c, const float4 *q, int64_t m, int nchunks,
-                                float *part, int64_t stride)
+static bool screened_of(const Ctx *c) { return c->kernel == DWG_KERNEL_SCREENED && c->lambda > 0.f; }
+
+int eval_chunks_variant(const Ctx *c, int64_t m, bool grad, int v)
 {
+    const GwnVariant &V = variant(grad, v);
+    int64_t QB = (int64_t)V.nt * 2 * V.p;
+    return pick_chunks(ceil_div(m, QB), c->npad / kSrcTile,
+                       variant_slots(grad, v, screened_of(c), c->device));
+}
+
+int eval_chunks(const Ctx *c, int64_t m, bool grad)
+{
+    return eval_chunks_variant(c, m, grad, grad ? c->var_grad : c->var_w);
+}
+
+int eval_launch_variant(Ctx *c, const float4 *q, int64_t m, bool grad, int v, int nchunks,
+                        float *part, int64_t stride)
+{
+    const GwnVariant &V = variant(grad, v);
     EvalParams ep = make_eval_params(c);
-    constexpr int QB = kEvalThreads * 2 * P;
+    int64_t QB = (int64_t)V.nt * 2 * V.p;
     int64_t qtiles = ceil_div(m, QB);
     int64_t ntiles = c->npad / kSrcTile;
     int tpc = (int)ceil_div(ntiles, nchunks);
     dim3 grid((unsigned)qtiles, (unsigned)nchunks);
-    if (ep.screened)
-        k_gwn<P, GRAD, true><<<grid, kEvalThreads, 0, c->stream>>>(c->d_src, ntiles, q, m, tpc,
-                                                                   part, stride, ep, c->d_err);
-    else
-        k_gwn<P, GRAD, false><<<grid, kEvalThreads, 0, c->stream>>>(c->d_src, ntiles, q, m, tpc,
-                                                                    part, stride, ep, c->d_err);
-    return cudaGetLastError();
-}
-
-constexpr int kPGrad = 2;   // query pairs per thread, gradient kernel
-constexpr int kPW = 4;      // query pairs per thread, w-only kernel
-
-int eval_chunks(const Ctx *c, int64_t m, bool grad)
-{
-    int QB = kEvalThreads * 2 * (grad ? kPGrad : kPW);
-    bool scr = c->kernel == DWG_KERNEL_SCREENED && c->lambda > 0.f;
-    int slots = grad ? (scr ? resident_slots<kPGrad, true, true>(c->device)
-                            : resident_slots<kPGrad, true, false>(c->device))
-                     : (scr ? resident_slots<kPW, false, true>(c->device)
-                            : resident_slots<kPW, false, false>(c->device));
-    return pick_chunks(ceil_div(m, QB), c->npad / kSrcTile, slots);
-}
-
-int eval_launch(Ctx *c, const float4 *q, int64_t m, bool grad, int nchunks, float *part,
-                int64_t stride)
-{
-    cudaError_t e = grad ? launch_gwn_t<kPGrad, true>(c, q, m, nchunks, part, stride)
-                         : launch_gwn_t<kPW, false>(c, q, m, nchunks, part, stride);
+    V.k[ep.screened ? 1 : 0]<<<grid, V.nt, 0, c->stream>>>(c->d_src, ntiles, q, m, tpc, part,
+                                                             stride, ep, c->d_err);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         c->err = std::string("gwn kernel launch: ") + cudaGetErrorString(e);
         return DWG_ERR_CUDA;
     }
     return DWG_OK;
 }
+
+int eval_launch(Ctx *c, const float4 *q, int64_t m, bool grad, int nchunks, float *part,
+                int64_t stride)
+{
+    return eval_launch_variant(c, q, m, grad, grad ? c->var_grad : c->var_w, nchunks, part,
+                               stride);
+}
+
+constexpr int kPGrad = 2;   // query pairs per thread, gradient kernel (batched launches)
+constexpr int kPW = 4;      // query pairs per thread, w-only kernel (batched and raw launches)
 
 // ---------------------------------------------------------------------------
 // reduce: combine chunk partials in chunk order; for gradients add back the
@@ -681,7 +643,7 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
 int gwn_w_chunks_raw(int64_t m, int64_t npad, int device)
 {
     return pick_chunks(ceil_div(m, kEvalThreads * 2 * kPW), npad / kSrcTile,
-                       resident_slots<kPW, false, false>(device));
+                       variant_slots(false, 0, false, device));
 }
 
 cudaError_t launch_gwn_w_raw(const float *src, int64_t npad, const float4 *q, int64_t m,
@@ -693,11 +655,11 @@ cudaError_t launch_gwn_w_raw(const float *src, int64_t npad, const float4 *q, in
     int tpc = (int)ceil_div(ntiles, nchunks);
     dim3 grid((unsigned)ceil_div(m, QB), (unsigned)nchunks);
     if (ep.screened)
-        k_gwn<kPW, false, true><<<grid, kEvalThreads, 0, s>>>(src, ntiles, q, m, tpc, part, m, ep,
-                                                              err);
+        k_gwn<kPW, kEvalThreads, false, true>
+            <<<grid, kEvalThreads, 0, s>>>(src, ntiles, q, m, tpc, part, m, ep, err);
     else
-        k_gwn<kPW, false, false><<<grid, kEvalThreads, 0, s>>>(src, ntiles, q, m, tpc, part, m,
-                                                               ep, err);
+        k_gwn<kPW, kEvalThreads, false, false>
+            <<<grid, kEvalThreads, 0, s>>>(src, ntiles, q, m, tpc, part, m, ep, err);
     return cudaGetLastError();
 }
 

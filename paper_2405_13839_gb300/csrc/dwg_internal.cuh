@@ -89,6 +89,7 @@ struct Ctx {
     // parameters
     int kernel = DWG_KERNEL_PLAIN;
     float eps = 0.f, lambda = 0.f, tol = 0.1f;
+    int conv_rule = DWG_CONV_TOP1;
     int max_iters = 30;
     int depth = 8, knn = 10, mode = DWG_UPDATE_LEVELSET;
     int init_mode = DWG_INIT_RANDOM;
@@ -125,6 +126,11 @@ struct Ctx {
     unsigned long long *d_acc = nullptr; // n x 3 fixed-point face sums
     double acc_scale = 1.0;
 
+    // evaluator shapes (indices into the variant tables of dwg_eval.cu) and
+    // what the last autotune measured
+    int var_grad = 0, var_w = 0;
+    double tune_w_err = 0.0, tune_ms_points = 0.0, tune_ms_corners = 0.0;
+
     // evaluation scratch: partial sums per source chunk
     int nchunks_p = 1, nchunks_c = 1;
     float *d_part_p = nullptr;   // [nchunks][4][2][n]
@@ -141,18 +147,23 @@ struct Ctx {
     int trace_cap = 0;
     int *d_err = nullptr;
 
-    // Barnes-Hut far field over the bucket tree
+    // Barnes-Hut far field over a binary tree of Morton ranges
     int path = DWG_PATH_AUTO;
     float tree_beta = 2.0f;            // 1 / opening angle
+    int tree_leaf = 16;                // points per tree leaf (16, 32, 64 or 128)
+    int tree_group = 0;                // 1: opening test per 64-query group
+    int tree_levels = 0;               // 2^tree_levels leaves
     bool tree_built = false;
     double tree_beta_set = -1.0;
     double *d_tree_A = nullptr, *d_tree_C = nullptr, *d_tree_R = nullptr, *d_tree_M = nullptr;
     float4 *d_tree_rec = nullptr, *d_tree_mrec = nullptr;
     unsigned long long *d_counter = nullptr;  // kernel evaluations of the tree path
 
-    // graph
+    // graph; bufgen counts reallocations of buffers a captured graph refers
+    // to, graph_gen is the count the graph was captured with
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_valid = false;
+    uint64_t bufgen = 0, graph_gen = ~0ull;
 
     // last results
     dwg_stats stats{};
@@ -234,6 +245,13 @@ EvalParams make_eval_params(const Ctx *c);
 int eval_chunks(const Ctx *c, int64_t m, bool grad);
 int eval_launch(Ctx *c, const float4 *q, int64_t m, bool grad, int nchunks, float *part,
                 int64_t stride);
+// evaluator shapes for the tuner: count, (P, NT) of variant v, chunking and
+// launch of a given variant
+int eval_variant_count(bool grad);
+void eval_variant_shape(bool grad, int v, int *p, int *nt);
+int eval_chunks_variant(const Ctx *c, int64_t m, bool grad, int v);
+int eval_launch_variant(Ctx *c, const float4 *q, int64_t m, bool grad, int v, int nchunks,
+                        float *part, int64_t stride);
 cudaError_t launch_pack_sources(const float4 *p4, const float4 *nrm, int64_t n, int64_t npad,
                                 float *src, cudaStream_t s);
 cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t m,
@@ -254,8 +272,17 @@ cudaError_t launch_reduce_w_raw(const float *part, int nchunks, int64_t m, float
 // dwg_api.cu
 void set_global_error(const std::string &msg);
 bool use_tree(const Ctx *c);
+// iteration buffers, spatial structures and source records of the current
+// normals, as before an iteration
+int engine_prepare(Ctx *c);
+
+// dwg_tune.cu
+void tuning_of(const Ctx *c, dwg_tuning *t);
+int apply_tuning(Ctx *c, const dwg_tuning *t);
+int autotune(Ctx *c, int what, double w_budget, const char *cache_path, dwg_tuning *out);
 
 // dwg_tree.cu
+void free_tree(Ctx *c);
 int build_tree(Ctx *c);
 int tree_records(Ctx *c);
 cudaError_t launch_tree_moments(Ctx *c);

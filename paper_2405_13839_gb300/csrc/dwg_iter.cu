@@ -547,7 +547,7 @@ __device__ void find_bin(const unsigned *hist, int nb, unsigned k, unsigned *war
 }
 
 __global__ void __launch_bounds__(kSelThreads)
-    k_select(const float *__restrict__ dtheta, int64_t n, float tol, IterState *st,
+    k_select(const float *__restrict__ dtheta, int64_t n, float tol, int rule, IterState *st,
              const double *__restrict__ dn_blocks, int ndn, double *tr_iso, double *tr_stat,
              double *tr_dn, long long *tr_faces, cudaGraphConditionalHandle cond, int use_cond)
 {
@@ -615,7 +615,11 @@ __global__ void __launch_bounds__(kSelThreads)
         }
         it += 1;
         st->iter = it;
-        int done = stat <= (double)tol;
+        // rule 0: mean of the largest 1 % of the changes <= tol degrees (Sec. 5.1);
+        // rule 1: mean |n_new - n_old| over all points <= 2 sin(tol / 2), the
+        // chord of tol degrees (the measure plotted in Fig. 6)
+        const double chord = 2.0 * sin((double)tol * (kPi / 360.0));
+        int done = rule == 1 ? (sh[0] / (double)n <= chord) : (stat <= (double)tol);
         st->done = done;
         if (use_cond) cudaGraphSetConditional(cond, (!done && it < st->max_iters) ? 1u : 0u);
     }
@@ -720,7 +724,7 @@ cudaError_t launch_normal_update(Ctx *c)
 
 cudaError_t launch_select(Ctx *c, cudaGraphConditionalHandle cond, int use_cond)
 {
-    k_select<<<1, kSelThreads, 0, c->stream>>>(c->d_dtheta, c->n, c->tol, c->d_state,
+    k_select<<<1, kSelThreads, 0, c->stream>>>(c->d_dtheta, c->n, c->tol, c->conv_rule, c->d_state,
                                                c->d_dn_blocks, (int)ceil_div(c->n, 256),
                                                c->d_tr_iso, c->d_tr_stat, c->d_tr_dn,
                                                c->d_tr_faces, cond, use_cond);

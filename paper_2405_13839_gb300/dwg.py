@@ -32,6 +32,8 @@ DWG_INIT_RANDOM = 0
 DWG_INIT_GIVEN = 1
 DWG_INIT_LEARNED = 2
 MLP_PARAMS = 12675
+DWG_CONV_TOP1 = 0
+DWG_CONV_MEAN = 1
 DWG_PATH_AUTO = 0
 DWG_PATH_ALLPAIRS = 1
 DWG_PATH_TREE = 2
@@ -56,6 +58,20 @@ class dwg_stats(ctypes.Structure):
                 ("interactions_eval", ctypes.c_double)]
 
 
+class dwg_tuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("points_pairs", ctypes.c_int),
+                ("points_threads", ctypes.c_int), ("corners_pairs", ctypes.c_int),
+                ("corners_threads", ctypes.c_int), ("tree_leaf", ctypes.c_int),
+                ("theta", ctypes.c_float), ("tree_group", ctypes.c_int),
+                ("w_err", ctypes.c_double),
+                ("ms_points", ctypes.c_double), ("ms_corners", ctypes.c_double),
+                ("from_cache", ctypes.c_int)]
+
+
+DWG_TUNE_SHAPES = 1
+DWG_TUNE_TREE = 2
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -77,6 +93,7 @@ def _load() -> ctypes.CDLL:
         "dwg_set_stream": ([H, P], I),
         "dwg_set_params": ([H, I, F, F, I, F], I),
         "dwg_set_update": ([H, I, I, I], I),
+        "dwg_set_convergence": ([H, I], I),
         "dwg_set_weights": ([H, P], I),
         "dwg_set_tree": ([H, I, F], I),
         "dwg_create_batch": ([P, P, I, ctypes.POINTER(H)], I),
@@ -99,6 +116,9 @@ def _load() -> ctypes.CDLL:
         "dwg_mlp_forward": ([P, P, I64, P, P], I),
         "dwg_mlp_grad": ([P, P, P, I64, P, ctypes.POINTER(ctypes.c_double), P], I),
         "dwg_mlp_adam": ([P, P, P, P, I, F, P], I),
+        "dwg_autotune": ([H, I, ctypes.c_double, ctypes.c_char_p, ctypes.POINTER(dwg_tuning)], I),
+        "dwg_get_tuning": ([H, ctypes.POINTER(dwg_tuning)], I),
+        "dwg_set_tuning": ([H, ctypes.POINTER(dwg_tuning)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -200,6 +220,10 @@ def dwg_set_stream(h, stream):
 def dwg_set_params(h, kernel, eps, screening, max_iters, tol):
     return _raise(h, _lib.dwg_set_params(h, int(kernel), float(eps), float(screening),
                                          int(max_iters), float(tol)))
+
+
+def dwg_set_convergence(h, rule):
+    return _raise(h, _lib.dwg_set_convergence(h, int(rule)))
 
 
 def dwg_set_update(h, depth, knn=10, mode=DWG_UPDATE_LEVELSET):
@@ -345,3 +369,32 @@ def dwg_mlp_grad(params, X, T, grad, stream=None):
 def dwg_mlp_adam(params, grad, m, v, step, lr, stream=None):
     return _raise(None, _lib.dwg_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step),
                                           float(lr), stream))
+
+
+def _tuning_dict(t):
+    return {name: getattr(t, name) for name, _ in dwg_tuning._fields_}
+
+
+def dwg_autotune(h, what=DWG_TUNE_SHAPES | DWG_TUNE_TREE, w_budget=1e-3, cache_path=None):
+    """Measure and apply the fastest settings (dict of dwg_tuning's fields)."""
+    t = dwg_tuning()
+    cp = None if cache_path is None else os.fsencode(cache_path)
+    _raise(h, _lib.dwg_autotune(h, int(what), float(w_budget), cp, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def dwg_get_tuning(h):
+    t = dwg_tuning()
+    _raise(h, _lib.dwg_get_tuning(h, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def dwg_set_tuning(h, **settings):
+    """Apply settings; fields not given keep their current values."""
+    t = dwg_tuning()
+    _raise(h, _lib.dwg_get_tuning(h, ctypes.byref(t)))
+    for k, v in settings.items():
+        if k not in dict(dwg_tuning._fields_):
+            raise KeyError(k)
+        setattr(t, k, v)
+    return _raise(h, _lib.dwg_set_tuning(h, ctypes.byref(t)))

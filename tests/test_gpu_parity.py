@@ -279,6 +279,35 @@ def test_orient_sphere_matches_oracle_and_analytic(dwglib, oracle_mod, handle):
     assert np.array_equal(out, out2)
 
 
+def test_orient_mean_change_rule_matches_oracle(dwglib, oracle_mod, handle):
+    """DWG_CONV_MEAN stops at the oracle's iteration (mean |n_new - n_old| <=
+    chord of tol) and gives its normals."""
+    n = 1200
+    p, nt = synth.torus(n, seed=4)
+    area = 4 * np.pi ** 2 * 0.3
+    a = np.full(n, area / n, np.float32)
+    eps = synth.default_eps(area, n)
+    n0 = synth.random_unit_normals(n, seed=2).astype(np.float32)
+    h = handle(p)
+    dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_params(h, 1, eps, 10.0, 40, 0.5)
+    dwglib.dwg_set_update(h, 5, 10, dwglib.DWG_UPDATE_LEVELSET)
+    dwglib.dwg_set_convergence(h, dwglib.DWG_CONV_MEAN)
+    dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, n0)
+    out = np.zeros((n, 3), np.float32)
+    rc, iters = dwglib.dwg_orient(h, out)
+    r = oracle_mod.orient(p, a, n0, oracle_mod.params(kernel=1, lam=10.0, eps=eps, depth=5,
+                                                      max_iters=40, tol=0.5, rule=1))
+    assert r["converged"] and rc == dwglib.DWG_OK
+    assert abs(iters - r["iters"]) <= 2, (iters, r["iters"])
+    assert agreement(out, r["normals"]) >= 0.995
+    tr = dwglib.dwg_get_trace(h)
+    chord = 2 * np.sin(np.radians(0.5) / 2)
+    assert tr["mean_dn"][-1] <= chord and np.all(tr["mean_dn"][:-1] > chord)
+    with pytest.raises(dwglib.DWGError):
+        dwglib.dwg_set_convergence(h, 7)
+
+
 def test_orient_torus_agrees_with_analytic(dwglib, handle):
     n = 20000
     p, nt = synth.torus(n, seed=0)

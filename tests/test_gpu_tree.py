@@ -37,6 +37,7 @@ def test_tree_eval_matches_oracle_tree(dwglib, oracle_mod, handle, n, kernel, la
     dwglib.dwg_set_weights(h, a)
     dwglib.dwg_set_params(h, kernel, eps, lam, 30, 0.1)
     dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, theta)
+    dwglib.dwg_set_tuning(h, tree_group=0)  # the per-query test of Sec. 5.2
     dwglib.dwg_set_normals(h, nrm)
     sel = np.unique((synth.uniform(7, n, min(n, 1500)) * n).astype(np.int64))
     q = np.vstack([p[sel], synth.uniform_box(500, [-1.5, -1.5, -0.6], [1.5, 1.5, 0.6],
@@ -90,3 +91,77 @@ def test_tree_orientation_torus(dwglib, handle):
     st = dwglib.dwg_get_stats(h)
     # the far field does the work of many points
     assert st["interactions"] < 0.5 * iters * (n * n + st["n_corners"] * n)
+
+
+@pytest.mark.parametrize("n", [1, 33, 1000, 5000, 40000])
+@pytest.mark.parametrize("kernel,lam,theta,leaf", [(0, 0.0, 0.5, 16), (0, 0.0, 1 / 2.3, 32),
+                                                   (1, 10.0, 0.5, 16), (1, 100.0, 0.7, 64)])
+def test_group_tree_matches_oracle_group_tree(dwglib, oracle_mod, handle, n, kernel, lam, theta,
+                                              leaf):
+    """Group form of the opening test (64 consecutive queries share the test
+    against their bounding box): the oracle's group tree makes the same
+    decisions (equal evaluation counts) and the values agree to the exact
+    path's tolerances."""
+    p, _ = synth.torus(n, seed=n + 5, noise=0.004)
+    a = np.full(n, 4 * np.pi ** 2 * 0.3 / n, np.float32)
+    nrm = synth.random_unit_normals(n, seed=n + 1).astype(np.float32)
+    eps = synth.default_eps(4 * np.pi ** 2 * 0.3, n)
+    h = handle(p)
+    dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_params(h, kernel, eps, lam, 30, 0.1)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, theta)
+    dwglib.dwg_set_tuning(h, tree_group=1, tree_leaf=leaf)
+    dwglib.dwg_set_normals(h, nrm)
+    # Morton-ordered points (compact groups) then scattered box queries
+    order = oracle_mod.morton_order(p)
+    sel = order[::max(1, n // 1500)]
+    q = np.vstack([p[sel], synth.uniform_box(500, [-1.5, -1.5, -0.6], [1.5, 1.5, 0.6],
+                                             seed=n + 2)]).astype(np.float32)
+    w = np.zeros(len(q), np.float32)
+    g = np.zeros((len(q), 3), np.float32)
+    dwglib.dwg_eval_gwn(h, q, w, g)
+    cnt_gpu = dwglib.dwg_get_stats(h)["interactions_eval"]
+    beta = float(np.float32(1) / np.float32(theta))
+    wo, go, cnt = oracle_mod.tree_gwn_group(p, nrm, a, q, kernel=kernel, eps=eps, lam=lam,
+                                            beta=beta, bucket=leaf, group=64, want_count=True)
+    check_wg(w, g, wo, go, s_g(p, nrm, a, q, eps))
+    assert cnt_gpu == cnt.sum() + len(sel)
+
+
+def test_group_tree_within_the_per_query_error_bound(dwglib, oracle_mod, handle):
+    """Plain kernel: |w_group - w_exact| <= the per-query first-order bound
+    (the group test only opens more nodes) plus the exact path's 1e-5."""
+    n = 30000
+    p, nt = synth.torus(n, seed=9, noise=0.003)
+    a = np.full(n, 4 * np.pi ** 2 * 0.3 / n, np.float32)
+    eps = synth.default_eps(4 * np.pi ** 2 * 0.3, n)
+    h = handle(p)
+    dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_params(h, 0, eps, 0.0, 30, 0.1)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+    dwglib.dwg_set_tuning(h, tree_group=1)
+    nrm = nt.astype(np.float32)
+    dwglib.dwg_set_normals(h, nrm)
+    q = p[oracle_mod.morton_order(p)[::20]]
+    w = np.zeros(len(q), np.float32)
+    dwglib.dwg_eval_gwn(h, q, w)
+    we = oracle_mod.gwn(p, nrm, a, q, eps=eps, grad=False)
+    _, bnd = oracle_mod.tree_gwn(p, nrm, a, q, eps=eps, beta=2.0, grad=False, want_bound=True)
+    assert np.all(np.abs(w - we) <= bnd + 1e-5)
+
+
+@pytest.mark.parametrize("group", [0, 1])
+def test_tree_orientation_torus_both_tests(dwglib, handle, group):
+    n = 60000
+    p, nt = synth.torus(n, seed=0)
+    area = 4 * np.pi ** 2 * 0.3
+    h = handle(p)
+    dwglib.dwg_set_weights(h, np.full(n, area / n, np.float32))
+    dwglib.dwg_set_params(h, 1, synth.default_eps(area, n), 10.0, 40, 0.1)
+    dwglib.dwg_set_update(h, 7, 10, dwglib.DWG_UPDATE_LEVELSET)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+    dwglib.dwg_set_tuning(h, tree_group=group)
+    dwglib.dwg_set_init(h, dwglib.DWG_INIT_RANDOM, 1)
+    out = np.zeros((n, 3), np.float32)
+    rc, iters = dwglib.dwg_orient(h, out)
+    assert agreement(out, nt) >= 0.999, (agreement(out, nt), iters)

@@ -55,3 +55,31 @@ def test_point_gradient_update_stalls(oracle_mod):
                             mode=oracle_mod.MODE_DIRECT)
     r = oracle_mod.orient(W["points"], W["weights"], n0, prm)
     assert agreement(r["normals"], W["normals_true"]) < 0.9
+
+
+def test_mean_change_rule_stops_at_the_first_small_mean_change(oracle_mod):
+    """Rule 1 stops after the first iteration whose mean |n_new - n_old| (the
+    quantity of Fig. 6) is at most the chord 2 sin(tol / 2); replaying the
+    iterations one by one finds the same stopping point."""
+    n = 1200
+    p, nt = synth.torus(n, seed=4)
+    area = 4 * np.pi ** 2 * 0.3
+    a = np.full(n, area / n)
+    n0 = synth.random_unit_normals(n, seed=2)
+    tol = 0.5
+    prm = oracle_mod.params(kernel=1, lam=10.0, eps=synth.default_eps(area, n), depth=5,
+                            max_iters=40, tol=tol, rule=1)
+    r = oracle_mod.orient(p, a, n0, prm)
+    chord = 2 * np.sin(np.radians(tol) / 2)
+    cur = n0.copy()
+    stop = None
+    for t in range(1, 41):
+        nxt = oracle_mod.iterate(p, a, cur, prm)["normals"]
+        md = np.mean(np.linalg.norm(nxt - cur, axis=1))
+        cur = nxt
+        if md <= chord:
+            stop = t
+            break
+    assert stop is not None and r["iters"] == stop and r["converged"]
+    np.testing.assert_array_equal(r["normals"], cur)
+    assert agreement(r["normals"], nt) >= 0.99
