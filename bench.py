@@ -196,7 +196,7 @@ def tune(dwg, h, W, args):
         return dwg.dwg_autotune(h, dwg.DWG_TUNE_SHAPES, 1e-3, None)
     n = len(W["points"])
     nt = np.asarray(W["normals_true"], np.float32).copy()
-    bad = np.linalg.norm(nt, axis=1) == 0
+    bad = ~(np.linalg.norm(nt, axis=1) > 0)   # outliers: no analytic normal
     nt[bad] = synth.random_unit_normals(int(bad.sum()), seed=3).astype(np.float32)
     dwg.dwg_set_normals(h, nt)
     sel = (synth.uniform(4, 5, 2048) * n).astype(np.int64)
@@ -242,6 +242,32 @@ def warm_start_compare(dwg, torch, dev, W, tuning, weights, max_iters):
             dwg.dwg_destroy(h)
     out["rule"] = "mean |n_new - n_old| <= chord of 0.1 deg (Fig. 6 measure), both inits"
     out["speedup"] = out["random"]["s"] / out["learned"]["s"]
+    # at equal accuracy: the fewest iterations from random normals that reach
+    # the learned start's final agreement (bisection over the iteration cap)
+    target = min(out["learned"]["agreement"], out["random"]["agreement"])
+    lo, hi = 0, out["random"]["iterations"]
+    h = dwg.dwg_create(torch.from_numpy(W["points"]).to(dev))
+    try:
+        configure(dwg, h, W, weights)
+        dwg.dwg_set_tuning(h, **{k: tuning[k] for k in TUNING_KEYS})
+        res = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lam"], mid, W["tol"])
+            dwg.dwg_set_convergence(h, dwg.DWG_CONV_MEAN)
+            dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
+            dwg.dwg_orient(h, res)
+            if agreement(res.cpu().numpy(), W["normals_true"]) >= target:
+                hi = mid
+            else:
+                lo = mid
+    finally:
+        dwg.dwg_destroy(h)
+    per_it = out["random"]["s"] / max(1, out["random"]["iterations"])
+    out["equal_accuracy"] = {
+        "agreement": target, "random_iterations": hi, "random_s": per_it * hi,
+        "learned_iterations": out["learned"]["iterations"], "learned_s": out["learned"]["s"],
+        "speedup": per_it * hi / out["learned"]["s"]}
     return out
 
 

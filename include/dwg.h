@@ -333,7 +333,8 @@ int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
  *   compiled evaluator shape, timed with CUDA events, median of three) and/or
  *   DWG_TUNE_TREE (per leaf size and test form, the largest opening angle in
  *   {0.9, 0.8, ..., 0.2} whose w differs from the exact all-pairs w by at most
- *   w_budget (absolute) on a sample of up to 2,048 points and 2,048 corners;
+ *   w_budget (absolute) on a sample of up to 2,048 points and 2,048 corners
+ *   (runs of 64 consecutive ones, spread evenly);
  *   then the fastest of those).  With path DWG_PATH_AUTO the faster path that meets
  *   the budget is chosen; with DWG_PATH_TREE and no angle meeting the budget
  *   the call fails with DWG_ERR_INVALID.  The chosen settings are applied to

@@ -203,6 +203,14 @@ static int ensure_iter_buffers(Ctx *c)
             c->part_c_cap = need_c;
         }
     }
+    // group form of the Barnes-Hut test: interaction lists, built once
+    if (tree && c->tree_group) {
+        bool built = false;
+        int rc = tree_lists(c, c->lists_p, c->d_p4, c->n, &built);
+        if (!rc && c->mode == DWG_UPDATE_LEVELSET)
+            rc = tree_lists(c, c->lists_c, c->d_corner_pos, c->ncorners, &built);
+        if (rc) return rc;
+    }
     if (c->trace_cap < c->max_iters) {
         ++c->bufgen;
         cudaFree(c->d_tr_iso);
@@ -244,7 +252,8 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
     mark(0);
     if (tree) {
         if (launch_tree_moments(c) != cudaSuccess ||
-            launch_tree_gwn(c, c->d_p4, c->n, true, c->d_part_p, c->n, c->d_state) != cudaSuccess)
+            launch_tree_iter(c, c->lists_p, c->d_p4, c->n, true, c->d_part_p, c->n, c->d_state) !=
+                cudaSuccess)
             return fail(c, DWG_ERR_CUDA, "tree launch failed");
     } else if ((rc = eval_launch(c, c->d_p4, c->n, true, c->nchunks_p, c->d_part_p, c->n))) {
         return rc;
@@ -259,8 +268,8 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
     if (c->mode == DWG_UPDATE_LEVELSET) {
         // w at the octree leaf corners, level set, face gradients to the k nearest points
         if (tree) {
-            if (launch_tree_gwn(c, c->d_corner_pos, c->ncorners, false, c->d_part_c, c->ncorners,
-                                c->d_state) != cudaSuccess)
+            if (launch_tree_iter(c, c->lists_c, c->d_corner_pos, c->ncorners, false, c->d_part_c,
+                                 c->ncorners, c->d_state) != cudaSuccess)
                 return fail(c, DWG_ERR_CUDA, "tree launch failed");
         } else if ((rc = eval_launch(c, c->d_corner_pos, c->ncorners, false, c->nchunks_c,
                                      c->d_part_c, c->ncorners))) {
@@ -446,6 +455,8 @@ void dwg_destroy(dwg_handle h)
                     h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
                     h->d_tree_mrec, h->d_counter, h->d_mlp_params};
     for (void *p : bufs) cudaFree(p);
+    free_lists(h->lists_p);
+    free_lists(h->lists_c);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -1271,11 +1282,11 @@ static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
         c->stream = h->stream;
         if (use_tree(c)) {
             if (launch_tree_moments(c) != cudaSuccess ||
-                launch_tree_gwn(c, c->d_p4, c->n, true, c->d_part_p, c->n, c->d_state) !=
-                    cudaSuccess ||
+                launch_tree_iter(c, c->lists_p, c->d_p4, c->n, true, c->d_part_p, c->n,
+                                 c->d_state) != cudaSuccess ||
                 (c->mode == DWG_UPDATE_LEVELSET &&
-                 launch_tree_gwn(c, c->d_corner_pos, c->ncorners, false, c->d_part_c, c->ncorners,
-                                 c->d_state) != cudaSuccess))
+                 launch_tree_iter(c, c->lists_c, c->d_corner_pos, c->ncorners, false, c->d_part_c,
+                                  c->ncorners, c->d_state) != cudaSuccess))
                 return fail(h, DWG_ERR_CUDA, "tree launch failed");
         }
         if (launch_reduce_points(c, c->d_part_p, c->nchunks_p, c->n, c->d_p4, 1, true, c->d_wg,

@@ -170,7 +170,7 @@ __global__ void k_scan_total(const int64_t *in, const int64_t *ex, int64_t n, in
 }
 
 // Exclusive scan of n int64 values; *d_total (device) receives the sum.
-static int scan_i64(Ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total)
+int scan_i64(Ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total)
 {
     if (n <= 0) {
         DWG_CUDA_TRY(c, cudaMemsetAsync(d_total, 0, sizeof(int64_t), c->stream));

@@ -415,7 +415,8 @@ static const GwnVariant kVarGrad[] = {
 static const GwnVariant kVarW[] = {
     DWG_GWN_VARIANT(4, 128, false), DWG_GWN_VARIANT(2, 128, false), DWG_GWN_VARIANT(3, 128, false),
     DWG_GWN_VARIANT(6, 128, false), DWG_GWN_VARIANT(2, 256, false), DWG_GWN_VARIANT(3, 256, false),
-    DWG_GWN_VARIANT(4, 256, false)};
+    DWG_GWN_VARIANT(4, 256, false), DWG_GWN_VARIANT(1, 128, false), DWG_GWN_VARIANT(1, 256, false),
+    DWG_GWN_VARIANT(2, 64, false)};
 #undef DWG_GWN_VARIANT
 constexpr int kNumVarGrad = (int)(sizeof(kVarGrad) / sizeof(kVarGrad[0]));
 constexpr int kNumVarW = (int)(sizeof(kVarW) / sizeof(kVarW[0]));
@@ -438,9 +439,9 @@ static const GwnVariant &variant(bool grad, int v)
 // resident CTAs of a variant on the whole device (cached per device)
 static int variant_slots(bool grad, int v, bool scr, int dev)
 {
-    static int cached[2][2][8][64] = {};
+    static int cached[2][2][16][64] = {};
     if (dev < 0 || dev >= 64) dev = 0;
-    if (v < 0 || v >= 8) v = 0;
+    if (v < 0 || v >= 16) v = 0;
     int &slot = cached[grad][scr][v][dev];
     if (!slot) {
         const GwnVariant &V = variant(grad, v);

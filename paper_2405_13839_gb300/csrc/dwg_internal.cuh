@@ -75,6 +75,19 @@ struct GwnItem {
     int cloud, qtile, chunk, pad;
 };
 
+// interaction lists of one query set for the group form of the Barnes-Hut
+// test: per group of 64 queries the far node ids and the near leaf ids
+struct TreeLists {
+    const float4 *q = nullptr;       // the query array they were built for
+    int64_t m = 0;
+    uint64_t key = 0;                // tree generation, beta, depth they were built for
+    int64_t *d_far_off = nullptr;    // ngroups + 1 offsets into d_far
+    int64_t *d_near_off = nullptr;   // ngroups + 1 offsets into d_near
+    int *d_far = nullptr, *d_near = nullptr;
+    int64_t nfar = 0, nnear = 0;
+    bool valid = false;
+};
+
 // ---------------------------------------------------------------------------
 // engine context
 // ---------------------------------------------------------------------------
@@ -152,6 +165,8 @@ struct Ctx {
     float tree_beta = 2.0f;            // 1 / opening angle
     int tree_leaf = 16;                // points per tree leaf (16, 32, 64 or 128)
     int tree_group = 0;                // 1: opening test per 64-query group
+    uint64_t tree_gen = 0;             // counts tree builds
+    TreeLists lists_p, lists_c;        // group-test lists at the points and corners
     int tree_levels = 0;               // 2^tree_levels leaves
     bool tree_built = false;
     double tree_beta_set = -1.0;
@@ -230,6 +245,8 @@ __device__ __forceinline__ int64_t quant21(float x, double lo, double inv_h)
 // launchers (defined in the .cu files); all return cudaGetLastError()
 // ---------------------------------------------------------------------------
 // dwg_build.cu
+// exclusive scan of n int64 values; *d_total (device) receives the sum
+int scan_i64(Ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total);
 cudaError_t launch_check_finite(const float *xyz, int64_t n, int *err, cudaStream_t s);
 cudaError_t launch_bbox(const float *xyz, int64_t n, float *d_minmax /*6*/, cudaStream_t s);
 cudaError_t launch_morton(const float *xyz, int64_t n, double lo0, double lo1, double lo2,
@@ -289,6 +306,14 @@ cudaError_t launch_tree_moments(Ctx *c);
 // st: loop state whose end makes the kernel skip its work (NULL: always run)
 cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float *part,
                             int64_t stride, const IterState *st);
+// the interaction lists of a query set (group test); *built = false when the
+// lists would not fit in device memory (the walk then runs every iteration)
+int tree_lists(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool *built);
+void free_lists(TreeLists &L);
+// one iteration's tree evaluation of a query set: the cached lists when they
+// are valid for it, else the walk
+cudaError_t launch_tree_iter(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool grad,
+                             float *part, int64_t stride, const IterState *st);
 
 // dwg_iter.cu
 cudaError_t launch_iso(Ctx *c);

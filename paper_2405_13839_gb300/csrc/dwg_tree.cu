@@ -34,6 +34,10 @@
 // f32x2 inner loop of the all-pairs path: no divergence and broadcast reads.
 // Each query does a few more terms than under its own test and gets a
 // smaller error bound.
+#include <string.h>
+
+#include <algorithm>
+
 #include "dwg_internal.cuh"
 #include "dwg_packed.cuh"
 
@@ -446,47 +450,49 @@ __device__ __forceinline__ void grp_flush(GrpAcc &A, const float4 *buf, int cnt,
     }
 }
 
-template <bool GRAD, bool SCREENED>
-__global__ void __launch_bounds__(32 * kGrpWarps)
-    k_tree_group(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ rec,
-                 const float4 *__restrict__ mrec, const float *__restrict__ src, int64_t n,
-                 int levels, int bucket, EvalParams ep, float *__restrict__ part, int64_t stride,
-                 unsigned long long *__restrict__ counter, int *err, const IterState *st)
-{
-    if (st && cloud_idle(st)) return;  // finished cloud of a batch
-    extern __shared__ __align__(16) unsigned char grp_smem_raw[];
-    GrpSmem &S = *reinterpret_cast<GrpSmem *>(grp_smem_raw);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t q0 = ((int64_t)blockIdx.x * kGrpWarps + wid) * kGrpQ;
-    if (q0 >= m) return;  // the whole warp
-    const int64_t ia = q0 + lane, ib = q0 + 32 + lane;
-    const float4 qa = q[min(ia, m - 1)], qb = q[min(ib, m - 1)];
-    const int nvalid = (int)min((int64_t)kGrpQ, m - q0);
-    // the group's bounding box (exact min / max of the float coordinates)
-    float lox = fminf(qa.x, qb.x), loy = fminf(qa.y, qb.y), loz = fminf(qa.z, qb.z);
-    float hix = fmaxf(qa.x, qb.x), hiy = fmaxf(qa.y, qb.y), hiz = fmaxf(qa.z, qb.z);
-    for (int o = 16; o > 0; o >>= 1) {
-        lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
-        loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
-        loz = fminf(loz, __shfl_xor_sync(0xffffffffu, loz, o));
-        hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
-        hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
-        hiz = fmaxf(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
-    }
-    const f2 qx = pk(qa.x, qb.x), qy = pk(qa.y, qb.y), qz = pk(qa.z, qb.z);
-    const f2 zero = pk(0.f, 0.f);
-    GrpAcc A;
-    A.hw = A.lw = A.hgx = A.lgx = A.hgy = A.lgy = A.hgz = A.lgz = zero;
+// The warp's 64 queries (two per lane, tail queries repeat the last one) and
+// their bounding box (exact min / max of the float coordinates).
+struct GrpQueries {
+    int64_t ia, ib;
+    int nvalid;
+    float4 qa, qb;
+    float lox, loy, loz, hix, hiy, hiz;
+};
 
-    int *stack = S.stack[wid];
-    float4 *farb = S.far[wid];
-    float4 *nearb = S.near[wid];
-    const float4 *src4 = reinterpret_cast<const float4 *>(src);
-    const int64_t nleaf = (int64_t)1 << levels;
+__device__ __forceinline__ GrpQueries grp_queries(const float4 *__restrict__ q, int64_t m,
+                                                  int64_t q0, int lane)
+{
+    GrpQueries G;
+    G.ia = q0 + lane;
+    G.ib = q0 + 32 + lane;
+    G.qa = q[min(G.ia, m - 1)];
+    G.qb = q[min(G.ib, m - 1)];
+    G.nvalid = (int)min((int64_t)kGrpQ, m - q0);
+    G.lox = fminf(G.qa.x, G.qb.x); G.loy = fminf(G.qa.y, G.qb.y); G.loz = fminf(G.qa.z, G.qb.z);
+    G.hix = fmaxf(G.qa.x, G.qb.x); G.hiy = fmaxf(G.qa.y, G.qb.y); G.hiz = fmaxf(G.qa.z, G.qb.z);
+    for (int o = 16; o > 0; o >>= 1) {
+        G.lox = fminf(G.lox, __shfl_xor_sync(0xffffffffu, G.lox, o));
+        G.loy = fminf(G.loy, __shfl_xor_sync(0xffffffffu, G.loy, o));
+        G.loz = fminf(G.loz, __shfl_xor_sync(0xffffffffu, G.loz, o));
+        G.hix = fmaxf(G.hix, __shfl_xor_sync(0xffffffffu, G.hix, o));
+        G.hiy = fmaxf(G.hiy, __shfl_xor_sync(0xffffffffu, G.hiy, o));
+        G.hiz = fmaxf(G.hiz, __shfl_xor_sync(0xffffffffu, G.hiz, o));
+    }
+    return G;
+}
+
+// One warp walks the tree for its group, 32 nodes per step (one per lane).
+// A node far from the group's box goes to on_far, a near leaf to on_near,
+// an open node pushes its children.  on_far(is_far, node, record, mask) is
+// called by every lane each step (warp-uniform); on_near(leaf) once per
+// near leaf, by every lane.  Returns false if the stack would overflow.
+template <class FarFn, class NearFn>
+__device__ __forceinline__ bool grp_walk(int *stack, const float4 *__restrict__ rec,
+                                         int64_t nleaf, const GrpQueries &G, int lane,
+                                         FarFn &&on_far, NearFn &&on_near)
+{
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long terms = 0;  // terms per query of the group (warp-uniform)
-    int far_cnt = 0, near_cnt = 0, sp = 1;
-    bool overflow = false;
+    int sp = 1;
     if (lane == 0) stack[0] = 1;
     __syncwarp();
     while (sp > 0) {
@@ -499,84 +505,41 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
         if (lane < k) {
             cr = rec[node];
             if (cr.w >= 0.f) {
-                float ex = fmaxf(fmaxf(__fsub_rn(lox, cr.x), __fsub_rn(cr.x, hix)), 0.f);
-                float ey = fmaxf(fmaxf(__fsub_rn(loy, cr.y), __fsub_rn(cr.y, hiy)), 0.f);
-                float ez = fmaxf(fmaxf(__fsub_rn(loz, cr.z), __fsub_rn(cr.z, hiz)), 0.f);
+                float ex = fmaxf(fmaxf(__fsub_rn(G.lox, cr.x), __fsub_rn(cr.x, G.hix)), 0.f);
+                float ey = fmaxf(fmaxf(__fsub_rn(G.loy, cr.y), __fsub_rn(cr.y, G.hiy)), 0.f);
+                float ez = fmaxf(fmaxf(__fsub_rn(G.loz, cr.z), __fsub_rn(cr.z, G.hiz)), 0.f);
                 float d2 = fmaf(ez, ez, fmaf(ey, ey, __fmul_rn(ex, ex)));
                 act = d2 > cr.w ? 1 : ((int64_t)node >= nleaf ? 2 : 3);
             }
         }
-        // far nodes: dipole records (c, M / 4 pi), duplicated for the packed loop
-        const unsigned fm = __ballot_sync(0xffffffffu, act == 1);
-        const int nf = __popc(fm);
-        if (far_cnt + nf > kGrpFar) {
-            __syncwarp();
-            grp_flush<GRAD, SCREENED>(A, farb, far_cnt, qx, qy, qz, ep);
-            terms += (unsigned long long)far_cnt;
-            far_cnt = 0;
-            __syncwarp();
-        }
-        if (act == 1) {
-            const float4 mm = mrec[node];
-            float4 *r = farb + 3 * (far_cnt + __popc(fm & lt));
-            r[0] = make_float4(cr.x, cr.x, cr.y, cr.y);
-            r[1] = make_float4(cr.z, cr.z, mm.x, mm.x);
-            r[2] = make_float4(mm.y, mm.y, mm.z, mm.z);
-        }
-        far_cnt += nf;
-        // open nodes: push both children
+        on_far(act == 1, node, cr, __ballot_sync(0xffffffffu, act == 1));
         const unsigned om = __ballot_sync(0xffffffffu, act == 3);
         const int no = __popc(om);
-        if (sp + 2 * no > kGrpStack) {
-            overflow = true;
-            break;
-        }
+        if (sp + 2 * no > kGrpStack) return false;
         if (act == 3) {
             const int pos = sp + 2 * __popc(om & lt);
             stack[pos] = 2 * node + 1;
             stack[pos + 1] = 2 * node;
         }
         sp += 2 * no;
-        // near leaves: their points' records, copied in order
         unsigned nm = __ballot_sync(0xffffffffu, act == 2);
         while (nm) {
             const int leader = __ffs(nm) - 1;
             nm &= nm - 1;
-            const int leaf = __shfl_sync(0xffffffffu, node, leader);
-            const int64_t j0 = ((int64_t)leaf - nleaf) * bucket;
-            const int cnt = (int)min((int64_t)bucket, n - j0);
-            int done = 0;
-            while (done < cnt) {
-                const int take = min(cnt - done, kGrpNear - near_cnt);
-                if (take == 0) {
-                    __syncwarp();
-                    grp_flush<GRAD, SCREENED>(A, nearb, near_cnt, qx, qy, qz, ep);
-                    terms += (unsigned long long)near_cnt;
-                    near_cnt = 0;
-                    __syncwarp();
-                    continue;
-                }
-                const float4 *from = src4 + 3 * (j0 + done);
-                float4 *to = nearb + 3 * near_cnt;
-                for (int t = lane; t < 3 * take; t += 32) to[t] = from[t];
-                near_cnt += take;
-                done += take;
-            }
+            on_near(__shfl_sync(0xffffffffu, node, leader));
         }
         __syncwarp();
     }
-    if (overflow) {
-        if (lane == 0) atomicOr(err, kErrStack);
-        return;
-    }
-    __syncwarp();
-    if (far_cnt) grp_flush<GRAD, SCREENED>(A, farb, far_cnt, qx, qy, qz, ep);
-    if (near_cnt) grp_flush<GRAD, SCREENED>(A, nearb, near_cnt, qx, qy, qz, ep);
-    terms += (unsigned long long)(far_cnt + near_cnt);
-    // chunk-0 partials, as the per-query kernel writes them
+    return true;
+}
+
+template <bool GRAD>
+__device__ __forceinline__ void grp_write(const GrpAcc &A, const GrpQueries &G, int64_t m,
+                                          float *__restrict__ part, int64_t stride)
+{
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int64_t i = h ? ib : ia;
+        const int64_t i = h ? G.ib : G.ia;
         if (i >= m) continue;
         float a, b;
         upk(A.hw, a, b); part[0 * stride + i] = h ? b : a;
@@ -590,7 +553,207 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
             upk(A.lgz, a, b); part[7 * stride + i] = h ? b : a;
         }
     }
-    if (lane == 0 && counter) atomicAdd(counter, terms * (unsigned long long)nvalid);
+}
+
+// a near leaf's point records appended to a shared buffer (flushing it when
+// full); `flush(cnt)` evaluates the buffer
+template <class FlushFn>
+__device__ __forceinline__ void grp_take_leaf(const float4 *__restrict__ src4, int64_t j0, int cnt,
+                                              float4 *nearb, int &near_cnt, int lane,
+                                              FlushFn &&flush)
+{
+    int done = 0;
+    while (done < cnt) {
+        const int take = min(cnt - done, kGrpNear - near_cnt);
+        if (take == 0) {
+            __syncwarp();
+            flush(near_cnt);
+            near_cnt = 0;
+            __syncwarp();
+            continue;
+        }
+        const float4 *from = src4 + 3 * (j0 + done);
+        float4 *to = nearb + 3 * near_cnt;
+        for (int t = lane; t < 3 * take; t += 32) to[t] = from[t];
+        near_cnt += take;
+        done += take;
+    }
+}
+
+template <bool GRAD, bool SCREENED>
+__global__ void __launch_bounds__(32 * kGrpWarps)
+    k_tree_group(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ rec,
+                 const float4 *__restrict__ mrec, const float *__restrict__ src, int64_t n,
+                 int levels, int bucket, EvalParams ep, float *__restrict__ part, int64_t stride,
+                 unsigned long long *__restrict__ counter, int *err, const IterState *st)
+{
+    if (st && cloud_idle(st)) return;  // finished cloud of a batch
+    extern __shared__ __align__(16) unsigned char grp_smem_raw[];
+    GrpSmem &S = *reinterpret_cast<GrpSmem *>(grp_smem_raw);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t q0 = ((int64_t)blockIdx.x * kGrpWarps + wid) * kGrpQ;
+    if (q0 >= m) return;  // the whole warp
+    const GrpQueries G = grp_queries(q, m, q0, lane);
+    const f2 qx = pk(G.qa.x, G.qb.x), qy = pk(G.qa.y, G.qb.y), qz = pk(G.qa.z, G.qb.z);
+    const f2 zero = pk(0.f, 0.f);
+    GrpAcc A;
+    A.hw = A.lw = A.hgx = A.lgx = A.hgy = A.lgy = A.hgz = A.lgz = zero;
+    float4 *farb = S.far[wid];
+    float4 *nearb = S.near[wid];
+    const float4 *src4 = reinterpret_cast<const float4 *>(src);
+    const int64_t nleaf = (int64_t)1 << levels;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long terms = 0;  // terms per query of the group (warp-uniform)
+    int far_cnt = 0, near_cnt = 0;
+    auto flush_near = [&](int cnt) {
+        grp_flush<GRAD, SCREENED>(A, nearb, cnt, qx, qy, qz, ep);
+        terms += (unsigned long long)cnt;
+    };
+    const bool ok = grp_walk(
+        S.stack[wid], rec, nleaf, G, lane,
+        [&](bool is_far, int node, const float4 &cr, unsigned fm) {
+            // far nodes: dipole records (c, M / 4 pi), duplicated for the packed loop
+            const int nf = __popc(fm);
+            if (far_cnt + nf > kGrpFar) {
+                __syncwarp();
+                grp_flush<GRAD, SCREENED>(A, farb, far_cnt, qx, qy, qz, ep);
+                terms += (unsigned long long)far_cnt;
+                far_cnt = 0;
+                __syncwarp();
+            }
+            if (is_far) {
+                const float4 mm = mrec[node];
+                float4 *r = farb + 3 * (far_cnt + __popc(fm & lt));
+                r[0] = make_float4(cr.x, cr.x, cr.y, cr.y);
+                r[1] = make_float4(cr.z, cr.z, mm.x, mm.x);
+                r[2] = make_float4(mm.y, mm.y, mm.z, mm.z);
+            }
+            far_cnt += nf;
+        },
+        [&](int leaf) {
+            const int64_t j0 = ((int64_t)leaf - nleaf) * bucket;
+            grp_take_leaf(src4, j0, (int)min((int64_t)bucket, n - j0), nearb, near_cnt, lane,
+                          flush_near);
+        });
+    if (!ok) {
+        if (lane == 0) atomicOr(err, kErrStack);
+        return;
+    }
+    __syncwarp();
+    if (far_cnt) grp_flush<GRAD, SCREENED>(A, farb, far_cnt, qx, qy, qz, ep);
+    if (near_cnt) grp_flush<GRAD, SCREENED>(A, nearb, near_cnt, qx, qy, qz, ep);
+    terms += (unsigned long long)(far_cnt + near_cnt);
+    grp_write<GRAD>(A, G, m, part, stride);
+    if (lane == 0 && counter) atomicAdd(counter, terms * (unsigned long long)G.nvalid);
+}
+
+// ---------------------------------------------------------------------------
+// interaction lists: node centres and radii depend on the positions only, so
+// each group's far nodes and near leaves are the same in every iteration.
+// They are found once (a counting walk, a scan, a filling walk) and each
+// iteration only evaluates them.
+// ---------------------------------------------------------------------------
+constexpr int kListWarps = 8;
+
+template <bool FILL>
+__global__ void __launch_bounds__(32 * kListWarps)
+    k_tree_lists(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ rec,
+                 int levels, int64_t *far_n, int64_t *near_n, int *__restrict__ far_ids,
+                 int *__restrict__ near_ids, int *err)
+{
+    __shared__ int stack[kListWarps][kGrpStack];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t g = (int64_t)blockIdx.x * kListWarps + wid;
+    const int64_t q0 = g * kGrpQ;
+    if (q0 >= m) return;
+    const GrpQueries G = grp_queries(q, m, q0, lane);
+    const int64_t nleaf = (int64_t)1 << levels;
+    const unsigned lt = (1u << lane) - 1u;
+    // FILL: far_n / near_n hold each group's first slot; else they get counts
+    int64_t nf = FILL ? far_n[g] : 0, nn = FILL ? near_n[g] : 0;
+    const bool ok = grp_walk(
+        stack[wid], rec, nleaf, G, lane,
+        [&](bool is_far, int node, const float4 &, unsigned fm) {
+            if (FILL && is_far) far_ids[nf + __popc(fm & lt)] = node;
+            nf += __popc(fm);
+        },
+        [&](int leaf) {
+            if (FILL && lane == 0) near_ids[nn] = leaf;
+            ++nn;
+        });
+    if (!ok) {
+        if (lane == 0) atomicOr(err, kErrStack);
+        return;
+    }
+    if (!FILL && lane == 0) {
+        far_n[g] = nf;
+        near_n[g] = nn;
+    }
+}
+
+// Evaluation of the lists: the warp stages far records (c, M / 4 pi) and
+// near leaves' point records in shared memory and runs the packed loop.
+template <bool GRAD, bool SCREENED>
+__global__ void __launch_bounds__(32 * kGrpWarps)
+    k_tree_eval_lists(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ rec,
+                      const float4 *__restrict__ mrec, const float *__restrict__ src, int64_t n,
+                      int levels, int bucket, const int64_t *__restrict__ far_off,
+                      const int *__restrict__ far_ids, const int64_t *__restrict__ near_off,
+                      const int *__restrict__ near_ids, EvalParams ep, float *__restrict__ part,
+                      int64_t stride, unsigned long long *__restrict__ counter,
+                      const IterState *st)
+{
+    if (st && cloud_idle(st)) return;  // finished cloud of a batch
+    __shared__ float4 farb_all[kGrpWarps][kGrpFar * 3];
+    __shared__ float4 nearb_all[kGrpWarps][kGrpNear * 3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t g = (int64_t)blockIdx.x * kGrpWarps + wid;
+    const int64_t q0 = g * kGrpQ;
+    if (q0 >= m) return;
+    const GrpQueries G = grp_queries(q, m, q0, lane);
+    const f2 qx = pk(G.qa.x, G.qb.x), qy = pk(G.qa.y, G.qb.y), qz = pk(G.qa.z, G.qb.z);
+    const f2 zero = pk(0.f, 0.f);
+    GrpAcc A;
+    A.hw = A.lw = A.hgx = A.lgx = A.hgy = A.lgy = A.hgz = A.lgz = zero;
+    float4 *farb = farb_all[wid];
+    float4 *nearb = nearb_all[wid];
+    const float4 *src4 = reinterpret_cast<const float4 *>(src);
+    const int64_t nleaf = (int64_t)1 << levels;
+    unsigned long long terms = 0;
+    // far nodes, kGrpFar at a time: each lane stages two records
+    const int64_t f0 = far_off[g], f1 = far_off[g + 1];
+    for (int64_t b = f0; b < f1; b += kGrpFar) {
+        const int cnt = (int)min((int64_t)kGrpFar, f1 - b);
+        for (int t = lane; t < cnt; t += 32) {
+            const int node = far_ids[b + t];
+            const float4 cr = rec[node];
+            const float4 mm = mrec[node];
+            float4 *r = farb + 3 * t;
+            r[0] = make_float4(cr.x, cr.x, cr.y, cr.y);
+            r[1] = make_float4(cr.z, cr.z, mm.x, mm.x);
+            r[2] = make_float4(mm.y, mm.y, mm.z, mm.z);
+        }
+        __syncwarp();
+        grp_flush<GRAD, SCREENED>(A, farb, cnt, qx, qy, qz, ep);
+        terms += (unsigned long long)cnt;
+        __syncwarp();
+    }
+    // near leaves: their points' records, in list order
+    int near_cnt = 0;
+    auto flush_near = [&](int cnt) {
+        grp_flush<GRAD, SCREENED>(A, nearb, cnt, qx, qy, qz, ep);
+        terms += (unsigned long long)cnt;
+    };
+    const int64_t e0 = near_off[g], e1 = near_off[g + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int64_t j0 = ((int64_t)near_ids[e] - nleaf) * bucket;
+        grp_take_leaf(src4, j0, (int)min((int64_t)bucket, n - j0), nearb, near_cnt, lane,
+                      flush_near);
+    }
+    __syncwarp();
+    if (near_cnt) flush_near(near_cnt);
+    grp_write<GRAD>(A, G, m, part, stride);
+    if (lane == 0 && counter) atomicAdd(counter, terms * (unsigned long long)G.nvalid);
 }
 
 // ---------------------------------------------------------------------------
@@ -613,8 +776,92 @@ static cudaError_t group_smem_attr(int dev)
     return e;
 }
 
+void free_lists(TreeLists &L)
+{
+    cudaFree(L.d_far_off);
+    cudaFree(L.d_near_off);
+    cudaFree(L.d_far);
+    cudaFree(L.d_near);
+    L = TreeLists();
+}
+
+static uint64_t lists_key(const Ctx *c)
+{
+    uint32_t bb;
+    memcpy(&bb, &c->tree_beta, sizeof bb);
+    return (c->tree_gen * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)bb << 8) ^ (uint64_t)c->built_depth;
+}
+
+int tree_lists(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool *built)
+{
+    *built = false;
+    const uint64_t key = lists_key(c);
+    if (L.valid && L.q == q && L.m == m && L.key == key) {
+        *built = true;
+        return DWG_OK;
+    }
+    free_lists(L);
+    ++c->bufgen;  // a captured graph may hold the old lists
+    if (m < 1) return DWG_OK;
+    const int64_t ng = ceil_div(m, kGrpQ);
+    const unsigned blocks = (unsigned)ceil_div(ng, kListWarps);
+    int64_t *cnt_f = nullptr, *cnt_n = nullptr;
+    auto run = [&]() -> int {
+        DWG_CUDA_TRY(c, cudaMalloc(&cnt_f, ng * sizeof(int64_t)));
+        DWG_CUDA_TRY(c, cudaMalloc(&cnt_n, ng * sizeof(int64_t)));
+        DWG_CUDA_TRY(c, cudaMalloc(&L.d_far_off, (ng + 1) * sizeof(int64_t)));
+        DWG_CUDA_TRY(c, cudaMalloc(&L.d_near_off, (ng + 1) * sizeof(int64_t)));
+        k_tree_lists<false><<<blocks, 32 * kListWarps, 0, c->stream>>>(
+            q, m, c->d_tree_rec, c->tree_levels, cnt_f, cnt_n, nullptr, nullptr, c->d_err);
+        DWG_CUDA_TRY(c, cudaGetLastError());
+        int rc = scan_i64(c, cnt_f, L.d_far_off, ng, L.d_far_off + ng);
+        if (!rc) rc = scan_i64(c, cnt_n, L.d_near_off, ng, L.d_near_off + ng);
+        if (rc) return rc;
+        int herr = 0;
+        DWG_CUDA_TRY(c, cudaMemcpyAsync(&L.nfar, L.d_far_off + ng, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        DWG_CUDA_TRY(c, cudaMemcpyAsync(&L.nnear, L.d_near_off + ng, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        DWG_CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                        c->stream));
+        DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (herr) {
+            c->err = "tree lists: traversal stack overflow";
+            return DWG_ERR_CUDA;
+        }
+        // the lists stay resident across iterations; take at most half of
+        // the free memory, else keep walking the tree every iteration
+        size_t free_b = 0, total_b = 0;
+        DWG_CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
+        const double need = 4.0 * (double)(L.nfar + L.nnear);
+        if (need > 0.5 * (double)free_b) return DWG_OK;
+        DWG_CUDA_TRY(c, cudaMalloc(&L.d_far, std::max<int64_t>(L.nfar, 1) * sizeof(int)));
+        DWG_CUDA_TRY(c, cudaMalloc(&L.d_near, std::max<int64_t>(L.nnear, 1) * sizeof(int)));
+        k_tree_lists<true><<<blocks, 32 * kListWarps, 0, c->stream>>>(
+            q, m, c->d_tree_rec, c->tree_levels, L.d_far_off, L.d_near_off, L.d_far, L.d_near,
+            c->d_err);
+        DWG_CUDA_TRY(c, cudaGetLastError());
+        L.q = q;
+        L.m = m;
+        L.key = key;
+        L.valid = true;
+        *built = true;
+        return DWG_OK;
+    };
+    int rc = run();
+    cudaFree(cnt_f);
+    cudaFree(cnt_n);
+    if (rc || !L.valid) {
+        free_lists(L);
+        if (!rc) *built = false;
+    }
+    return rc;
+}
+
 void free_tree(Ctx *c)
 {
+    free_lists(c->lists_p);
+    free_lists(c->lists_c);
     cudaFree(c->d_tree_A);
     cudaFree(c->d_tree_C);
     cudaFree(c->d_tree_R);
@@ -668,6 +915,7 @@ int build_tree(Ctx *c)
     cudaFree(Sp);
     c->tree_built = true;
     c->tree_beta_set = -1.0;
+    ++c->tree_gen;
     ++c->bufgen;  // a captured graph holds the old node arrays
     return DWG_OK;
 }
@@ -711,6 +959,32 @@ static cudaError_t launch_group_t(Ctx *c, const float4 *q, int64_t m, float *par
         q, m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->tree_levels, c->tree_leaf, ep,
         part, stride, c->d_counter, c->d_err, st);
     return cudaGetLastError();
+}
+
+template <bool GRAD, bool SCREENED>
+static cudaError_t launch_lists_t(Ctx *c, const TreeLists &L, float *part, int64_t stride,
+                                  const IterState *st)
+{
+    EvalParams ep = make_eval_params(c);
+    const int64_t per_cta = (int64_t)kGrpWarps * kGrpQ;
+    k_tree_eval_lists<GRAD, SCREENED><<<(unsigned)ceil_div(L.m, per_cta), 32 * kGrpWarps, 0,
+                                         c->stream>>>(
+        L.q, L.m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->tree_levels, c->tree_leaf,
+        L.d_far_off, L.d_far, L.d_near_off, L.d_near, ep, part, stride, c->d_counter, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_iter(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool grad,
+                             float *part, int64_t stride, const IterState *st)
+{
+    if (!(c->tree_group && L.valid && L.q == q && L.m == m && L.key == lists_key(c)))
+        return launch_tree_gwn(c, q, m, grad, part, stride, st);
+    const bool scr = make_eval_params(c).screened != 0;
+    if (grad)
+        return scr ? launch_lists_t<true, true>(c, L, part, stride, st)
+                   : launch_lists_t<true, false>(c, L, part, stride, st);
+    return scr ? launch_lists_t<false, true>(c, L, part, stride, st)
+               : launch_lists_t<false, false>(c, L, part, stride, st);
 }
 
 cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float *part,

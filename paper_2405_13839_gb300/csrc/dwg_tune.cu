@@ -37,11 +37,17 @@ constexpr int kLeaves[] = {16, 32, 64, 128};
 constexpr int64_t kSampleEach = 2048;        // tree-accuracy sample: points and corners
 constexpr double kMaxTimedInteractions = 4e11;  // cap of one timed all-pairs launch
 
-__global__ void k_strided_copy(const float4 *__restrict__ src, int64_t count, int64_t stride,
-                               float4 *__restrict__ dst)
+// sample of `count` queries out of m: runs of 64 consecutive ones (a warp
+// group of the group traversal sees its real bounding boxes) spread evenly
+__global__ void k_sample_runs(const float4 *__restrict__ src, int64_t m, int64_t count,
+                              float4 *__restrict__ dst)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) dst[i] = src[i * stride];
+    if (i >= count) return;
+    const int64_t runs = (count + 63) / 64;
+    const int64_t step = max((int64_t)64, m / runs);
+    const int64_t j = (i / 64) * step + (i % 64);
+    dst[i] = src[min(j, m - 1)];
 }
 
 __global__ void k_max_abs_diff(const float *__restrict__ a, const float *__restrict__ b, int64_t m,
@@ -363,11 +369,11 @@ int autotune(Ctx *c, int what, double budget, const char *cache_path, dwg_tuning
         TUNE_TRY(cudaMalloc(&wex.p, S * sizeof(float)));
         TUNE_TRY(cudaMalloc(&wtr.p, S * sizeof(float)));
         TUNE_TRY(cudaMalloc(&dmax.p, sizeof(float)));
-        k_strided_copy<<<(unsigned)ceil_div(sp, 256), 256, 0, c->stream>>>(
-            c->d_p4, sp, std::max<int64_t>(1, c->n / sp), q.as<float4>());
+        k_sample_runs<<<(unsigned)ceil_div(sp, 256), 256, 0, c->stream>>>(c->d_p4, c->n, sp,
+                                                                            q.as<float4>());
         if (sc > 0)
-            k_strided_copy<<<(unsigned)ceil_div(sc, 256), 256, 0, c->stream>>>(
-                c->d_corner_pos, sc, std::max<int64_t>(1, c->ncorners / sc), q.as<float4>() + sp);
+            k_sample_runs<<<(unsigned)ceil_div(sc, 256), 256, 0, c->stream>>>(
+                c->d_corner_pos, c->ncorners, sc, q.as<float4>() + sp);
         TUNE_TRY(cudaGetLastError());
         // exact reference: all-pairs w of the sample
         if ((rc = eval_launch_variant(c, q.as<float4>(), S, false, 0, nch, part.as<float>(), S)))
@@ -406,18 +412,25 @@ int autotune(Ctx *c, int what, double budget, const char *cache_path, dwg_tuning
             if (th_ok < 0.f) continue;
             c->tree_beta = 1.0f / th_ok;
             if ((rc = tree_records(c))) return rc;
+            if (G) {  // the iteration evaluates interaction lists, built once
+                bool built = false;
+                if ((rc = tree_lists(c, c->lists_p, c->d_p4, c->n, &built))) return rc;
+                if (lset &&
+                    (rc = tree_lists(c, c->lists_c, c->d_corner_pos, c->ncorners, &built)))
+                    return rc;
+            }
             double mp = 0.0, mc = 0.0;
             rc = time_ms(c, [&]() {
                 if (launch_tree_moments(c) != cudaSuccess ||
-                    launch_tree_gwn(c, c->d_p4, c->n, true, c->d_part_p, c->n, nullptr) !=
-                        cudaSuccess)
+                    launch_tree_iter(c, c->lists_p, c->d_p4, c->n, true, c->d_part_p, c->n,
+                                     nullptr) != cudaSuccess)
                     return DWG_ERR_CUDA;
                 return DWG_OK;
             }, &mp);
             if (!rc && lset)
                 rc = time_ms(c, [&]() {
-                    return launch_tree_gwn(c, c->d_corner_pos, c->ncorners, false, c->d_part_c,
-                                           c->ncorners, nullptr) == cudaSuccess
+                    return launch_tree_iter(c, c->lists_c, c->d_corner_pos, c->ncorners, false,
+                                            c->d_part_c, c->ncorners, nullptr) == cudaSuccess
                                ? DWG_OK
                                : DWG_ERR_CUDA;
                 }, &mc);
@@ -439,6 +452,8 @@ int autotune(Ctx *c, int what, double budget, const char *cache_path, dwg_tuning
         c->tree_beta = saved_beta;
         c->tree_group = saved_group;
         c->tree_built = false;
+        free_lists(c->lists_p);
+        free_lists(c->lists_c);
         if ((rc = device_error(c))) return rc;
         if (path_req == DWG_PATH_TREE && !tree_ok) {
             c->err = "autotune: no opening angle down to 0.2 meets the error budget";

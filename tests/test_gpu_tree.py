@@ -165,3 +165,40 @@ def test_tree_orientation_torus_both_tests(dwglib, handle, group):
     out = np.zeros((n, 3), np.float32)
     rc, iters = dwglib.dwg_orient(h, out)
     assert agreement(out, nt) >= 0.999, (agreement(out, nt), iters)
+
+
+@pytest.mark.parametrize("kernel,lam,leaf", [(0, 0.0, 16), (1, 10.0, 32), (1, 100.0, 64)])
+def test_group_lists_step_matches_oracle_group_tree(dwglib, oracle_mod, handle, kernel, lam,
+                                                    leaf):
+    """One iteration on the Barnes-Hut path with the group test evaluates the
+    interaction lists built once per cloud (w and grad w at the points, in
+    Morton order, 64 per group): the values are the oracle's group tree on
+    the Morton-ordered points."""
+    n = 20000
+    p, _ = synth.torus(n, seed=12, noise=0.004)
+    area = 4 * np.pi ** 2 * 0.3
+    a = np.full(n, area / n, np.float32)
+    eps = synth.default_eps(area, n)
+    nrm = synth.random_unit_normals(n, seed=13).astype(np.float32)
+    h = handle(p)
+    dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_params(h, kernel, eps, lam, 30, 0.1)
+    dwglib.dwg_set_update(h, 6, 10, dwglib.DWG_UPDATE_LEVELSET)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+    dwglib.dwg_set_tuning(h, tree_group=1, tree_leaf=leaf)
+    dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, nrm)
+    w = np.zeros(n, np.float32)
+    g = np.zeros((n, 3), np.float32)
+    for rep in range(2):  # the second step reuses the lists with new normals
+        dwglib.dwg_step(h, w, g)
+        order = oracle_mod.morton_order(p)
+        wo_s, go_s = oracle_mod.tree_gwn_group(p, nrm, a, p[order], kernel=kernel, eps=eps,
+                                               lam=lam, beta=2.0, bucket=leaf, group=64)
+        wo = np.empty(n)
+        go = np.empty((n, 3))
+        wo[order] = wo_s
+        go[order] = go_s
+        sel = np.arange(0, n, 7)
+        check_wg(w[sel], g[sel], wo[sel], go[sel], s_g(p, nrm, a, p[sel], eps))
+        nrm = np.zeros((n, 3), np.float32)
+        dwglib.dwg_get_normals(h, nrm)

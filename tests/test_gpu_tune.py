@@ -16,7 +16,8 @@ from test_gpu_parity import check_wg, make_cloud, s_g
 pytestmark = pytest.mark.gpu
 
 SHAPES_GRAD = [(2, 128), (1, 128), (3, 128), (1, 256), (2, 256)]
-SHAPES_W = [(4, 128), (2, 128), (3, 128), (6, 128), (2, 256), (3, 256), (4, 256)]
+SHAPES_W = [(4, 128), (2, 128), (3, 128), (6, 128), (2, 256), (3, 256), (4, 256), (1, 128),
+            (1, 256), (2, 64)]
 
 
 @pytest.fixture
@@ -154,7 +155,7 @@ def test_autotune_shapes_applies_a_compiled_shape(dwglib, oracle_mod, handle, tm
     assert len(open(cache).read().strip().splitlines()) == 1
 
 
-@pytest.mark.parametrize("budget", [3e-3, 3e-4])
+@pytest.mark.parametrize("budget", [1e-2, 3e-3])
 def test_autotune_tree_meets_the_error_budget(dwglib, oracle_mod, handle, budget):
     n = 60000
     p, _ = synth.torus(n, seed=7, noise=0.003)
@@ -207,3 +208,17 @@ def test_autotune_auto_path_picks_a_path_and_orients(dwglib, handle):
     dwglib.dwg_orient(h, out)
     d = np.sum(out * nt, axis=1)
     assert np.mean(np.sign(d.sum()) * d > 0) >= 0.999
+
+
+def test_autotune_tree_rejects_an_unreachable_budget(dwglib, handle):
+    """A first-order far field cannot reach 1e-9 at any opening angle down to
+    0.2: on the tree path the tuner reports it instead of choosing one."""
+    n = 20000
+    p, _ = synth.torus(n, seed=3)
+    h = handle(p)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+    before = dwglib.dwg_get_tuning(h)
+    with pytest.raises(dwglib.DWGError) as e:
+        dwglib.dwg_autotune(h, dwglib.DWG_TUNE_TREE, 1e-9, None)
+    assert e.value.code == dwglib.DWG_ERR_INVALID
+    assert dwglib.dwg_get_tuning(h) == before
