@@ -66,7 +66,8 @@ extern "C" {
 #define DWG_INIT_LEARNED 2
 
 /* Evaluation path: exact all-pairs sums, or the Barnes-Hut far field of
- * Sec. 5.2; AUTO takes all-pairs up to 262,144 points and the tree above. */
+ * Sec. 5.2; AUTO takes all-pairs up to 65,536 points and the tree above
+ * (dwg_autotune can choose by measurement instead). */
 #define DWG_PATH_AUTO 0
 #define DWG_PATH_ALLPAIRS 1
 #define DWG_PATH_TREE 2
@@ -318,10 +319,12 @@ int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
  *   tree_leaf:       points per Barnes-Hut leaf (16, 32, 64 or 128);
  *   theta:           opening angle of the Barnes-Hut path (as dwg_set_tree);
  *   tree_group:      0: the opening test per query (Sec. 5.2 as printed);
- *                    1: per group of 64 consecutive queries, against the
- *                    group's bounding box -- conservative (far for the box is
- *                    far for each query), so every query's error stays within
- *                    its per-query bound, and the group shares one walk;
+ *                    1 (default): per group of 64 consecutive queries,
+ *                    against the group's bounding box -- conservative (far
+ *                    for the box is far for each query), so every query's
+ *                    error stays within its per-query bound; the groups'
+ *                    interaction lists at the points and the leaf corners
+ *                    are built once and evaluated every iteration;
  *   w_err:           largest |w_tree - w_exact| the tuner saw on its sample
  *                    (0 for the exact path);
  *   ms_points, ms_corners: device time of one evaluation at the points and

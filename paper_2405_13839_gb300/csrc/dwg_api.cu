@@ -45,7 +45,7 @@ bool use_tree(const Ctx *c)
 {
     if (c->path == DWG_PATH_TREE) return true;
     if (c->path == DWG_PATH_ALLPAIRS) return false;
-    return c->n > 262144;
+    return c->n > 65536;
 }
 }  // namespace dwg
 
@@ -453,7 +453,7 @@ void dwg_destroy(dwg_handle h)
                     h->d_acc, h->d_part_p, h->d_part_c, h->d_wsum_blocks, h->d_dn_blocks,
                     h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err,
                     h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
-                    h->d_tree_mrec, h->d_counter, h->d_mlp_params};
+                    h->d_tree_mrec, h->d_tree_frec, h->d_counter, h->d_mlp_params};
     for (void *p : bufs) cudaFree(p);
     free_lists(h->lists_p);
     free_lists(h->lists_c);

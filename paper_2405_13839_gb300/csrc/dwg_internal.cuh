@@ -85,6 +85,12 @@ struct TreeLists {
     int64_t *d_near_off = nullptr;   // ngroups + 1 offsets into d_near
     int *d_far = nullptr, *d_near = nullptr;
     int64_t nfar = 0, nnear = 0;
+    // work items: (group, first record) of at most a fixed number of
+    // records each, their offsets per group and their partial sums
+    int64_t *d_item_off = nullptr;
+    int2 *d_items = nullptr;
+    float *d_ipart = nullptr;
+    int64_t nitems = 0;
     bool valid = false;
 };
 
@@ -164,7 +170,7 @@ struct Ctx {
     int path = DWG_PATH_AUTO;
     float tree_beta = 2.0f;            // 1 / opening angle
     int tree_leaf = 16;                // points per tree leaf (16, 32, 64 or 128)
-    int tree_group = 0;                // 1: opening test per 64-query group
+    int tree_group = 1;                // 1: opening test per 64-query group, 0: per query
     uint64_t tree_gen = 0;             // counts tree builds
     TreeLists lists_p, lists_c;        // group-test lists at the points and corners
     int tree_levels = 0;               // 2^tree_levels leaves
@@ -172,6 +178,7 @@ struct Ctx {
     double tree_beta_set = -1.0;
     double *d_tree_A = nullptr, *d_tree_C = nullptr, *d_tree_R = nullptr, *d_tree_M = nullptr;
     float4 *d_tree_rec = nullptr, *d_tree_mrec = nullptr;
+    float4 *d_tree_frec = nullptr;     // node as a duplicated 48-byte source record
     unsigned long long *d_counter = nullptr;  // kernel evaluations of the tree path
 
     // graph; bufgen counts reallocations of buffers a captured graph refers

@@ -166,13 +166,24 @@ __global__ void k_tree_level_moments(int64_t first, double *M)
     for (int k = 0; k < 3; ++k) M[3 * node + k] = __dadd_rn(M[3 * l + k], M[3 * r + k]);
 }
 
-__global__ void k_tree_moment_records(int64_t nn, const double *M, float4 *mrec)
+// m = M / (4 pi) as float; frec (may be NULL): the node as a 48-byte source
+// record (c and m, each value twice) like the point records, for the list
+// evaluation's bulk copies
+__global__ void k_tree_moment_records(int64_t nn, const double *M, const float4 *rec, float4 *mrec,
+                                      float4 *frec)
 {
     int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= nn) return;
     const double fpi = 4.0 * kPi;
-    mrec[node] = make_float4((float)__ddiv_rn(M[3 * node], fpi), (float)__ddiv_rn(M[3 * node + 1], fpi),
-                             (float)__ddiv_rn(M[3 * node + 2], fpi), 0.f);
+    const float mx = (float)__ddiv_rn(M[3 * node], fpi), my = (float)__ddiv_rn(M[3 * node + 1], fpi),
+                mz = (float)__ddiv_rn(M[3 * node + 2], fpi);
+    mrec[node] = make_float4(mx, my, mz, 0.f);
+    if (frec) {
+        const float4 c = rec[node];
+        frec[3 * node + 0] = make_float4(c.x, c.x, c.y, c.y);
+        frec[3 * node + 1] = make_float4(c.z, c.z, mx, mx);
+        frec[3 * node + 2] = make_float4(my, my, mz, mz);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -691,69 +702,177 @@ __global__ void __launch_bounds__(32 * kListWarps)
     }
 }
 
-// Evaluation of the lists: the warp stages far records (c, M / 4 pi) and
-// near leaves' point records in shared memory and runs the packed loop.
+// Evaluation of the lists.  A group's terms are one stream of 48-byte
+// records: its far nodes (frec) followed by its near leaves' points (the
+// source records; every leaf is read whole -- the last, partial leaf runs
+// into the padding records, which have zero moment and add exactly 0).  The
+// warp copies the stream in chunks of 64 records into shared memory with
+// cp.async (each lane two records, six 16-byte copies), double-buffered so
+// that the copy of chunk k+1 overlaps the packed evaluation of chunk k.
+constexpr int kLstChunk = 64;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// global address of record r of the group's stream
+__device__ __forceinline__ const float4 *lst_record(int64_t r, int64_t nf, int64_t f0, int64_t e0,
+                                                    const int *__restrict__ far_ids,
+                                                    const int *__restrict__ near_ids,
+                                                    const float4 *__restrict__ frec,
+                                                    const float4 *__restrict__ src4, int64_t nleaf,
+                                                    int bucket)
+{
+    if (r < nf) return frec + 3 * (int64_t)far_ids[f0 + r];
+    const int64_t rr = r - nf;
+    const int64_t leaf = near_ids[e0 + rr / bucket];
+    return src4 + 3 * ((leaf - nleaf) * bucket + rr % bucket);
+}
+
+// Work items: a group's stream is cut into items of at most kItemRecords
+// records so that no warp is left with a group whose box straddles a jump
+// of the Morton order (such a group opens most of the tree and would keep
+// one warp busy long after the rest of the grid has finished).  Each item
+// writes its (hi, lo) sums for the group's 64 queries; k_tree_combine adds
+// the items of a group in order (deterministic).
+constexpr int kItemRecords = 2048;
+
+__global__ void k_tree_items(const int64_t *__restrict__ far_off, const int64_t *__restrict__ near_off,
+                             int64_t ng, int bucket, int64_t *__restrict__ cnt)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const int64_t total = (far_off[g + 1] - far_off[g]) + (near_off[g + 1] - near_off[g]) * bucket;
+    cnt[g] = max((int64_t)1, (total + kItemRecords - 1) / kItemRecords);
+}
+
+__global__ void k_tree_item_table(const int64_t *__restrict__ item_off, int64_t ng,
+                                  int2 *__restrict__ items)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    for (int64_t i = item_off[g], j = 0; i < item_off[g + 1]; ++i, ++j)
+        items[i] = make_int2((int)g, (int)(j * kItemRecords));
+}
+
 template <bool GRAD, bool SCREENED>
 __global__ void __launch_bounds__(32 * kGrpWarps)
-    k_tree_eval_lists(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ rec,
-                      const float4 *__restrict__ mrec, const float *__restrict__ src, int64_t n,
-                      int levels, int bucket, const int64_t *__restrict__ far_off,
-                      const int *__restrict__ far_ids, const int64_t *__restrict__ near_off,
-                      const int *__restrict__ near_ids, EvalParams ep, float *__restrict__ part,
-                      int64_t stride, unsigned long long *__restrict__ counter,
+    k_tree_eval_lists(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ frec,
+                      const float *__restrict__ src, int64_t n, int levels, int bucket,
+                      const int64_t *__restrict__ far_off, const int *__restrict__ far_ids,
+                      const int64_t *__restrict__ near_off, const int *__restrict__ near_ids,
+                      const int2 *__restrict__ items, int64_t nitems, EvalParams ep,
+                      float *__restrict__ ipart, unsigned long long *__restrict__ counter,
                       const IterState *st)
 {
     if (st && cloud_idle(st)) return;  // finished cloud of a batch
-    __shared__ float4 farb_all[kGrpWarps][kGrpFar * 3];
-    __shared__ float4 nearb_all[kGrpWarps][kGrpNear * 3];
+    constexpr int NA = GRAD ? 4 : 1;
+    __shared__ float4 buf_all[kGrpWarps][2][kLstChunk * 3];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t g = (int64_t)blockIdx.x * kGrpWarps + wid;
+    const int64_t it = (int64_t)blockIdx.x * kGrpWarps + wid;
+    if (it >= nitems) return;
+    const int2 item = items[it];
+    const int64_t g = item.x;
     const int64_t q0 = g * kGrpQ;
-    if (q0 >= m) return;
     const GrpQueries G = grp_queries(q, m, q0, lane);
     const f2 qx = pk(G.qa.x, G.qb.x), qy = pk(G.qa.y, G.qb.y), qz = pk(G.qa.z, G.qb.z);
     const f2 zero = pk(0.f, 0.f);
     GrpAcc A;
     A.hw = A.lw = A.hgx = A.lgx = A.hgy = A.lgy = A.hgz = A.lgz = zero;
-    float4 *farb = farb_all[wid];
-    float4 *nearb = nearb_all[wid];
     const float4 *src4 = reinterpret_cast<const float4 *>(src);
     const int64_t nleaf = (int64_t)1 << levels;
-    unsigned long long terms = 0;
-    // far nodes, kGrpFar at a time: each lane stages two records
-    const int64_t f0 = far_off[g], f1 = far_off[g + 1];
-    for (int64_t b = f0; b < f1; b += kGrpFar) {
-        const int cnt = (int)min((int64_t)kGrpFar, f1 - b);
-        for (int t = lane; t < cnt; t += 32) {
-            const int node = far_ids[b + t];
-            const float4 cr = rec[node];
-            const float4 mm = mrec[node];
-            float4 *r = farb + 3 * t;
-            r[0] = make_float4(cr.x, cr.x, cr.y, cr.y);
-            r[1] = make_float4(cr.z, cr.z, mm.x, mm.x);
-            r[2] = make_float4(mm.y, mm.y, mm.z, mm.z);
+    const int64_t f0 = far_off[g], nf = far_off[g + 1] - f0;
+    const int64_t e0 = near_off[g], ne = near_off[g + 1] - e0;
+    const int64_t r_begin = item.y;
+    const int64_t r_end = min(r_begin + kItemRecords, nf + ne * bucket);
+    const int64_t nchunks = (r_end - r_begin + kLstChunk - 1) / kLstChunk;
+    auto issue = [&](int64_t chunk) {
+        float4 *b = buf_all[wid][chunk & 1];
+        const int64_t r0 = r_begin + chunk * kLstChunk;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = lane + 32 * h;
+            if (r0 + t < r_end) {
+                const float4 *from =
+                    lst_record(r0 + t, nf, f0, e0, far_ids, near_ids, frec, src4, nleaf, bucket);
+                cp_async16(b + 3 * t + 0, from + 0);
+                cp_async16(b + 3 * t + 1, from + 1);
+                cp_async16(b + 3 * t + 2, from + 2);
+            }
         }
-        __syncwarp();
-        grp_flush<GRAD, SCREENED>(A, farb, cnt, qx, qy, qz, ep);
-        terms += (unsigned long long)cnt;
-        __syncwarp();
-    }
-    // near leaves: their points' records, in list order
-    int near_cnt = 0;
-    auto flush_near = [&](int cnt) {
-        grp_flush<GRAD, SCREENED>(A, nearb, cnt, qx, qy, qz, ep);
-        terms += (unsigned long long)cnt;
+        cp_async_commit();
     };
-    const int64_t e0 = near_off[g], e1 = near_off[g + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-        const int64_t j0 = ((int64_t)near_ids[e] - nleaf) * bucket;
-        grp_take_leaf(src4, j0, (int)min((int64_t)bucket, n - j0), nearb, near_cnt, lane,
-                      flush_near);
+    if (nchunks > 0) issue(0);
+    for (int64_t k = 0; k < nchunks; ++k) {
+        if (k + 1 < nchunks) issue(k + 1);
+        else cp_async_commit();  // an empty group keeps the wait count uniform
+        cp_async_wait1();        // chunk k has landed (this lane's copies)
+        __syncwarp();            // ... and every lane's
+        const int cnt = (int)min((int64_t)kLstChunk, r_end - r_begin - k * kLstChunk);
+        grp_flush<GRAD, SCREENED>(A, buf_all[wid][k & 1], cnt, qx, qy, qz, ep);
+        __syncwarp();  // buffer k & 1 is reused by the copy of chunk k + 2
     }
-    __syncwarp();
-    if (near_cnt) flush_near(near_cnt);
-    grp_write<GRAD>(A, G, m, part, stride);
-    if (lane == 0 && counter) atomicAdd(counter, terms * (unsigned long long)G.nvalid);
+    // the item's sums: ipart[((it * NA + a) * 2 + h) * 64 + slot]
+    float *o = ipart + it * (int64_t)NA * 2 * kGrpQ;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int slot = lane + 32 * h2;
+        float a, b;
+        upk(A.hw, a, b); o[0 * kGrpQ + slot] = h2 ? b : a;
+        upk(A.lw, a, b); o[1 * kGrpQ + slot] = h2 ? b : a;
+        if (GRAD) {
+            upk(A.hgx, a, b); o[2 * kGrpQ + slot] = h2 ? b : a;
+            upk(A.lgx, a, b); o[3 * kGrpQ + slot] = h2 ? b : a;
+            upk(A.hgy, a, b); o[4 * kGrpQ + slot] = h2 ? b : a;
+            upk(A.lgy, a, b); o[5 * kGrpQ + slot] = h2 ? b : a;
+            upk(A.hgz, a, b); o[6 * kGrpQ + slot] = h2 ? b : a;
+            upk(A.lgz, a, b); o[7 * kGrpQ + slot] = h2 ? b : a;
+        }
+    }
+    if (counter && r_begin == 0) {
+        // terms per query of the whole group: far nodes and the leaves' real points
+        int64_t pts = 0;
+        for (int64_t e = lane; e < ne; e += 32) {
+            const int64_t j0 = ((int64_t)near_ids[e0 + e] - nleaf) * bucket;
+            pts += min((int64_t)bucket, n - j0);
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) pts += __shfl_xor_sync(0xffffffffu, pts, o2);
+        if (lane == 0)
+            atomicAdd(counter, (unsigned long long)(nf + pts) * (unsigned long long)G.nvalid);
+    }
+}
+
+// per query: the items of its group added in order (two-sum on the hi
+// parts, lo parts summed), written as the chunk-0 partials of the reduce
+template <bool GRAD>
+__global__ void k_tree_combine(const float *__restrict__ ipart, const int64_t *__restrict__ item_off,
+                               int64_t m, float *__restrict__ part, int64_t stride,
+                               const IterState *st)
+{
+    if (st && cloud_idle(st)) return;
+    constexpr int NA = GRAD ? 4 : 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t g = i / kGrpQ, slot = i % kGrpQ;
+    float h[NA], l[NA];
+    for (int a = 0; a < NA; ++a) { h[a] = 0.f; l[a] = 0.f; }
+    for (int64_t it = item_off[g]; it < item_off[g + 1]; ++it) {
+        const float *o = ipart + it * (int64_t)NA * 2 * kGrpQ;
+        for (int a = 0; a < NA; ++a) {
+            two_sum1(h[a], l[a], o[(2 * a) * kGrpQ + slot]);
+            l[a] = __fadd_rn(l[a], o[(2 * a + 1) * kGrpQ + slot]);
+        }
+    }
+    for (int a = 0; a < NA; ++a) {
+        part[(2 * a) * stride + i] = h[a];
+        part[(2 * a + 1) * stride + i] = l[a];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -778,6 +897,9 @@ static cudaError_t group_smem_attr(int dev)
 
 void free_lists(TreeLists &L)
 {
+    cudaFree(L.d_item_off);
+    cudaFree(L.d_items);
+    cudaFree(L.d_ipart);
     cudaFree(L.d_far_off);
     cudaFree(L.d_near_off);
     cudaFree(L.d_far);
@@ -817,6 +939,7 @@ int tree_lists(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool *built)
         int rc = scan_i64(c, cnt_f, L.d_far_off, ng, L.d_far_off + ng);
         if (!rc) rc = scan_i64(c, cnt_n, L.d_near_off, ng, L.d_near_off + ng);
         if (rc) return rc;
+        DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // cnt_f is reused below
         int herr = 0;
         DWG_CUDA_TRY(c, cudaMemcpyAsync(&L.nfar, L.d_far_off + ng, sizeof(int64_t),
                                         cudaMemcpyDeviceToHost, c->stream));
@@ -833,13 +956,29 @@ int tree_lists(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool *built)
         // the free memory, else keep walking the tree every iteration
         size_t free_b = 0, total_b = 0;
         DWG_CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
-        const double need = 4.0 * (double)(L.nfar + L.nnear);
+        const double need = 4.0 * (double)(L.nfar + L.nnear) +
+                            (8.0 + 4.0 * 8 * kGrpQ) * ((double)(L.nfar + L.nnear * c->tree_leaf) /
+                                                           kItemRecords + (double)ng);
         if (need > 0.5 * (double)free_b) return DWG_OK;
         DWG_CUDA_TRY(c, cudaMalloc(&L.d_far, std::max<int64_t>(L.nfar, 1) * sizeof(int)));
         DWG_CUDA_TRY(c, cudaMalloc(&L.d_near, std::max<int64_t>(L.nnear, 1) * sizeof(int)));
         k_tree_lists<true><<<blocks, 32 * kListWarps, 0, c->stream>>>(
             q, m, c->d_tree_rec, c->tree_levels, L.d_far_off, L.d_near_off, L.d_far, L.d_near,
             c->d_err);
+        DWG_CUDA_TRY(c, cudaGetLastError());
+        // work items and their partial-sum buffer
+        DWG_CUDA_TRY(c, cudaMalloc(&L.d_item_off, (ng + 1) * sizeof(int64_t)));
+        k_tree_items<<<(unsigned)ceil_div(ng, 256), 256, 0, c->stream>>>(
+            L.d_far_off, L.d_near_off, ng, c->tree_leaf, cnt_f);
+        DWG_CUDA_TRY(c, cudaGetLastError());
+        if ((rc = scan_i64(c, cnt_f, L.d_item_off, ng, L.d_item_off + ng))) return rc;
+        DWG_CUDA_TRY(c, cudaMemcpyAsync(&L.nitems, L.d_item_off + ng, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        DWG_CUDA_TRY(c, cudaMalloc(&L.d_items, L.nitems * sizeof(int2)));
+        DWG_CUDA_TRY(c, cudaMalloc(&L.d_ipart, L.nitems * 8 * kGrpQ * sizeof(float)));
+        k_tree_item_table<<<(unsigned)ceil_div(ng, 256), 256, 0, c->stream>>>(L.d_item_off, ng,
+                                                                              L.d_items);
         DWG_CUDA_TRY(c, cudaGetLastError());
         L.q = q;
         L.m = m;
@@ -868,6 +1007,8 @@ void free_tree(Ctx *c)
     cudaFree(c->d_tree_M);
     cudaFree(c->d_tree_rec);
     cudaFree(c->d_tree_mrec);
+    cudaFree(c->d_tree_frec);
+    c->d_tree_frec = nullptr;
     c->d_tree_A = c->d_tree_C = c->d_tree_R = c->d_tree_M = nullptr;
     c->d_tree_rec = c->d_tree_mrec = nullptr;
     c->tree_built = false;
@@ -892,6 +1033,7 @@ int build_tree(Ctx *c)
     DWG_CUDA_TRY(c, cudaMalloc(&c->d_tree_M, 3 * nn * sizeof(double)));
     DWG_CUDA_TRY(c, cudaMalloc(&c->d_tree_rec, nn * sizeof(float4)));
     DWG_CUDA_TRY(c, cudaMalloc(&c->d_tree_mrec, nn * sizeof(float4)));
+    DWG_CUDA_TRY(c, cudaMalloc(&c->d_tree_frec, 3 * nn * sizeof(float4)));
     DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_tree_A, 0, nn * sizeof(double), c->stream));
     DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_tree_M, 0, 3 * nn * sizeof(double), c->stream));
     double *Sp = nullptr;
@@ -941,8 +1083,8 @@ cudaError_t launch_tree_moments(Ctx *c)
         int64_t first = (int64_t)1 << lv;
         k_tree_level_moments<<<(unsigned)ceil_div(first, B), B, 0, c->stream>>>(first, c->d_tree_M);
     }
-    k_tree_moment_records<<<(unsigned)ceil_div(nn, B), B, 0, c->stream>>>(nn, c->d_tree_M,
-                                                                           c->d_tree_mrec);
+    k_tree_moment_records<<<(unsigned)ceil_div(nn, B), B, 0, c->stream>>>(
+        nn, c->d_tree_M, c->d_tree_rec, c->d_tree_mrec, c->d_tree_frec);
     return cudaGetLastError();
 }
 
@@ -966,11 +1108,12 @@ static cudaError_t launch_lists_t(Ctx *c, const TreeLists &L, float *part, int64
                                   const IterState *st)
 {
     EvalParams ep = make_eval_params(c);
-    const int64_t per_cta = (int64_t)kGrpWarps * kGrpQ;
-    k_tree_eval_lists<GRAD, SCREENED><<<(unsigned)ceil_div(L.m, per_cta), 32 * kGrpWarps, 0,
-                                         c->stream>>>(
-        L.q, L.m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->tree_levels, c->tree_leaf,
-        L.d_far_off, L.d_far, L.d_near_off, L.d_near, ep, part, stride, c->d_counter, st);
+    k_tree_eval_lists<GRAD, SCREENED><<<(unsigned)ceil_div(L.nitems, kGrpWarps), 32 * kGrpWarps,
+                                         0, c->stream>>>(
+        L.q, L.m, c->d_tree_frec, c->d_src, c->n, c->tree_levels, c->tree_leaf, L.d_far_off,
+        L.d_far, L.d_near_off, L.d_near, L.d_items, L.nitems, ep, L.d_ipart, c->d_counter, st);
+    k_tree_combine<GRAD><<<(unsigned)ceil_div(L.m, 256), 256, 0, c->stream>>>(
+        L.d_ipart, L.d_item_off, L.m, part, stride, st);
     return cudaGetLastError();
 }
 

@@ -124,6 +124,7 @@ def test_eval_torus_100k_sampled(dwglib, oracle_mod, handle):
     n0 = synth.random_unit_normals(n, seed=1).astype(np.float32)
     h = handle(p)
     dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_ALLPAIRS, 0.5)
     for kernel, lam in ((0, 0.0), (1, 10.0)):
         dwglib.dwg_set_params(h, kernel, eps, lam, 30, 0.1)
         dwglib.dwg_set_update(h, 8, 10, dwglib.DWG_UPDATE_LEVELSET)
