@@ -215,6 +215,8 @@ typedef struct {
     double interactions;     /* kernel evaluations of the last dwg_orient */
     double ms_orient;        /* device time of the last dwg_orient */
     double interactions_eval; /* kernel evaluations of the last dwg_eval_gwn */
+    double interactions_points_step;  /* dwg_profile_step: evaluations at the points */
+    double interactions_corners_step; /* dwg_profile_step: evaluations at the corners */
 } dwg_stats;
 
 int dwg_get_stats(dwg_handle h, dwg_stats *out);
@@ -245,8 +247,10 @@ int dwg_get_corners(dwg_handle h, int64_t *keys_out, int64_t cap, int64_t *count
  *   cloud gets its own root cube, octree, kNN tree, iso-value and
  *   convergence test; its default softening is its own (0.5 L / sqrt(n)) and
  *   its default octree depth is round(log2(n) / 2) clamped to [5, 10].
- *   dwg_set_params / dwg_set_update / dwg_set_tree on the batch handle apply
- *   to every cloud; dwg_set_init takes DWG_INIT_RANDOM (cloud c uses seed + c).
+ *   dwg_set_params / dwg_set_update / dwg_set_tree / dwg_set_convergence on
+ *   the batch handle apply to every cloud (dwg_set_params with eps = 0 keeps
+ *   each cloud's own default softening); dwg_set_init takes DWG_INIT_RANDOM
+ *   (cloud c uses seed + c).
  * dwg_orient_batch: runs every cloud until it converges (or max_iters); a
  *   converged cloud stops iterating while the others go on.  The whole loop
  *   is one CUDA graph launch; per iteration the all-pairs sums of every

@@ -240,8 +240,10 @@ static void invalidate_graph(Ctx *c)
 // the iteration body (Alg. 1, one pass of the repeat loop)
 // ---------------------------------------------------------------------------
 // ev (optional): 10 events recorded around the body's launches for profiling
+// snap (optional, device, 2 entries): the evaluation counter after the
+// point and after the corner evaluation (profiling of the tree path)
 static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
-                        cudaEvent_t *ev = nullptr)
+                        cudaEvent_t *ev = nullptr, unsigned long long *snap = nullptr)
 {
     int rc;
     auto mark = [&](int k) {
@@ -259,6 +261,9 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
         return rc;
     }
     mark(1);
+    if (snap)
+        cudaMemcpyAsync(snap, c->d_counter, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                        c->stream);
     if (launch_reduce_points(c, c->d_part_p, c->nchunks_p, c->n, c->d_p4, 1, true, c->d_wg,
                              c->d_wsum_blocks) != cudaSuccess)
         return fail(c, DWG_ERR_CUDA, "reduce launch failed");
@@ -276,6 +281,9 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
             return rc;
         }
         mark(4);
+        if (snap)
+            cudaMemcpyAsync(snap + 1, c->d_counter, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, c->stream);
         if (launch_reduce_w(c, c->d_part_c, c->nchunks_c, c->ncorners, c->d_wc) != cudaSuccess)
             return fail(c, DWG_ERR_CUDA, "reduce_w launch failed");
         mark(5);
@@ -381,7 +389,8 @@ static int prepare_normals(Ctx *c)
                     DWG_CUDA_TRY(c, cudaMalloc(&Y, c->n * 3 * sizeof(float)));
                     DWG_CUDA_TRY(c, cudaMalloc(&cR, 4 * sizeof(double)));
                     if (launch_features(c, X, false, cR) != cudaSuccess ||
-                        launch_mlp_forward(c->d_mlp_params, X, c->n, Y, c->stream) != cudaSuccess ||
+                        launch_mlp_forward(c->d_mlp_params, X, c->n, Y, c->stream, c->d_err) !=
+                            cudaSuccess ||
                         launch_normals_from_y(c, Y) != cudaSuccess)
                         return fail(c, DWG_ERR_CUDA, "learned init launch failed");
                     DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -593,7 +602,9 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
     if (!h) return DWG_ERR_INVALID;
     if (kernel != DWG_KERNEL_PLAIN && kernel != DWG_KERNEL_SCREENED)
         return fail(h, DWG_ERR_INVALID, "kernel must be DWG_KERNEL_PLAIN or DWG_KERNEL_SCREENED");
-    if (!(eps > 0.f) || !isfinite(eps)) return fail(h, DWG_ERR_INVALID, "eps must be > 0");
+    const bool keep_eps = h->is_batch && eps == 0.f;  // each cloud keeps its own softening
+    if (!keep_eps && (!(eps > 0.f) || !isfinite(eps)))
+        return fail(h, DWG_ERR_INVALID, "eps must be > 0 (0 on a batch handle: per-cloud default)");
     if (!(screening >= 0.f) || !isfinite(screening))
         return fail(h, DWG_ERR_INVALID, "screening must be >= 0");
     if (max_iters < 1 || max_iters > 100000)
@@ -604,9 +615,10 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
     h->lambda = screening;
     h->max_iters = max_iters;
     h->tol = tol;
-    h->eps_given = true;
+    h->eps_given = !keep_eps;
     invalidate_graph(h);
-    for (dwg_ctx *c : h->clouds) dwg_set_params(c, kernel, eps, screening, max_iters, tol);
+    for (dwg_ctx *c : h->clouds)
+        dwg_set_params(c, kernel, keep_eps ? c->eps : eps, screening, max_iters, tol);
     return DWG_OK;
 }
 
@@ -871,9 +883,24 @@ int dwg_profile_step(dwg_handle h, float *ms_out, int cap, int *count)
     LAUNCH_CHECK(h);
     cudaEvent_t ev[10];
     for (int k = 0; k < 10; ++k) DWG_CUDA_TRY(h, cudaEventCreate(&ev[k]));
+    unsigned long long *snap = nullptr, hs[2] = {0, 0};
+    DWG_CUDA_TRY(h, cudaMalloc(&snap, 2 * sizeof(unsigned long long)));
+    DWG_CUDA_TRY(h, cudaMemsetAsync(snap, 0, 2 * sizeof(unsigned long long), h->stream));
     cudaGraphConditionalHandle none = 0;
-    rc = enqueue_body(h, none, 0, ev);
+    rc = enqueue_body(h, none, 0, ev, snap);
     cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hs, snap, sizeof(hs), cudaMemcpyDeviceToHost);
+    cudaFree(snap);
+    if (use_tree(h)) {
+        h->stats.interactions_points_step = (double)hs[0];
+        h->stats.interactions_corners_step =
+            h->mode == DWG_UPDATE_LEVELSET ? (double)(hs[1] - hs[0]) : 0.0;
+    } else {
+        h->stats.interactions_points_step = (double)h->n * (double)h->n;
+        h->stats.interactions_corners_step =
+            h->mode == DWG_UPDATE_LEVELSET ? (double)h->ncorners * (double)h->n : 0.0;
+    }
     float ms[9] = {0};
     for (int k = 0; k < 9; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
     for (int k = 0; k < 10; ++k) cudaEventDestroy(ev[k]);
@@ -1111,7 +1138,13 @@ int dwg_mlp_forward(const float *params, const float *X, int64_t B, float *Y, vo
     int rc = mlp_check({params, X, Y}, B);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    return mlp_finish(launch_mlp_forward(params, X, B, Y, s), s);
+    rc = mlp_finish(launch_mlp_forward(params, X, B, Y, s, nullptr), s);
+    if (rc) return rc;
+    if (mlp_forward_error(s) != 0) {
+        set_global_error("dwg_mlp_forward: a tensor-core wait gave up");
+        return DWG_ERR_TIMEOUT;
+    }
+    return DWG_OK;
 }
 
 int dwg_mlp_grad(const float *params, const float *X, const float *T, int64_t B, float *grad,

@@ -336,7 +336,11 @@ cudaError_t launch_normals_from_y(Ctx *c, const float *Y);
 
 // dwg_mlp.cu
 constexpr int kMlpParamCount = 12675;
-cudaError_t launch_mlp_forward(const float *P, const float *X, int64_t B, float *Y, cudaStream_t s);
+// err: device flag for a wait that gave up (NULL: the library's own flag,
+// read and cleared by mlp_forward_error)
+cudaError_t launch_mlp_forward(const float *P, const float *X, int64_t B, float *Y, cudaStream_t s,
+                               int *err);
+int mlp_forward_error(cudaStream_t s);
 cudaError_t launch_mlp_grad(const float *P, const float *X, const float *T, int64_t B, float *grad,
                             double *loss, cudaStream_t s);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int step, float lr,

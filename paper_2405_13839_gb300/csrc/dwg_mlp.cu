@@ -5,16 +5,18 @@
 // Network: 64 inputs (16 neighbour offsets scaled by the patch radius, the
 // point's position relative to the cloud centroid, zero padding), three
 // hidden layers of 64 with ReLU, 3 outputs (the normal before
-// normalisation).  Weights are rounded to bfloat16 and every layer is a
-// tensor-core product (mma.sync m16n8k16, bf16 x bf16 -> fp32); biases,
-// accumulators, the loss and the optimiser state are fp32.
+// normalisation).  Weights and activations are rounded to bfloat16 and every
+// layer is a tensor-core product with fp32 accumulation; biases, the loss
+// and the optimiser state are fp32.
 //
 // Kernels:
-//   k_mlp_forward   rows of X -> Y (inference; 16 rows per warp, the
-//                   accumulator fragments of one layer are the A fragments
-//                   of the next, no shared-memory round trip);
+//   k_mlp_forward_tc  rows of X -> Y (inference) on the tcgen05 tensor cores:
+//                   128-row tiles, operands in shared memory, accumulators
+//                   in tensor memory;
 //   k_mlp_grad      forward + backward of the mean squared error over a
-//                   batch: dY W4, dZ3 W3, dZ2 W2 on tensor cores, weight
+//                   batch on the warp-level tensor-core instruction
+//                   (mma.sync m16n8k16, the fragments of one layer feed the
+//                   next in registers): dY W4, dZ3 W3, dZ2 W2, weight
 //                   gradients dZ^T H on tensor cores from per-warp shared
 //                   stashes, summed per CTA in shared memory, then added to
 //                   the global gradient;
@@ -177,32 +179,232 @@ __device__ __forceinline__ void out_layer(const MlpSmem &S, const uint32_t (&a)[
     for (int e = 0; e < 4; ++e) y[e] += S.b4[2 * t + (e & 1)];
 }
 
-__global__ void __launch_bounds__(32 * kMlpWarps)
-    k_mlp_forward(const float *__restrict__ P, const float *__restrict__ X, int64_t B,
-                  float *__restrict__ Y)
+// --- inference on the 5th-generation tensor cores (tcgen05) -----------------
+//
+// One CTA of 128 threads runs tiles of 128 rows (persistent over the tiles).
+// Every layer is D (128 x N, fp32, in tensor memory) = A (128 x 64, bf16,
+// shared memory) x W^T (W: N x 64 bf16, shared memory), issued by one thread
+// as four K = 16 steps of tcgen05.mma (kind::f16, M = 128, N = 64, or 16 for
+// the output layer whose rows 3..15 are zero).  Both operands are K-major
+// in the canonical no-swizzle layout: 8 x 16-byte core matrices, 128 bytes
+// apart along K (leading byte offset) and 1024 bytes apart along the rows
+// (stride byte offset).  tcgen05.commit signals an mbarrier when the layer's
+// MMAs are done; each thread then reads its row (thread t = tensor-memory
+// lane t) with tcgen05.ld, adds the bias, applies ReLU, rounds to bf16 and
+// writes the row back into the A buffer for the next layer.
+constexpr int kTcRows = 128;
+constexpr int kTcCols = 64;  // tensor-memory columns (fp32 accumulator of N <= 64)
+
+struct MlpTcSmem {
+    uint16_t W[3][64 * 64];   // canonical K-major layout, see tc_off
+    uint16_t W4[16 * 64];     // output layer, rows 3..15 zero
+    uint16_t A[kTcRows * 64]; // activations of the current layer
+    float b[3][64];
+    float b4[16];
+    uint64_t bar;
+    uint32_t tmem_base;
+};
+
+// element (r, k) of a K-major bf16 operand with 64 columns: core matrix
+// (r / 8, k / 8) of 8 rows x 16 bytes, cores 128 bytes apart along K
+__device__ __forceinline__ int tc_off(int r, int k)
 {
-    __shared__ MlpSmem S;
-    load_weights(P, S, nullptr);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    for (int64_t row0 = ((int64_t)blockIdx.x * kMlpWarps + warp) * 16; row0 < B;
-         row0 += (int64_t)gridDim.x * kMlpRows) {
-        uint32_t a[4][4], mask;
-        float acc[8][4], y[4];
-        load_x(X, row0, B, a, lane);
-        for (int l = 0; l < 3; ++l) {
-            layer_mma(S.W[l], a, acc, lane);
-            bias_relu(acc, S.b[l], a, mask, lane);
-        }
-        out_layer(S, a, y, lane);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            int col = 2 * t + (e & 1);
-            int64_t r = row0 + g + (e >= 2 ? 8 : 0);
-            if (col < 3 && r < B) Y[r * 3 + col] = y[e];
-        }
+    return (((r >> 3) * 8 + (k >> 3)) * 64) + (r & 7) * 8 + (k & 7);  // in bf16 elements
+}
+
+// shared-memory matrix descriptor: start address, leading byte offset 128,
+// stride byte offset 1024, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(const void *p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t tc_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
     }
+    return false;
+}
+
+// 16 consecutive fp32 columns of this thread's lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcRows)
+    k_mlp_forward_tc(const float *__restrict__ P, const float *__restrict__ X, int64_t B,
+                     float *__restrict__ Y, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    MlpTcSmem &S = *reinterpret_cast<MlpTcSmem *>(tc_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // weights and biases, bf16 in the canonical layout
+    for (int i = tid; i < 64 * 64; i += kTcRows) {
+        const int o = i / 64, k = i % 64;
+        S.W[0][tc_off(o, k)] = bf16_bits(P[kOffW1 + i]);
+        S.W[1][tc_off(o, k)] = bf16_bits(P[kOffW2 + i]);
+        S.W[2][tc_off(o, k)] = bf16_bits(P[kOffW3 + i]);
+    }
+    for (int i = tid; i < 16 * 64; i += kTcRows) {
+        const int o = i / 64, k = i % 64;
+        S.W4[tc_off(o, k)] = o < 3 ? bf16_bits(P[kOffW4 + i]) : (uint16_t)0;
+    }
+    for (int i = tid; i < 64; i += kTcRows) {
+        S.b[0][i] = P[kOffB1 + i];
+        S.b[1][i] = P[kOffB2 + i];
+        S.b[2][i] = P[kOffB3 + i];
+    }
+    if (tid < 16) S.b4[tid] = tid < 3 ? P[kOffB4 + tid] : 0.f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&S.bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&S.tmem_base)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem_base;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (B + kTcRows - 1) / kTcRows;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t row0 = tile * kTcRows;
+        // the tile's rows of X (coalesced float4 reads) -> bf16 A
+        const float4 *X4 = reinterpret_cast<const float4 *>(X + row0 * 64);
+        for (int e = tid; e < kTcRows * 16; e += kTcRows) {
+            const int r = e >> 4, c4 = e & 15;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row0 + r < B) v = X4[e];
+            uint2 packed = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+            *reinterpret_cast<uint2 *>(&S.A[tc_off(r, 4 * c4)]) = packed;
+        }
+        for (int l = 0; l < 4 && ok; ++l) {
+            const uint16_t *W = l < 3 ? S.W[l] : S.W4;
+            const int N = l < 3 ? 64 : 16;
+            // A written by the threads -> visible to the tensor cores
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t idesc = tc_idesc(N);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc_mma(tmem, tc_desc(&S.A[tc_off(0, 16 * kk)]), tc_desc(&W[tc_off(0, 16 * kk)]),
+                           idesc, kk > 0 ? 1u : 0u);
+                tc_commit(&S.bar);
+            }
+            // every thread waits; the outcome is made uniform before anyone
+            // leaves the loop, so that no barrier below is skipped by a part
+            // of the block
+            const bool got = tc_wait(&S.bar, phase);
+            if (!__syncthreads_and(got)) {
+                ok = false;
+                if (tid == 0) atomicOr(err, kErrTimeout);
+                break;
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int r = tid;
+            if (l < 3) {
+                const float *bias = S.b[l];
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float v[16];
+                    tc_ld16(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4) {
+                        float z0 = fmaxf(v[i] + bias[c0 + i], 0.f);
+                        float z1 = fmaxf(v[i + 1] + bias[c0 + i + 1], 0.f);
+                        float z2 = fmaxf(v[i + 2] + bias[c0 + i + 2], 0.f);
+                        float z3 = fmaxf(v[i + 3] + bias[c0 + i + 3], 0.f);
+                        *reinterpret_cast<uint2 *>(&S.A[tc_off(r, c0 + i)]) =
+                            make_uint2(pack_bf16(z0, z1), pack_bf16(z2, z3));
+                    }
+                }
+            } else {
+                float v[16];
+                tc_ld16(lane_addr, v);
+                if (row0 + r < B) {
+                    Y[(row0 + r) * 3 + 0] = v[0] + S.b4[0];
+                    Y[(row0 + r) * 3 + 1] = v[1] + S.b4[1];
+                    Y[(row0 + r) * 3 + 2] = v[2] + S.b4[2];
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // A and the accumulator are reused by the next tile
+    }
+    if (!ok && tid == 0) {
+        // let any MMA still in flight finish (bounded) before the memory goes
+        tc_wait(&S.bar, phase);
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTcCols)
+                     : "memory");
 }
 
 // --- training -------------------------------------------------------------
@@ -449,11 +651,31 @@ static int mlp_sms()
     return v > 0 ? v : 148;
 }
 
-cudaError_t launch_mlp_forward(const float *P, const float *X, int64_t B, float *Y, cudaStream_t s)
+// device flag for the forward calls that have no handle (dwg_mlp_forward)
+static __device__ int g_mlp_err;
+
+cudaError_t launch_mlp_forward(const float *P, const float *X, int64_t B, float *Y, cudaStream_t s,
+                               int *err)
 {
-    int64_t blocks = std::min<int64_t>(ceil_div(B, kMlpRows), (int64_t)mlp_sms() * 8);
-    k_mlp_forward<<<(unsigned)std::max<int64_t>(blocks, 1), 32 * kMlpWarps, 0, s>>>(P, X, B, Y);
+    if (!err) {
+        cudaError_t e = cudaGetSymbolAddress((void **)&err, g_mlp_err);
+        if (e != cudaSuccess) return e;
+    }
+    int64_t blocks = std::min<int64_t>(ceil_div(B, kTcRows), (int64_t)mlp_sms() * 4);
+    k_mlp_forward_tc<<<(unsigned)std::max<int64_t>(blocks, 1), kTcRows, sizeof(MlpTcSmem), s>>>(
+        P, X, B, Y, err);
     return cudaGetLastError();
+}
+
+int mlp_forward_error(cudaStream_t s)
+{
+    int *d = nullptr, h = 0;
+    if (cudaGetSymbolAddress((void **)&d, g_mlp_err) != cudaSuccess) return -1;
+    if (cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -1;
+    if (h) cudaMemsetAsync(d, 0, sizeof(int), s);
+    return h;
 }
 
 cudaError_t launch_mlp_grad(const float *P, const float *X, const float *T, int64_t B, float *grad,

@@ -55,7 +55,9 @@ class dwg_stats(ctypes.Structure):
                 ("converged", ctypes.c_int), ("faces_last", ctypes.c_int64),
                 ("iso_last", ctypes.c_double), ("stat_last", ctypes.c_double),
                 ("interactions", ctypes.c_double), ("ms_orient", ctypes.c_double),
-                ("interactions_eval", ctypes.c_double)]
+                ("interactions_eval", ctypes.c_double),
+                ("interactions_points_step", ctypes.c_double),
+                ("interactions_corners_step", ctypes.c_double)]
 
 
 class dwg_tuning(ctypes.Structure):

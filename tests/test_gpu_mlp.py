@@ -31,8 +31,10 @@ def test_features_match_reference(dwglib):
     assert close.mean() >= 0.999, close.mean()
 
 
-@pytest.mark.parametrize("B", [1, 15, 16, 64, 1000, 4097])
+@pytest.mark.parametrize("B", [1, 15, 16, 64, 127, 128, 129, 1000, 4097, 200003])
 def test_forward_matches_bf16_reference(dwglib, torch, B):
+    """The tcgen05 forward: single rows, partial and whole 128-row tiles, and
+    more tiles than the persistent grid has CTAs."""
     theta = mlp.init_params(1)
     X = synth.normal(2, 1, B * 64).reshape(B, 64)
     Y = torch.zeros((B, 3), dtype=torch.float32, device="cuda")
