@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--one-step", action="store_true",
                     help="run one iteration of the workload and exit (for profiler captures)")
+    ap.add_argument("--init", default="random", choices=["random", "learned"],
+                    help="initial normals of --one-step (learned: the warm-start network runs)")
     return ap.parse_args()
 
 
@@ -170,13 +172,20 @@ def flush_l2(torch, buf):
     buf.add_(1.0)  # writes 256 MiB, larger than the 129 MB L2
 
 
-def agreement(out, nt):
+def agreement(out, nt, labels=None):
     """Share of points whose normal agrees in sign with the analytic one,
     after aligning the global sign (points without an analytic normal, the
-    outliers, are left out)."""
+    outliers, are left out).  With labels (the primitive of each sample of a
+    union of shapes), the sign is aligned per label: each connected part of
+    the surface is oriented on its own."""
     m = np.linalg.norm(nt, axis=1) > 0
     d = np.sum(np.asarray(out, np.float64)[m] * nt[m], axis=1)
-    s = 1.0 if d.sum() >= 0 else -1.0
+    if labels is None:
+        s = 1.0 if d.sum() >= 0 else -1.0
+        return float(np.mean(s * d > 0))
+    lab = np.asarray(labels)[m]
+    sums = np.bincount(lab, weights=d)
+    s = np.where(sums >= 0, 1.0, -1.0)[lab]
     return float(np.mean(s * d > 0))
 
 
@@ -245,7 +254,8 @@ def warm_start_compare(dwg, torch, dev, W, tuning, weights, max_iters):
                 sec = time.perf_counter() - t0
             st = dwg.dwg_get_stats(h)
             out[init] = {"s": sec, "iterations": it, "converged": rc == dwg.DWG_OK,
-                         "agreement": agreement(res.cpu().numpy(), W["normals_true"]),
+                         "agreement": agreement(res.cpu().numpy(), W["normals_true"],
+                                                W.get("labels")),
                          "top1_stat_deg_last": st["stat_last"]}
         finally:
             dwg.dwg_destroy(h)
@@ -266,7 +276,7 @@ def warm_start_compare(dwg, torch, dev, W, tuning, weights, max_iters):
             dwg.dwg_set_convergence(h, dwg.DWG_CONV_MEAN)
             dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
             dwg.dwg_orient(h, res)
-            if agreement(res.cpu().numpy(), W["normals_true"]) >= target:
+            if agreement(res.cpu().numpy(), W["normals_true"], W.get("labels")) >= target:
                 hi = mid
             else:
                 lo = mid
@@ -333,7 +343,7 @@ def run_ours(args, rank, world, local):
     ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(ms) / 1e3
     st_orient = dwg.dwg_get_stats(h)
-    agree = agreement(out.cpu().numpy(), W["normals_true"])
+    agree = agreement(out.cpu().numpy(), W["normals_true"], W.get("labels"))
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([dev_s, inter], dtype=torch.float64)
@@ -417,7 +427,8 @@ def run_ours(args, rank, world, local):
     warm = None
     if not args.no_warm and world == 1:
         warm = warm_start_compare(dwg, torch, dev, W, tuning, a_dev, max(100, W["max_iters"]))
-    launches_per_step = 3 + 9 * statistics.mean(it_list)  # reset, random init, pack + 9 per iteration
+    # reset, random init, pack, then the graph's kernels once per iteration
+    launches_per_step = 3 + st_orient["kernels_per_iteration"] * statistics.mean(it_list)
     return dict(value=value, dev_s=dev_s, ms=ms, iters=it_list, rcs=rc_list, st=st_orient,
                 roof=roof, clocks=ck, e2e=e2e, wall=wall, agree=agree, tuning=tuning, warm=warm,
                 launches=int(round(launches_per_step * args.steps)), W=W, nc=nc)
@@ -468,7 +479,12 @@ def one_step(args):
     h = dwg.dwg_create(W["points"])
     configure(dwg, h, W, W["weights"])
     tune(dwg, h, W, args)
-    dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
+    if args.init == "learned":
+        from paper_2405_13839_gb300 import train_init
+        params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)
+        dwg.dwg_set_init(h, dwg.DWG_INIT_LEARNED, 1, params)
+    else:
+        dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
     iso, stat = dwg.dwg_step(h)
     torch.cuda.synchronize()
     t = dwg.dwg_get_tuning(h)
@@ -616,6 +632,9 @@ def main():
         "converged": r["rcs"][0] == 0,
         "top1_stat_deg_last": r["st"]["stat_last"],
         "agreement_with_analytic_normals": r["agree"],
+        "agreement_basis": ("sign aligned per primitive of the union (each connected part is "
+                            "oriented on its own)" if W.get("labels") is not None else
+                            "one global sign"),
         "warm_start": r["warm"],
         "interactions_per_step": r["value"] * r["dev_s"] / args.steps / world,
         "roofline": r["roof"], "cpu_baseline": cpu, "clocks": r["clocks"], "e2e": r["e2e"],

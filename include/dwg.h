@@ -217,6 +217,7 @@ typedef struct {
     double interactions_eval; /* kernel evaluations of the last dwg_eval_gwn */
     double interactions_points_step;  /* dwg_profile_step: evaluations at the points */
     double interactions_corners_step; /* dwg_profile_step: evaluations at the corners */
+    int kernels_per_iteration;        /* kernel launches in one iteration of the graph */
 } dwg_stats;
 
 int dwg_get_stats(dwg_handle h, dwg_stats *out);

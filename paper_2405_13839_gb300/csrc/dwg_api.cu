@@ -303,6 +303,21 @@ static int enqueue_body(Ctx *c, cudaGraphConditionalHandle cond, int use_cond,
     return DWG_OK;
 }
 
+// kernel launches in a captured graph (the iteration body)
+static int count_kernel_nodes(cudaGraph_t g)
+{
+    size_t num = 0;
+    if (cudaGraphGetNodes(g, nullptr, &num) != cudaSuccess || num == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(num);
+    if (cudaGraphGetNodes(g, nodes.data(), &num) != cudaSuccess) return 0;
+    int k = 0;
+    for (size_t i = 0; i < num; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 static int build_graph(Ctx *c)
 {
     invalidate_graph(c);
@@ -345,6 +360,7 @@ static int build_graph(Ctx *c)
         if (rc) return rc;
         return fail(c, DWG_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
     }
+    c->stats.kernels_per_iteration = count_kernel_nodes(body);
     e = cudaGraphInstantiate(&c->graph_exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -460,6 +476,7 @@ void dwg_destroy(dwg_handle h)
                     h->d_dtheta, h->d_wg, h->d_bvh_lo, h->d_bvh_hi, h->d_leaves,
                     h->d_leaf_corners, h->d_corner_keys, h->d_corner_pos, h->d_wc, h->d_faces,
                     h->d_acc, h->d_part_p, h->d_part_c, h->d_wsum_blocks, h->d_dn_blocks,
+                    h->d_sel, h->d_sel_hist, h->d_sel_part,
                     h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err,
                     h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
                     h->d_tree_mrec, h->d_tree_frec, h->d_counter, h->d_mlp_params};
@@ -536,6 +553,10 @@ static int create_impl(dwg_ctx *c, const float *points, int64_t n)
         c->wsum_blocks = wsum_block_count(n);
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_wsum_blocks, c->wsum_blocks * sizeof(double)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_dn_blocks, ceil_div(n, 256) * sizeof(double)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_sel, sizeof(SelState)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_sel_hist, kSelBins * sizeof(unsigned)));
+        DWG_CUDA_TRY(c, cudaMemsetAsync(c->d_sel_hist, 0, kSelBins * sizeof(unsigned), c->stream));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_sel_part, select_blocks(n) * sizeof(double)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_state, sizeof(IterState)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_counter, sizeof(unsigned long long)));
         k_iter_reset<<<1, 1, 0, c->stream>>>(c->d_state, c->max_iters, nullptr);
@@ -1378,6 +1399,8 @@ static int batch_build_graph(dwg_ctx *h)
     rc = batch_body(h, cond);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(h->stream, &captured);
+    if (!rc && e == cudaSuccess)
+        h->stats.kernels_per_iteration = count_kernel_nodes(cp.conditional.phGraph_out[0]);
     h->stream = saved;
     for (dwg_ctx *c : h->clouds) c->stream = saved;
     if (rc || e != cudaSuccess) {

@@ -51,6 +51,14 @@ __device__ __forceinline__ bool cloud_idle(const IterState *st)
 }
 #endif
 
+// radix-select state of the convergence statistic (device)
+struct SelState {
+    unsigned prefix;     // bits of the threshold found so far
+    unsigned krem;       // rank still to find below the prefix
+    unsigned above;      // values strictly above the threshold
+    unsigned pad;
+};
+
 struct EvalParams {
     float eps2;        // eps^2
     float s;           // sqrt(lambda)
@@ -158,6 +166,10 @@ struct Ctx {
     double *d_wsum_blocks = nullptr;  // per-block w sums at the points
     int wsum_blocks = 0;
     double *d_dn_blocks = nullptr;    // per-block sums of |n_new - n_old|
+    // convergence select: state, 4096 global bins, per-block partial sums
+    SelState *d_sel = nullptr;
+    unsigned *d_sel_hist = nullptr;
+    double *d_sel_part = nullptr;
 
     // iteration state and traces
     IterState *d_state = nullptr;
@@ -328,6 +340,7 @@ cudaError_t launch_mc_faces(Ctx *c);
 cudaError_t launch_knn_scatter(Ctx *c);
 cudaError_t launch_normal_update(Ctx *c);
 cudaError_t launch_select(Ctx *c, cudaGraphConditionalHandle cond, int use_cond);
+int select_blocks(int64_t n);
 cudaError_t launch_random_normals(float4 *nrm, const int64_t *perm, int64_t n, uint64_t seed,
                                   cudaStream_t s);
 cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t *idx_out);

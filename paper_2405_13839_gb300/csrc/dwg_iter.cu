@@ -14,6 +14,8 @@
 //   k_select       convergence statistic of Sec. 5.1: mean of the
 //                  ceil(n / 100) largest changes, by exact three-level radix
 //                  select on the float bits, then the loop condition.
+#include <algorithm>
+
 #include "dwg_internal.cuh"
 
 namespace dwg {
@@ -108,10 +110,14 @@ __device__ __forceinline__ bool tet_face(const F3 x[4], const float f[4], const 
     return true;
 }
 
+// Faces of the level set.  Each face record also carries, in the centroid's
+// w, the position in the Morton-sorted points of the face's leaf cell (found
+// once per cut leaf): the k-nearest search of its faces starts there.
 __global__ void __launch_bounds__(256)
-    k_mc_faces(const int *__restrict__ leaf_corners, int64_t nl, const float4 *__restrict__ cpos,
-               const float *__restrict__ wc, IterState *st, float4 *__restrict__ faces,
-               int64_t max_faces, int *err)
+    k_mc_faces(const int *__restrict__ leaf_corners, const int4 *__restrict__ leaves, int64_t nl,
+               const float4 *__restrict__ cpos, const float *__restrict__ wc,
+               const uint64_t *__restrict__ codes, int64_t n, IterState *st,
+               float4 *__restrict__ faces, int64_t max_faces, int *err)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,6 +149,18 @@ __global__ void __launch_bounds__(256)
             if (tet_face(xt, ft, at, area[cnt], cen[cnt])) ++cnt;
         }
     }
+    int seed = 0;
+    if (cnt > 0) {
+        const int4 L = leaves[l];
+        const uint64_t code = ((uint64_t)(uint32_t)L.y | ((uint64_t)(uint32_t)L.z << 32))
+                              << (3 * (kMortonBits - L.x));
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(&codes[mid]) < code) lo = mid + 1; else hi = mid;
+        }
+        seed = (int)lo;
+    }
     // warp-aggregated append
     const int lane = threadIdx.x & 31;
     int incl = cnt;
@@ -161,7 +179,7 @@ __global__ void __launch_bounds__(256)
             break;
         }
         faces[2 * o] = make_float4(area[k].x, area[k].y, area[k].z, 0.f);
-        faces[2 * o + 1] = make_float4(cen[k].x, cen[k].y, cen[k].z, 0.f);
+        faces[2 * o + 1] = make_float4(cen[k].x, cen[k].y, cen[k].z, __int_as_float(seed));
     }
 }
 
@@ -223,7 +241,8 @@ __device__ __forceinline__ void knn_insert(uint64_t key, int j, int k, uint64_t 
 // Morton code in the sorted order, which bounds the search ball before the
 // depth-first descent (nearer child first) prunes the bucket tree.
 template <int KMAX, bool FIXED>
-__device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *bj, int *err)
+__device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *bj, int *err,
+                                           int64_t seed = -1)
 {
     uint64_t best[KMAX];
 #pragma unroll
@@ -232,14 +251,19 @@ __device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *b
         bj[t] = -1;
     }
     const int kk = FIXED ? KMAX : k;
-    // seed: the sorted neighbours of q's position on the Morton curve
-    uint64_t code = morton3((uint64_t)quant21(q.x, T.cube_lo[0], T.inv_h21),
-                            (uint64_t)quant21(q.y, T.cube_lo[1], T.inv_h21),
-                            (uint64_t)quant21(q.z, T.cube_lo[2], T.inv_h21));
-    int64_t lo = 0, hi = T.n;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (__ldg(&T.codes[mid]) < code) lo = mid + 1; else hi = mid;
+    // seed: the sorted neighbours of q's position on the Morton curve (or a
+    // given position near q)
+    int64_t lo = seed;
+    if (lo < 0) {
+        uint64_t code = morton3((uint64_t)quant21(q.x, T.cube_lo[0], T.inv_h21),
+                                (uint64_t)quant21(q.y, T.cube_lo[1], T.inv_h21),
+                                (uint64_t)quant21(q.z, T.cube_lo[2], T.inv_h21));
+        int64_t hi = T.n;
+        lo = 0;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (__ldg(&T.codes[mid]) < code) lo = mid + 1; else hi = mid;
+        }
     }
     const int64_t s0 = max((int64_t)0, lo - kk), s1 = min(T.n, lo + kk);
     for (int64_t j = s0; j < s1; ++j) {
@@ -298,7 +322,7 @@ __global__ void __launch_bounds__(128)
     if (f >= nf) return;
     float4 A = faces[2 * f], C = faces[2 * f + 1];
     int bj[KMAX];
-    knn_search<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, bj, err);
+    knn_search<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, bj, err, (int64_t)__float_as_int(C.w));
     long long vx = llrint((double)A.x * scale);
     long long vy = llrint((double)A.y * scale);
     long long vz = llrint((double)A.z * scale);
@@ -546,46 +570,74 @@ __device__ void find_bin(const unsigned *hist, int nb, unsigned k, unsigned *war
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSelThreads)
-    k_select(const float *__restrict__ dtheta, int64_t n, float tol, int rule, IterState *st,
-             const double *__restrict__ dn_blocks, int ndn, double *tr_iso, double *tr_stat,
-             double *tr_dn, long long *tr_faces, cudaGraphConditionalHandle cond, int use_cond)
+// The exact k-th largest change by a three-level radix select on the float
+// bits (non-negative floats order like their bit patterns): bits 31..20,
+// 19..8, 7..0.  Each level is a histogram over all changes by many CTAs
+// (shared-memory bins, then integer atomics into the global bins: exact)
+// and one CTA that finds the bin holding the k-th largest; then a grid sums
+// the changes strictly above the threshold into per-block FP64 partials
+// and one CTA adds the partials in a fixed order and takes the decision.
+constexpr int kSelGridThreads = 256;
+
+__global__ void __launch_bounds__(kSelGridThreads)
+    k_sel_hist(const float *__restrict__ dtheta, int64_t n, int level,
+               const SelState *__restrict__ ss, unsigned *__restrict__ hist, const IterState *st)
 {
-    if (cloud_idle(st)) return;  // finished cloud of a batch
-    __shared__ unsigned hist[kSelBins];
+    if (cloud_idle(st)) return;
+    __shared__ unsigned h[kSelBins];
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned *bits = reinterpret_cast<const unsigned *>(dtheta);
+    const int shift = level == 0 ? 20 : (level == 1 ? 8 : 0);
+    const unsigned mask = level == 2 ? 255u : 4095u;
+    const int sh_hi = level == 1 ? 20 : 8;  // bits above this level's field (levels 1, 2)
+    const unsigned prefix = ss->prefix;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned v = bits[i];
+        if (level > 0 && (v >> sh_hi) != prefix) continue;
+        atomicAdd(&h[(v >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+    k_sel_find(int64_t n, int level, SelState *__restrict__ ss, unsigned *__restrict__ hist,
+               const IterState *st)
+{
+    if (cloud_idle(st)) return;
     __shared__ unsigned warp_sums[33];
     __shared__ int s_bin;
     __shared__ unsigned s_above;
-    __shared__ double sh[kSelThreads];
-    const unsigned *bits = reinterpret_cast<const unsigned *>(dtheta);
-    unsigned k = (unsigned)((n + 99) / 100);
-    unsigned krem = k, above_total = 0;
-    unsigned prefix = 0;
-    // level 1: bits 31..20, level 2: bits 19..8, level 3: bits 7..0
-    const int shifts[3] = {20, 8, 0};
-    const int nbins[3] = {4096, 4096, 256};
-    for (int lv = 0; lv < 3; ++lv) {
-        for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0;
-        __syncthreads();
-        int sh_hi = shifts[lv] + (lv == 2 ? 8 : 12);  // bits above this level's field
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            unsigned v = bits[i];
-            if (lv > 0 && (v >> sh_hi) != prefix) continue;
-            unsigned bin = (v >> shifts[lv]) & (unsigned)(nbins[lv] - 1);
-            atomicAdd(&hist[bin], 1u);
-        }
-        __syncthreads();
-        find_bin(hist, nbins[lv], krem, warp_sums, &s_bin, &s_above);
-        prefix = (prefix << (lv == 2 ? 8 : 12)) | (unsigned)s_bin;
-        above_total += s_above;
-        krem -= s_above;
-        __syncthreads();
+    const int nb = level == 2 ? 256 : 4096;
+    if (level == 0 && threadIdx.x == 0) {
+        ss->krem = (unsigned)((n + 99) / 100);
+        ss->above = 0;
+        ss->prefix = 0;
     }
-    const unsigned tbits = prefix;
-    const float tval = __uint_as_float(tbits);
-    // sum of the values strictly above the threshold, FP64, fixed order
+    __syncthreads();
+    find_bin(hist, nb, ss->krem, warp_sums, &s_bin, &s_above);
+    if (threadIdx.x == 0) {
+        ss->prefix = (ss->prefix << (level == 2 ? 8 : 12)) | (unsigned)s_bin;
+        ss->above += s_above;
+        ss->krem -= s_above;
+    }
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0;  // for the next level
+}
+
+__global__ void __launch_bounds__(kSelGridThreads)
+    k_sel_sum(const float *__restrict__ dtheta, int64_t n, const SelState *__restrict__ ss,
+              double *__restrict__ part, const IterState *st)
+{
+    if (cloud_idle(st)) return;
+    __shared__ double sh[kSelGridThreads];
+    const unsigned *bits = reinterpret_cast<const unsigned *>(dtheta);
+    const unsigned tbits = ss->prefix;
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
         if (bits[i] > tbits) s += (double)dtheta[i];
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -593,7 +645,26 @@ __global__ void __launch_bounds__(kSelThreads)
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    double sum_above = sh[0];
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+    k_sel_final(int64_t n, float tol, int rule, const SelState *__restrict__ ss,
+                const double *__restrict__ part, int npart, IterState *st,
+                const double *__restrict__ dn_blocks, int ndn, double *tr_iso, double *tr_stat,
+                double *tr_dn, long long *tr_faces, cudaGraphConditionalHandle cond, int use_cond)
+{
+    if (cloud_idle(st)) return;  // finished cloud of a batch
+    __shared__ double sh[kSelThreads];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < npart; b += blockDim.x) s += part[b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double sum_above = sh[0];
     __syncthreads();
     double dn = 0.0;
     for (int b = threadIdx.x; b < ndn; b += blockDim.x) dn += dn_blocks[b];
@@ -604,7 +675,9 @@ __global__ void __launch_bounds__(kSelThreads)
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double stat = (sum_above + (double)(k - above_total) * (double)tval) / (double)k;
+        const unsigned k = (unsigned)((n + 99) / 100);
+        const float tval = __uint_as_float(ss->prefix);
+        double stat = (sum_above + (double)(k - ss->above) * (double)tval) / (double)k;
         int it = st->iter;
         st->stat = stat;
         if (tr_iso && it < st->max_iters) {
@@ -684,8 +757,8 @@ cudaError_t launch_iso(Ctx *c)
 cudaError_t launch_mc_faces(Ctx *c)
 {
     k_mc_faces<<<(unsigned)ceil_div(c->nleaves, 256), 256, 0, c->stream>>>(
-        c->d_leaf_corners, c->nleaves, c->d_corner_pos, c->d_wc, c->d_state, c->d_faces,
-        c->max_faces, c->d_err);
+        c->d_leaf_corners, c->d_leaves, c->nleaves, c->d_corner_pos, c->d_wc, c->d_codes, c->n,
+        c->d_state, c->d_faces, c->max_faces, c->d_err);
     return cudaGetLastError();
 }
 
@@ -722,12 +795,26 @@ cudaError_t launch_normal_update(Ctx *c)
     return cudaGetLastError();
 }
 
+int select_blocks(int64_t n)
+{
+    return (int)std::min<int64_t>(std::max<int64_t>(ceil_div(n, 4 * kSelGridThreads), 1), 1024);
+}
+
 cudaError_t launch_select(Ctx *c, cudaGraphConditionalHandle cond, int use_cond)
 {
-    k_select<<<1, kSelThreads, 0, c->stream>>>(c->d_dtheta, c->n, c->tol, c->conv_rule, c->d_state,
-                                               c->d_dn_blocks, (int)ceil_div(c->n, 256),
-                                               c->d_tr_iso, c->d_tr_stat, c->d_tr_dn,
-                                               c->d_tr_faces, cond, use_cond);
+    const int nb = select_blocks(c->n);
+    for (int level = 0; level < 3; ++level) {
+        k_sel_hist<<<nb, kSelGridThreads, 0, c->stream>>>(c->d_dtheta, c->n, level, c->d_sel,
+                                                          c->d_sel_hist, c->d_state);
+        k_sel_find<<<1, kSelThreads, 0, c->stream>>>(c->n, level, c->d_sel, c->d_sel_hist,
+                                                     c->d_state);
+    }
+    k_sel_sum<<<nb, kSelGridThreads, 0, c->stream>>>(c->d_dtheta, c->n, c->d_sel, c->d_sel_part,
+                                                     c->d_state);
+    k_sel_final<<<1, kSelThreads, 0, c->stream>>>(
+        c->n, c->tol, c->conv_rule, c->d_sel, c->d_sel_part, nb, c->d_state, c->d_dn_blocks,
+        (int)ceil_div(c->n, 256), c->d_tr_iso, c->d_tr_stat, c->d_tr_dn, c->d_tr_faces, cond,
+        use_cond);
     return cudaGetLastError();
 }
 

@@ -328,17 +328,29 @@ __global__ void __launch_bounds__(kTcRows)
     uint32_t phase = 0;
     bool ok = true;
     const int64_t ntiles = (B + kTcRows - 1) / kTcRows;
+    // a tile's rows of X, coalesced float4 reads (element e = tid + 128 i is
+    // row e / 16, columns 4 (e % 16) ..); the next tile's are loaded while
+    // the current tile's layers run
+    float4 xr[16];
+    auto load_x = [&](int64_t t) {
+        const int64_t r0 = t * kTcRows;
+        const float4 *X4 = reinterpret_cast<const float4 *>(X + r0 * 64);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = tid + kTcRows * i;
+            xr[i] = r0 + (e >> 4) < B ? X4[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    if ((int64_t)blockIdx.x < ntiles) load_x(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t row0 = tile * kTcRows;
-        // the tile's rows of X (coalesced float4 reads) -> bf16 A
-        const float4 *X4 = reinterpret_cast<const float4 *>(X + row0 * 64);
-        for (int e = tid; e < kTcRows * 16; e += kTcRows) {
-            const int r = e >> 4, c4 = e & 15;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row0 + r < B) v = X4[e];
-            uint2 packed = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
-            *reinterpret_cast<uint2 *>(&S.A[tc_off(r, 4 * c4)]) = packed;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {  // -> bf16 A
+            const int e = tid + kTcRows * i, r = e >> 4, c4 = e & 15;
+            *reinterpret_cast<uint2 *>(&S.A[tc_off(r, 4 * c4)]) =
+                make_uint2(pack_bf16(xr[i].x, xr[i].y), pack_bf16(xr[i].z, xr[i].w));
         }
+        if (tile + gridDim.x < ntiles) load_x(tile + gridDim.x);
         for (int l = 0; l < 4 && ok; ++l) {
             const uint16_t *W = l < 3 ? S.W[l] : S.W4;
             const int N = l < 3 ? 64 : 16;

@@ -57,7 +57,8 @@ class dwg_stats(ctypes.Structure):
                 ("interactions", ctypes.c_double), ("ms_orient", ctypes.c_double),
                 ("interactions_eval", ctypes.c_double),
                 ("interactions_points_step", ctypes.c_double),
-                ("interactions_corners_step", ctypes.c_double)]
+                ("interactions_corners_step", ctypes.c_double),
+                ("kernels_per_iteration", ctypes.c_int)]
 
 
 class dwg_tuning(ctypes.Structure):

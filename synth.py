@@ -372,12 +372,17 @@ def _rotation(seed, stream):
                      [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
 
 
-def union_of_shapes(n, n_tori=20, n_ellipsoids=20, seed=0, noise=0.0025):
+def union_of_shapes(n, n_tori=20, n_ellipsoids=20, seed=0, noise=0.0025, labels=False):
     """Samples of the boundary of a union of randomly posed tori (R ~ U[0.08,
     0.2], r ~ U[0.2 R, 0.4 R]) and ellipsoids (semi-axes ~ U[0.04, 0.15]) with
     centres ~ U[0, 1]^3: area-uniform samples of each primitive, those inside
     another primitive dropped, subsampled to exactly n; Gaussian noise sigma
-    = noise x bounding-box diagonal; analytic outward normals."""
+    = noise x bounding-box diagonal; analytic outward normals.  With labels,
+    also the index of the primitive each sample lies on: the union has
+    several connected components, and each one can settle in either
+    orientation (a component whose normals point inward has w of the wrong
+    sign inside, the level set of the global iso-value does not pass near
+    it, and no face turns it)."""
     prims = []
     for k in range(n_tori + n_ellipsoids):
         c = uniform(seed, 1000 + k, 3)
@@ -402,7 +407,7 @@ def union_of_shapes(n, n_tori=20, n_ellipsoids=20, seed=0, noise=0.0025):
         return ((y / prm) ** 2).sum(1) < 1.0
 
     total_area = sum(p[4] for p in prims)
-    pts, nrms = [], []
+    pts, nrms, labs = [], [], []
     for k, (kind, c, Rm, prm, area) in enumerate(prims):
         m = int(np.ceil(1.25 * n * area / total_area)) + 16
         if kind == "t":
@@ -419,23 +424,27 @@ def union_of_shapes(n, n_tori=20, n_ellipsoids=20, seed=0, noise=0.0025):
                 keep &= ~inside(x, j)
         pts.append(x[keep])
         nrms.append(nn[keep])
+        labs.append(np.full(int(keep.sum()), k, dtype=np.int32))
     P = np.vstack(pts)
+    lab = np.concatenate(labs)
     N = np.vstack(nrms)
     if len(P) < n:
         raise ValueError("not enough samples; raise the oversampling factor")
     sel = np.sort(np.argsort(uniform(seed, 6000, len(P)), kind="stable")[:n])
-    P, N = P[sel], N[sel]
+    P, N, lab = P[sel], N[sel], lab[sel]
     if noise > 0:
         diag = bbox_diag(P)
         P = P + noise * diag * normal(seed, 6001, P.size).reshape(P.shape)
+    if labels:
+        return _as_f32(P), N, lab
     return _as_f32(P), N
 
 
 def workload_union15m():
     """15,000,000 points on a union of 20 tori and 20 ellipsoids, 0.25 % noise;
     Barnes-Hut path; random initial normals versus the learned warm start."""
-    p, nt = union_of_shapes(15_000_000, seed=0)
+    p, nt, lab = union_of_shapes(15_000_000, seed=0, labels=True)
     ext = float((p.max(0) - p.min(0)).max())
-    return dict(name="union-15m", points=p, normals_true=nt,
+    return dict(name="union-15m", points=p, normals_true=nt, labels=lab,
                 weights=np.ones(len(p), np.float32), eps=0.5 * ext / np.sqrt(len(p)),
                 depth=11, max_iters=30, tol=0.1, theta=0.5)

@@ -348,3 +348,21 @@ def test_error_paths(dwglib, handle):
     dwglib.dwg_set_update(h, 3, 10, 0)
     dwglib.dwg_orient(h, out)
     assert np.all(np.isfinite(out))
+
+
+@pytest.mark.parametrize("n", [1, 99, 101, 5000, 300001])
+def test_select_statistic_equals_oracle_on_the_same_changes(dwglib, oracle_mod, handle, n):
+    """The convergence statistic of a step (multi-CTA radix select, FP64 sums
+    in a fixed order) against the oracle's mean of the ceil(n/100) largest of
+    the same float32 changes: equal to rounding of the FP64 sum."""
+    p, _, a, eps = make_cloud(n, seed=n % 97 + 3, kind="box")
+    n0 = synth.random_unit_normals(n, seed=5).astype(np.float32)
+    h = handle(p)
+    dwglib.dwg_set_params(h, 0, max(eps, 1e-3), 0.0, 30, 0.1)
+    dwglib.dwg_set_update(h, 3, 10, dwglib.DWG_UPDATE_DIRECT)
+    dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+    dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, n0)
+    dth = np.zeros(n, np.float32)
+    iso, stat = dwglib.dwg_step(h, None, None, dth)
+    ref = oracle_mod.top1_mean(dth.astype(np.float64))
+    assert stat == pytest.approx(ref, rel=1e-12, abs=1e-12)
