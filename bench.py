@@ -103,15 +103,19 @@ def workload(args):
     return W
 
 
-def profiled_traffic(kernel_file):
-    """dram bytes per launch recorded in a committed ncu summary (or None)."""
+def profiled_traffic(kernel_file, shape):
+    """DRAM bytes per launch recorded in a committed ncu summary of the same
+    kernel shape (or None when the summary is of another shape)."""
+    got, traffic = None, None
     try:
         for line in open(os.path.join(ROOT, "profiles", kernel_file)):
+            if line.startswith("shape:"):
+                got = line.split(":", 1)[1].strip()
             if line.startswith("dram_bytes_per_launch:"):
-                return int(line.split(":")[1])
+                traffic = int(line.split(":")[1])
     except OSError:
-        pass
-    return None
+        return None
+    return traffic if got == shape else None
 
 
 def measured_peaks():
@@ -379,8 +383,10 @@ def run_ours(args, rank, world, local):
             work = float(n) * n
             ops = FP32_OPS[("wg", kind)]
         achieved = work / (kms[dom] / 1e3)
-        traffic = profiled_traffic("eval_corners_torus100k.md") if (
-            dom == "eval_corners" and kind == 0 and W["depth"] == 8 and args.no_tune) else None
+        shape = f"corners_pairs={tuning['corners_pairs']},corners_threads={tuning['corners_threads']}"
+        traffic = profiled_traffic("eval_corners_torus100k.md", shape) if (
+            dom == "eval_corners" and kind == 0 and W["name"] == "torus-100k" and
+            W["depth"] == 8) else None
     else:
         # Barnes-Hut: the dominant of the two tree launches (w and grad at the
         # points, w at the corners), its evaluations performed (counted on the

@@ -727,12 +727,12 @@ __device__ __forceinline__ const float4 *lst_record(int64_t r, int64_t nf, int64
                                                     const int *__restrict__ near_ids,
                                                     const float4 *__restrict__ frec,
                                                     const float4 *__restrict__ src4, int64_t nleaf,
-                                                    int bucket)
+                                                    int lg_bucket)
 {
     if (r < nf) return frec + 3 * (int64_t)far_ids[f0 + r];
-    const int64_t rr = r - nf;
-    const int64_t leaf = near_ids[e0 + rr / bucket];
-    return src4 + 3 * ((leaf - nleaf) * bucket + rr % bucket);
+    const int64_t rr = r - nf;  // leaves hold 2^lg_bucket points
+    const int64_t leaf = near_ids[e0 + (rr >> lg_bucket)];
+    return src4 + 3 * (((leaf - nleaf) << lg_bucket) + (rr & ((1 << lg_bucket) - 1)));
 }
 
 // Work items: a group's stream is cut into items of at most kItemRecords
@@ -789,6 +789,7 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
     const int64_t nleaf = (int64_t)1 << levels;
     const int64_t f0 = far_off[g], nf = far_off[g + 1] - f0;
     const int64_t e0 = near_off[g], ne = near_off[g + 1] - e0;
+    const int lg_bucket = __ffs(bucket) - 1;  // leaf sizes are powers of two
     const int64_t r_begin = item.y;
     const int64_t r_end = min(r_begin + kItemRecords, nf + ne * bucket);
     const int64_t nchunks = (r_end - r_begin + kLstChunk - 1) / kLstChunk;
@@ -800,7 +801,7 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
             const int t = lane + 32 * h;
             if (r0 + t < r_end) {
                 const float4 *from =
-                    lst_record(r0 + t, nf, f0, e0, far_ids, near_ids, frec, src4, nleaf, bucket);
+                    lst_record(r0 + t, nf, f0, e0, far_ids, near_ids, frec, src4, nleaf, lg_bucket);
                 cp_async16(b + 3 * t + 0, from + 0);
                 cp_async16(b + 3 * t + 1, from + 1);
                 cp_async16(b + 3 * t + 2, from + 2);

@@ -104,3 +104,39 @@ def test_learned_init_is_the_normalised_network_output(dwglib, torch):
     y = Y.cpu().numpy()
     ref = y / np.linalg.norm(y, axis=1, keepdims=True)
     np.testing.assert_allclose(n0, ref, atol=1e-6)
+
+
+@pytest.mark.parametrize("shape", ["sphere", "ellipsoid"])
+def test_shipped_warm_start_converges_in_fewer_iterations(dwglib, shape):
+    """What the trained network gains over the method without it: from the
+    shipped weights the orientation reaches the same final agreement with
+    the analytic normals in at most half the iterations of random normals
+    (mean-change rule, same tolerance)."""
+    from paper_2405_13839_gb300 import train_init
+    params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)
+    n = 40000
+    if shape == "sphere":
+        p, nt = synth.sphere(n, seed=21)
+    else:
+        q, nt = synth.ellipsoid_points(n, [1.0, 0.6, 0.35], seed=22, stream=71)
+        p = q.astype(np.float32)
+    res = {}
+    for init in ("random", "learned"):
+        h = dwglib.dwg_create(p)
+        try:
+            dwglib.dwg_set_params(h, 1, 0.5 * 2.0 / np.sqrt(n), 10.0, 100, 0.1)
+            dwglib.dwg_set_update(h, 7, 10, dwglib.DWG_UPDATE_LEVELSET)
+            dwglib.dwg_set_convergence(h, dwglib.DWG_CONV_MEAN)
+            if init == "learned":
+                dwglib.dwg_set_init(h, dwglib.DWG_INIT_LEARNED, 1, params)
+            else:
+                dwglib.dwg_set_init(h, dwglib.DWG_INIT_RANDOM, 1)
+            out = np.zeros((n, 3), np.float32)
+            rc, it = dwglib.dwg_orient(h, out)
+        finally:
+            dwglib.dwg_destroy(h)
+        d = np.sum(out * nt, axis=1)
+        res[init] = (rc, it, float(np.mean(np.sign(d.sum()) * d > 0)))
+    assert res["learned"][0] == dwglib.DWG_OK and res["random"][0] == dwglib.DWG_OK, res
+    assert res["learned"][2] >= 0.999 and res["learned"][2] >= res["random"][2] - 1e-4, res
+    assert 2 * res["learned"][1] <= res["random"][1], res
