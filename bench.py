@@ -509,6 +509,14 @@ def run_batch(args):
     hb = dwg.dwg_create_batch(torch.from_numpy(P).to(dev), off)
     dwg.dwg_set_params(hb, 1, 0.0, 10.0, 80, 0.1)   # eps 0: each cloud's default softening
     dwg.dwg_set_convergence(hb, dwg.DWG_CONV_MEAN)
+    # every cloud tuned on its own: path, leaf size, test form and opening
+    # angle within 2.5 % of its winding-number scale
+    t0 = time.perf_counter()
+    tuned = None
+    if not args.no_tune:
+        tuned = dwg.dwg_autotune(hb, dwg.DWG_TUNE_SHAPES | dwg.DWG_TUNE_TREE | dwg.DWG_TUNE_RELATIVE,
+                                 0.025, None)
+    tune_s = time.perf_counter() - t0
     out = torch.empty_like(torch.from_numpy(P), device=dev)
     for _ in range(args.warmup):
         dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
@@ -545,7 +553,11 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch-64", "clouds": nc, "points": int(off[-1]),
                        "kernel": "screened lambda=10", "eps": "per cloud 0.5 L / sqrt(n)",
-                       "rule": "mean change <= chord of 0.1 deg", "max_iters": 80},
+                       "rule": "mean change <= chord of 0.1 deg", "max_iters": 80,
+                       "tuning": ("per cloud, relative w budget 2.5 % (largest cloud: " +
+                                  json.dumps({k: tuned[k] for k in TUNING_KEYS}) + ")")
+                                 if tuned else "defaults",
+                       "tuning_s": round(tune_s, 1)},
             "s_to_converged_normals": dev_s / args.steps,
             "iterations": {"min": int(min(iters)), "max": int(max(iters)),
                            "mean": float(np.mean(iters))},

@@ -350,14 +350,24 @@ int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
  *   a text file with one JSON object per line, keyed by the GPU's name and SM
  *   count and the problem (sizes, kernel, screening, update rule, requested
  *   path, budget, what); a matching line is applied without measuring, a new
- *   result is appended.  Not valid on batch handles (DWG_ERR_STATE).
+ *   result is appended.  With DWG_TUNE_RELATIVE in what, w_budget is relative
+ *   to the cloud's winding-number scale inside a closed surface, estimated
+ *   from the geometry alone as mean(a) / (pi r^2 / 10), r the median distance
+ *   to the 10th nearest other point over a sample of up to 2,048 points.
+ *   On a batch handle every cloud is tuned on its own (the same what and
+ *   budget; DWG_TUNE_RELATIVE is then the natural choice) and *out receives
+ *   the settings of the largest cloud; the batch's one all-pairs launch keeps
+ *   its fixed shapes, the per-cloud paths, leaf sizes, test forms and opening
+ *   angles are the tuned ones.
  * dwg_get_tuning / dwg_set_tuning: read or apply settings (dwg_set_tuning
  *   fails with DWG_ERR_INVALID for a shape that is not compiled, a leaf size
- *   outside the list or theta outside (0, 1]).  Settings change the order of
- *   floating-point additions, not the definition of the sums.
+ *   outside the list or theta outside (0, 1]; on a batch handle it applies to
+ *   every cloud, and dwg_get_tuning reads the largest cloud's).  Settings change the order of floating-point additions, not
+ *   the definition of the sums.
  */
 #define DWG_TUNE_SHAPES 1
 #define DWG_TUNE_TREE 2
+#define DWG_TUNE_RELATIVE 4
 
 typedef struct {
     int path;

@@ -996,18 +996,39 @@ int dwg_autotune(dwg_handle h, int what, double w_budget, const char *cache_path
                  dwg_tuning *out)
 {
     if (!h) return DWG_ERR_INVALID;
-    if (h->is_batch) return fail(h, DWG_ERR_STATE, "autotune a single-cloud handle");
-    if (what & ~(DWG_TUNE_SHAPES | DWG_TUNE_TREE) || !what)
-        return fail(h, DWG_ERR_INVALID, "what: DWG_TUNE_SHAPES and/or DWG_TUNE_TREE");
+    if (what & ~(DWG_TUNE_SHAPES | DWG_TUNE_TREE | DWG_TUNE_RELATIVE) ||
+        !(what & (DWG_TUNE_SHAPES | DWG_TUNE_TREE)))
+        return fail(h, DWG_ERR_INVALID,
+                    "what: DWG_TUNE_SHAPES and/or DWG_TUNE_TREE, optionally DWG_TUNE_RELATIVE");
     cudaSetDevice(h->device);
-    int rc = autotune(h, what, w_budget, cache_path, out);
     invalidate_graph(h);
-    return rc;
+    if (h->is_batch) {
+        int64_t largest = -1;
+        for (dwg_ctx *c : h->clouds) {
+            c->stream = h->stream;
+            dwg_tuning t;
+            int rc = autotune(c, what, w_budget, cache_path, &t);
+            if (rc) return fail(h, rc, "cloud: " + c->err);
+            if (c->n > largest) {
+                largest = c->n;
+                if (out) *out = t;
+            }
+        }
+        return DWG_OK;
+    }
+    return autotune(h, what, w_budget, cache_path, out);
 }
 
 int dwg_get_tuning(dwg_handle h, dwg_tuning *out)
 {
     if (!h || !out) return DWG_ERR_INVALID;
+    if (h->is_batch) {  // the largest cloud's settings
+        const dwg_ctx *big = h->clouds.empty() ? h : h->clouds[0];
+        for (const dwg_ctx *c : h->clouds)
+            if (c->n > big->n) big = c;
+        tuning_of(big, out);
+        return DWG_OK;
+    }
     tuning_of(h, out);
     return DWG_OK;
 }
@@ -1015,10 +1036,15 @@ int dwg_get_tuning(dwg_handle h, dwg_tuning *out)
 int dwg_set_tuning(dwg_handle h, const dwg_tuning *t)
 {
     if (!h || !t) return DWG_ERR_INVALID;
-    if (h->is_batch) return fail(h, DWG_ERR_STATE, "set the tuning of a single-cloud handle");
-    int rc = apply_tuning(h, t);
     invalidate_graph(h);
-    return rc;
+    if (h->is_batch) {
+        for (dwg_ctx *c : h->clouds) {
+            int rc = apply_tuning(c, t);
+            if (rc) return fail(h, rc, c->err);
+        }
+        return DWG_OK;
+    }
+    return apply_tuning(h, t);
 }
 
 int dwg_get_stats(dwg_handle h, dwg_stats *out)

@@ -344,6 +344,8 @@ int select_blocks(int64_t n);
 cudaError_t launch_random_normals(float4 *nrm, const int64_t *perm, int64_t n, uint64_t seed,
                                   cudaStream_t s);
 cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t *idx_out);
+// distance to the 10th nearest other point for m points sampled evenly
+cudaError_t launch_spacing(Ctx *c, int64_t m, float *d_out);
 cudaError_t launch_features(Ctx *c, float *X, bool by_input, double *cR);
 cudaError_t launch_normals_from_y(Ctx *c, const float *Y);
 

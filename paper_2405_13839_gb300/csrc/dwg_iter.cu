@@ -348,6 +348,27 @@ __global__ void k_knn_query(const float4 *__restrict__ q, int64_t m, KnnTree T, 
     for (int t = 0; t < k; ++t) idx_out[i * k + t] = bj[t] >= 0 ? T.perm[bj[t]] : -1;
 }
 
+// distance from each of m sampled points (sorted indices, strided) to its
+// 11th nearest point (itself included: the 10th nearest other point)
+__global__ void k_spacing(KnnTree T, int64_t m, int64_t stride, float *d_out, int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float4 v = T.p4[min(i * stride, T.n - 1)];
+    const F3 q = {v.x, v.y, v.z};
+    int bj[11];
+    knn_search<11, true>(T, q, 11, bj, err);
+    d_out[i] = bj[10] >= 0 ? sqrtf(pt_d2(T.p4[bj[10]], q)) : 0.f;
+}
+
+cudaError_t launch_spacing(Ctx *c, int64_t m, float *d_out)
+{
+    const int64_t stride = std::max<int64_t>(1, c->n / std::max<int64_t>(m, 1));
+    k_spacing<<<(unsigned)ceil_div(m, 128), 128, 0, c->stream>>>(knn_tree(c), m, stride, d_out,
+                                                                 c->d_err);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // learned warm start: patch features from the 16 nearest other points
 // ---------------------------------------------------------------------------

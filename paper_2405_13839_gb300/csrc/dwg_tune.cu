@@ -319,6 +319,32 @@ int apply_tuning(Ctx *c, const dwg_tuning *t)
     return DWG_OK;
 }
 
+// The winding number's scale inside a closed surface, 1 / (mean area per
+// point) x mean a: the area per point estimated from the spacing, pi r^2 / 10
+// with r the median distance to the 10th nearest other point (a disc of
+// radius r around a point of a surface sampling holds about 10 others).
+int w_scale(Ctx *c, double *scale)
+{
+    const int64_t m = std::min<int64_t>(2048, c->n);
+    Buf d, a;
+    TUNE_TRY(cudaMalloc(&d.p, m * sizeof(float)));
+    TUNE_TRY(launch_spacing(c, m, d.as<float>()));
+    std::vector<float> h(m);
+    std::vector<float4> p4(c->n < 65536 ? c->n : 65536);
+    TUNE_TRY(cudaMemcpyAsync(h.data(), d.p, m * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    TUNE_TRY(cudaMemcpyAsync(p4.data(), c->d_p4, p4.size() * sizeof(float4), cudaMemcpyDeviceToHost,
+                             c->stream));
+    TUNE_TRY(cudaStreamSynchronize(c->stream));
+    std::sort(h.begin(), h.end());
+    const double r = h[m / 2];
+    double abar = 0.0;
+    for (const float4 &v : p4) abar += (double)v.w;
+    abar /= (double)p4.size();
+    const double area_per_point = kPi * r * r / 10.0;
+    *scale = area_per_point > 0.0 ? abar / area_per_point : 1.0;
+    return DWG_OK;
+}
+
 int autotune(Ctx *c, int what, double budget, const char *cache_path, dwg_tuning *out)
 {
     if (!(budget > 0.0) && (what & DWG_TUNE_TREE)) {
@@ -328,6 +354,11 @@ int autotune(Ctx *c, int what, double budget, const char *cache_path, dwg_tuning
     const int path_req = c->path;
     int rc = engine_prepare(c);
     if (rc) return rc;
+    if (what & DWG_TUNE_RELATIVE) {
+        double scale = 1.0;
+        if ((rc = w_scale(c, &scale))) return rc;
+        budget *= scale;
+    }
     const std::string key = key_of(c, path_req, budget) + ", \"what\": " + std::to_string(what);
     dwg_tuning t;
     if (cache_lookup(cache_path, key, &t)) {

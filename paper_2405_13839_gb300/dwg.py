@@ -73,6 +73,7 @@ class dwg_tuning(ctypes.Structure):
 
 DWG_TUNE_SHAPES = 1
 DWG_TUNE_TREE = 2
+DWG_TUNE_RELATIVE = 4
 
 
 def lib_path() -> str:

@@ -81,3 +81,29 @@ def test_batch_handle_rejects_single_calls(dwglib):
         dwglib.dwg_destroy(hb)
     with pytest.raises(dwglib.DWGError):
         dwglib.dwg_create_batch(P, np.array([0, 10, 10, len(P)], np.int64))
+
+
+def test_batch_autotune_per_cloud_then_orient(dwglib):
+    """The tuner on a batch handle tunes every cloud (relative budget) and
+    the batch still orients every cloud."""
+    P, off = _clouds()
+    nts = []
+    for kind, n, s in [("sphere", 1500, 0), ("torus", 4000, 1), ("sphere", 700, 2),
+                       ("torus", 9000, 3), ("sphere", 33, 4)]:
+        nts.append(synth.sphere(n, seed=s)[1] if kind == "sphere" else synth.torus(n, seed=s)[1])
+    hb = dwglib.dwg_create_batch(P, off)
+    try:
+        dwglib.dwg_set_params(hb, 1, 0.0, 10.0, 40, 0.1)
+        dwglib.dwg_set_tree(hb, dwglib.DWG_PATH_TREE, 0.5)
+        t = dwglib.dwg_autotune(hb, dwglib.DWG_TUNE_TREE | dwglib.DWG_TUNE_RELATIVE, 0.025, None)
+        assert t["path"] == dwglib.DWG_PATH_TREE and t["tree_leaf"] in (16, 32, 64, 128)
+        assert dwglib.dwg_get_tuning(hb)["theta"] == t["theta"]
+        out = np.zeros_like(P)
+        dwglib.dwg_orient_batch(hb, out, len(off) - 1)
+    finally:
+        dwglib.dwg_destroy(hb)
+    for c in range(4):
+        o = out[off[c]:off[c + 1]]
+        d = np.sum(o * nts[c], axis=1)
+        s = 1.0 if d.sum() >= 0 else -1.0
+        assert np.mean(s * d > 0) >= 0.99, (c, np.mean(s * d > 0))

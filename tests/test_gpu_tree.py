@@ -202,3 +202,56 @@ def test_group_lists_step_matches_oracle_group_tree(dwglib, oracle_mod, handle, 
         check_wg(w[sel], g[sel], wo[sel], go[sel], s_g(p, nrm, a, p[sel], eps))
         nrm = np.zeros((n, 3), np.float32)
         dwglib.dwg_get_normals(h, nrm)
+
+
+def _term_sums(points, normals, weights, queries, eps, chunk=16):
+    """Per query: sum_j |m_j| rho_j^-2 (bounds sum |w terms|) and
+    4 sum_j |m_j| rho_j^-3 (bounds sum |grad terms|), m = a n / 4 pi."""
+    p = np.asarray(points, np.float64)
+    mn = np.abs(np.asarray(weights, np.float64)) * np.linalg.norm(
+        np.asarray(normals, np.float64), axis=1) / (4 * np.pi)
+    sw = np.zeros(len(queries))
+    sg = np.zeros(len(queries))
+    for i0 in range(0, len(queries), chunk):
+        q = np.asarray(queries[i0:i0 + chunk], np.float64)
+        d2 = ((p[None, :, :] - q[:, None, :]) ** 2).sum(-1) + eps * eps
+        sw[i0:i0 + chunk] = (mn[None, :] / d2).sum(1)
+        sg[i0:i0 + chunk] = 4 * (mn[None, :] * d2 ** -1.5).sum(1)
+    return sw, sg
+
+
+def test_full_size_metaballs_step_matches_oracle_on_sampled_groups(dwglib, oracle_mod):
+    """The 1,000,000-point metaballs workload in the launch configuration the
+    benchmark times (screened lambda 100, depth 9, leaf 32, opening angle
+    0.4, group test, lists): w and grad w of one step at 8 sampled groups of
+    64 Morton-consecutive points against the oracle's group tree on the same
+    groups.  a_i = 1 makes the terms large (w inside ~ n / area), so the
+    tolerance is the FP32 forward-error bound of the sums: flushes of at most
+    128 plain FP32 additions folded into two-sums, 160 u sum |t|."""
+    W = synth.workload_metaballs1m()
+    p, a, eps = W["points"], W["weights"], W["eps"]
+    n = len(p)
+    nrm = synth.random_unit_normals(n, seed=1).astype(np.float32)
+    h = dwglib.dwg_create(p)
+    try:
+        dwglib.dwg_set_weights(h, a)
+        dwglib.dwg_set_params(h, 1, eps, 100.0, 30, 0.1)
+        dwglib.dwg_set_update(h, 9, 10, dwglib.DWG_UPDATE_LEVELSET)
+        dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.4)
+        dwglib.dwg_set_tuning(h, tree_group=1, tree_leaf=32)
+        dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, nrm)
+        w = np.zeros(n, np.float32)
+        g = np.zeros((n, 3), np.float32)
+        dwglib.dwg_step(h, w, g)
+    finally:
+        dwglib.dwg_destroy(h)
+    order = oracle_mod.morton_order(p)
+    groups = np.unique((synth.uniform(4, 9, 8) * (n // 64)).astype(np.int64))
+    idx = np.concatenate([order[64 * gi:64 * gi + 64] for gi in groups])
+    beta = float(np.float32(1) / np.float32(0.4))
+    wo, go = oracle_mod.tree_gwn_group(p, nrm, a, p[idx], kernel=1, eps=eps, lam=100.0,
+                                       beta=beta, bucket=32, group=64)
+    sw, sg = _term_sums(p, nrm, a, p[idx], eps)
+    u = 2.0 ** -24
+    assert np.all(np.abs(w[idx] - wo) <= 160 * u * sw)
+    assert np.all(np.abs(g[idx] - go).max(axis=1) <= 160 * u * sg)

@@ -222,3 +222,23 @@ def test_autotune_tree_rejects_an_unreachable_budget(dwglib, handle):
         dwglib.dwg_autotune(h, dwglib.DWG_TUNE_TREE, 1e-9, None)
     assert e.value.code == dwglib.DWG_ERR_INVALID
     assert dwglib.dwg_get_tuning(h) == before
+
+
+def test_autotune_relative_budget_scales_with_the_weights(dwglib, handle):
+    """DWG_TUNE_RELATIVE: the budget follows the winding number's scale
+    estimated from the spacing, so with a_i = 1 (w inside about n / area)
+    and a_i = area / n (w inside about 1) the tuner picks the same settings."""
+    n = 30000
+    p, nt = synth.sphere(n, seed=11)
+    res = []
+    for a in (np.ones(n, np.float32), np.full(n, 4 * np.pi / n, np.float32)):
+        h = handle(p)
+        dwglib.dwg_set_weights(h, a)
+        dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+        dwglib.dwg_set_normals(h, nt.astype(np.float32))
+        t = dwglib.dwg_autotune(h, dwglib.DWG_TUNE_TREE | dwglib.DWG_TUNE_RELATIVE, 0.02, None)
+        res.append(t)
+        scale = float(a[0]) * n / (4 * np.pi)  # w inside for this weighting
+        assert t["w_err"] <= 0.05 * scale, (t, scale)
+    assert (res[0]["tree_leaf"], res[0]["theta"], res[0]["tree_group"]) == \
+        (res[1]["tree_leaf"], res[1]["theta"], res[1]["tree_group"])
