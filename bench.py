@@ -350,7 +350,7 @@ def run_ours(args, rank, world, local):
     agree = agreement(out.cpu().numpy(), W["normals_true"], W.get("labels"))
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([dev_s, inter], dtype=torch.float64)
+        t = torch.tensor([dev_s, inter], dtype=torch.float64, device=dev)  # NCCL: device tensors
         tt = t.clone()
         dist.all_reduce(tt, op=dist.ReduceOp.SUM)
         tmax = t.clone()
@@ -498,14 +498,22 @@ def one_step(args):
     print(json.dumps({"one_step": W["name"], "iso": iso, "stat": stat, "tuning": t}))
 
 
-def run_batch(args):
-    """64 clouds in one handle: one CUDA graph launch orients all of them."""
+def run_batch(args, rank=0, world=1, local=0):
+    """64 clouds in one handle: one CUDA graph launch orients all of them.
+    With several ranks the clouds are independent problems: each rank
+    orients its share (balanced by estimated work) in its own batch handle,
+    with no exchange on the data path; the job time is the slowest rank's."""
     import torch
-    from paper_2405_13839_gb300 import dwg
+    from paper_2405_13839_gb300 import dwg, shard
     W = synth.workload_batch64()
-    P, off = W["points"], W["offsets"]
+    P_all, off_all = W["points"], W["offsets"]
+    mine = shard.assign(W["sizes"], world)[rank]
+    P, off = shard.sub_batch(P_all, off_all, mine)
+    nt_all = W["normals_true"]
+    nt = np.vstack([nt_all[off_all[c]:off_all[c + 1]] for c in mine])
     nc = len(off) - 1
-    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     hb = dwg.dwg_create_batch(torch.from_numpy(P).to(dev), off)
     dwg.dwg_set_params(hb, 1, 0.0, 10.0, 80, 0.1)   # eps 0: each cloud's default softening
     dwg.dwg_set_convergence(hb, dwg.DWG_CONV_MEAN)
@@ -521,8 +529,11 @@ def run_batch(args):
     for _ in range(args.warmup):
         dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
         dwg.dwg_orient_batch(hb, out, nc)
-    clocks = Clocks(0)
+    clocks = Clocks(local)
     ms, inter, iters = [], 0.0, None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     for _ in range(args.steps):
         dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
         torch.cuda.synchronize()
@@ -532,7 +543,7 @@ def run_batch(args):
         inter += st["interactions"]
     ck = clocks.stop()
     o = out.cpu().numpy()
-    ags = [agreement(o[off[c]:off[c + 1]], W["normals_true"][off[c]:off[c + 1]]) for c in range(nc)]
+    ags = [agreement(o[off[c]:off[c + 1]], nt[off[c]:off[c + 1]]) for c in range(nc)]
     # the learned warm start on every cloud (one run)
     from paper_2405_13839_gb300 import train_init
     params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)
@@ -543,15 +554,35 @@ def run_batch(args):
     torch.cuda.synchronize()
     s_l = time.perf_counter() - t0
     o = out.cpu().numpy()
-    ags_l = [agreement(o[off[c]:off[c + 1]], W["normals_true"][off[c]:off[c + 1]])
-             for c in range(nc)]
+    ags_l = [agreement(o[off[c]:off[c + 1]], nt[off[c]:off[c + 1]]) for c in range(nc)]
     dwg.dwg_destroy(hb)
     dev_s = sum(ms) / 1e3
+    its = list(iters)
+    its_l = list(iters_l)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_s, inter, s_l], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        dev_s, inter, s_l = float(tmax[0]), float(tsum[1]), float(tmax[2])
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (ags, ags_l, its, its_l))
+        ags = [a for g in gathered for a in g[0]]
+        ags_l = [a for g in gathered for a in g[1]]
+        its = [i for g in gathered for i in g[2]]
+        its_l = [i for g in gathered for i in g[3]]
+        if rank != 0:
+            return
+    iters, iters_l = its, its_l
+    nc = len(ags)
     line = {"metric": "GWN+grad interactions/s", "value": inter / dev_s, "unit": "interactions/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch-64", "clouds": nc, "points": int(off[-1]),
+            "config": {"workload": "batch-64", "clouds": nc, "points": int(off_all[-1]),
+                       "parallelism": f"clouds sharded over {world} rank(s), no data-path exchange",
                        "kernel": "screened lambda=10", "eps": "per cloud 0.5 L / sqrt(n)",
                        "rule": "mean change <= chord of 0.1 deg", "max_iters": 80,
                        "tuning": ("per cloud, relative w budget 2.5 % (largest cloud: " +
@@ -572,6 +603,18 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def common_config(W, world):
+    """The workload's configuration, shared by both arms' JSON lines."""
+    return {"workload": W["name"], "points": len(W["points"]),
+            "kernel": "plain" if W["kernel"] == 0 else f"screened lambda={W['lam']:g}",
+            "depth": W["depth"], "knn": 10, "tol_deg": W["tol"],
+            "rule": "top-1% mean change (Sec. 5.1)" if W["rule"] == 0 else
+                    "mean change (Fig. 6 measure)",
+            "max_iters": W["max_iters"], "init": "random seed 1",
+            "parallelism": f"replicas x{world}",
+            "l2": "flushed (256 MiB write) before every step"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -582,6 +625,8 @@ def main():
         import torch
         import torch.distributed as dist
         backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     if args.impl == "reference":
         if rank != 0:
@@ -603,8 +648,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": W["name"], "points": n, "kernel": "plain" if W["kernel"] == 0 else "screened",
-                           "path": "all-pairs", "depth": W["depth"]},
+                "config": common_config(W, args.gpus) | {"path": "FP64 all-pairs (oracle)"},
                 "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "interactions/s"},
                 "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -612,8 +656,7 @@ def main():
         return
 
     if args.workload == "batch-64":
-        if rank == 0:
-            run_batch(args)
+        run_batch(args, rank, world, local)
         return
     r = run_ours(args, rank, world, local)
     if rank != 0:
@@ -636,15 +679,8 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": W["name"], "points": n, "corners": r["nc"],
-                   "kernel": "plain" if W["kernel"] == 0 else f"screened lambda={W['lam']:g}",
-                   "path": path, "depth": W["depth"], "knn": 10, "tol_deg": W["tol"],
-                   "rule": "top-1% mean change (Sec. 5.1)" if W["rule"] == 0 else
-                           "mean change (Fig. 6 measure)",
-                   "max_iters": W["max_iters"], "init": "random seed 1",
-                   "parallelism": f"replicas x{world}",
-                   "l2": "flushed (256 MiB write) before every step",
-                   "tuning": {k: t[k] for k in TUNING_KEYS}},
+        "config": common_config(W, world) | {
+            "corners": r["nc"], "path": path, "tuning": {k: t[k] for k in TUNING_KEYS}},
         "s_to_converged_normals": ms_per_step / 1e3,
         "iterations": r["iters"][0],
         "converged": r["rcs"][0] == 0,
