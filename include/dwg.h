@@ -158,7 +158,10 @@ int dwg_set_weights(dwg_handle h, const float *a);
  * uniforms 2i and 2i+1 (top 53 bits * 2^-53), z = 1 - 2 u0,
  * phi = 2 pi u1, n = (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z);
  * normals is ignored.  DWG_INIT_GIVEN copies normals (float32 n x 3, input
- * order, host or device; each is normalised, zero vectors rejected).
+ * order, host or device; each is normalised -- a vector of unit length to
+ * within 4e-7 is taken as is, so normals from dwg_get_normals or dwg_orient
+ * resume an orientation exactly (checkpoint / resume) -- zero vectors
+ * rejected).
  * DWG_INIT_LEARNED (a project extension, not in the paper): `normals` points
  * to the 12,675 float32 parameters of the kNN-patch network (layout in
  * dwg_mlp_forward); the initial normal of each point is the normalised

@@ -97,6 +97,9 @@ __global__ void k_normals_in(const float *__restrict__ v, const int64_t *__restr
         atomicOr(err, kErrNonfinite);
         l = 1.f;
     }
+    // a vector of unit length to float rounding is taken as is, so that
+    // normals read back from the library resume an orientation bit for bit
+    if (fabsf(l - 1.f) <= 4e-7f) l = 1.f;
     out[i] = make_float4(x / l, y / l, z / l, 0.f);
 }
 // sorted float4 -> caller layout (input order)

@@ -366,3 +366,33 @@ def test_select_statistic_equals_oracle_on_the_same_changes(dwglib, oracle_mod, 
     iso, stat = dwglib.dwg_step(h, None, None, dth)
     ref = oracle_mod.top1_mean(dth.astype(np.float64))
     assert stat == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_checkpoint_resume_is_bit_exact(dwglib, handle):
+    """The iteration's state is the normals: stopping after 8 iterations,
+    reading the normals and orienting 8 more from them gives the normals of
+    16 iterations in one run, bit for bit (deterministic sums and
+    order-independent fixed-point scatter)."""
+    n = 3000
+    p, _ = synth.torus(n, seed=8, noise=0.003)
+    area = 4 * np.pi ** 2 * 0.3
+    eps = synth.default_eps(area, n)
+    n0 = synth.random_unit_normals(n, seed=9).astype(np.float32)
+    outs, totals = [], []
+    for caps in ((16,), (8, 8)):
+        h = handle(p)
+        dwglib.dwg_set_weights(h, np.full(n, area / n, np.float32))
+        dwglib.dwg_set_update(h, 6, 10, dwglib.DWG_UPDATE_LEVELSET)
+        start, total = n0, 0
+        for cap in caps:
+            dwglib.dwg_set_params(h, 1, eps, 10.0, cap, 1e-6)  # tol met only at an exact fixed point
+            dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, start)
+            out = np.zeros((n, 3), np.float32)
+            rc, it = dwglib.dwg_orient(h, out)
+            assert 1 <= it <= cap
+            total += it
+            start = out
+        outs.append(out)
+        totals.append(total)
+    assert totals[0] >= 9 and totals[1] == totals[0]  # the split run resumed mid-way
+    assert np.array_equal(outs[0], outs[1])
