@@ -13,10 +13,12 @@ the 10 nearest points, updates the normals and tests convergence, all inside
 one CUDA graph launch.
 
 Metric: GWN+grad interactions per second (performed kernel evaluations),
-whole job over all ranks; also seconds to converged normals, from random
-initial normals and from the learned warm start.  Multi-GPU runs are
-independent replicas (weak scaling): the method's per-cloud loop has an
-exchange step only when one cloud is split, which this benchmark does not do.
+whole job over all ranks; also seconds to converged normals from random
+initial normals, the learned warm start and the paper's PCA and Gauss-map
+initialisations.  Multi-GPU: batch-64 shards its independent clouds over the
+ranks; the single-cloud workloads run independent replicas (weak scaling):
+the method's per-cloud loop has an exchange step only when one cloud is
+split, which this benchmark does not do.
 
 Other workloads (--workload): metaballs-1m (Barnes-Hut path), union-15m
 (Barnes-Hut path, random versus learned initial normals), batch-64 (64 clouds
@@ -65,12 +67,12 @@ def parse():
                     help="apply these settings instead of tuning, e.g. "
                          "'corners_pairs=2,corners_threads=128' (profiler captures)")
     ap.add_argument("--no-warm", action="store_true",
-                    help="skip the random-versus-learned initial normals comparison")
+                    help="skip the comparison of initial normals (random, learned, PCA, Gauss map)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--one-step", action="store_true",
                     help="run one iteration of the workload and exit (for profiler captures)")
-    ap.add_argument("--init", default="random", choices=["random", "learned"],
+    ap.add_argument("--init", default="random", choices=["random", "learned", "pca", "gauss"],
                     help="initial normals of --one-step (learned: the warm-start network runs)")
     return ap.parse_args()
 
@@ -232,13 +234,15 @@ def tune(dwg, h, W, args):
 
 
 def warm_start_compare(dwg, torch, dev, W, tuning, weights, max_iters):
-    """Seconds to converged normals from random initial normals and from the
-    learned warm start (both to the same rule and tolerance)."""
+    """Seconds to converged normals from each initialisation: random, the
+    learned warm start, and the paper's PCA and Gauss-map options (Sec. 5.1),
+    all to the same rule and tolerance."""
     from paper_2405_13839_gb300 import train_init
     params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)
     out = {}
     n = len(W["points"])
-    for init in ("random", "learned"):
+    modes = {"random": dwg.DWG_INIT_RANDOM, "pca": dwg.DWG_INIT_PCA, "gauss": dwg.DWG_INIT_GAUSS}
+    for init in ("random", "learned", "pca", "gauss"):
         h = dwg.dwg_create(torch.from_numpy(W["points"]).to(dev))
         try:
             configure(dwg, h, W, weights)
@@ -252,7 +256,7 @@ def warm_start_compare(dwg, torch, dev, W, tuning, weights, max_iters):
                 if init == "learned":
                     dwg.dwg_set_init(h, dwg.DWG_INIT_LEARNED, 1, params)
                 else:
-                    dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
+                    dwg.dwg_set_init(h, modes[init], 1)
                 rc, it = dwg.dwg_orient(h, res)
                 torch.cuda.synchronize()
                 sec = time.perf_counter() - t0
@@ -263,8 +267,10 @@ def warm_start_compare(dwg, torch, dev, W, tuning, weights, max_iters):
                          "top1_stat_deg_last": st["stat_last"]}
         finally:
             dwg.dwg_destroy(h)
-    out["rule"] = "mean |n_new - n_old| <= chord of 0.1 deg (Fig. 6 measure), both inits"
+    out["rule"] = "mean |n_new - n_old| <= chord of 0.1 deg (Fig. 6 measure), every init"
     out["speedup"] = out["random"]["s"] / out["learned"]["s"]
+    out["speedup_pca"] = out["random"]["s"] / out["pca"]["s"]
+    out["speedup_gauss"] = out["random"]["s"] / out["gauss"]["s"]
     # at equal accuracy: the fewest iterations from random normals that reach
     # the learned start's final agreement (bisection over the iteration cap)
     target = min(out["learned"]["agreement"], out["random"]["agreement"])
@@ -291,6 +297,57 @@ def warm_start_compare(dwg, torch, dev, W, tuning, weights, max_iters):
         "agreement": target, "random_iterations": hi, "random_s": per_it * hi,
         "learned_iterations": out["learned"]["iterations"], "learned_s": out["learned"]["s"],
         "speedup": per_it * hi / out["learned"]["s"]}
+    return out
+
+
+def setup_and_variants(dwg, torch, dev, W, reps=3):
+    """Device time of the one-time per-cloud steps the paper adds around the
+    iteration (Sec. 5.1 area weights and initialisations, Sec. 5.2 clamp
+    radii) on this workload, and the w + grad w throughput at the points of
+    the modified kernel (Sec. 5.2) beside the softened one, both all-pairs."""
+    n = len(W["points"])
+    pts = torch.from_numpy(W["points"]).to(dev)
+    out = {}
+    h = dwg.dwg_create(pts)
+    try:
+        nrm = torch.empty((n, 3), dtype=torch.float32, device=dev)
+
+        def timed(fn):
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                ts.append(1e3 * (time.perf_counter() - t0))
+            return round(statistics.median(ts), 3)
+
+        out["voronoi_weights_ms"] = timed(lambda: dwg.dwg_voronoi_weights(h, 15))
+        for name, mode in (("random", dwg.DWG_INIT_RANDOM), ("pca", dwg.DWG_INIT_PCA),
+                           ("gauss", dwg.DWG_INIT_GAUSS)):
+            def init(mode=mode):
+                dwg.dwg_set_init(h, mode, 1)
+                dwg.dwg_get_normals(h, nrm)
+            out[f"init_{name}_ms"] = timed(init)
+        out["clamp_radii_ms"] = timed(lambda: dwg.dwg_set_regularization(
+            h, dwg.DWG_REG_CLAMP, 10, 0.0, 0.0))
+        if n <= 200_000:
+            dwg.dwg_set_weights(h, torch.from_numpy(W["weights"]).to(dev))
+            dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lam"], 30, 0.1)
+            dwg.dwg_set_tree(h, dwg.DWG_PATH_ALLPAIRS, 0.5)
+            w = torch.empty(n, dtype=torch.float32, device=dev)
+            g = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            for reg in (dwg.DWG_REG_SOFTEN, dwg.DWG_REG_CLAMP):
+                dwg.dwg_set_regularization(h, reg, 10, 0.0, 0.0)
+                dwg.dwg_eval_gwn(h, pts, w, g)  # warm-up
+                ms = timed(lambda: dwg.dwg_eval_gwn(h, pts, w, g))
+                key = "softened" if reg == dwg.DWG_REG_SOFTEN else "modified_kernel"
+                out[f"eval_points_{key}"] = {"ms": ms, "interactions_per_s": n * n / (ms / 1e3)}
+            out["eval_points_basis"] = ("dwg_eval_gwn at the n points, w and grad w, all-pairs, "
+                                        "call wall time incl. the reduce (median of 3)")
+    finally:
+        dwg.dwg_destroy(h)
+    out["basis"] = "median of 3 calls, host wall time around synchronous C-ABI calls"
     return out
 
 
@@ -433,11 +490,14 @@ def run_ours(args, rank, world, local):
     warm = None
     if not args.no_warm and world == 1:
         warm = warm_start_compare(dwg, torch, dev, W, tuning, a_dev, max(100, W["max_iters"]))
+    extras = None
+    if not args.no_warm and world == 1:
+        extras = setup_and_variants(dwg, torch, dev, W)
     # reset, random init, pack, then the graph's kernels once per iteration
     launches_per_step = 3 + st_orient["kernels_per_iteration"] * statistics.mean(it_list)
     return dict(value=value, dev_s=dev_s, ms=ms, iters=it_list, rcs=rc_list, st=st_orient,
                 roof=roof, clocks=ck, e2e=e2e, wall=wall, agree=agree, tuning=tuning, warm=warm,
-                launches=int(round(launches_per_step * args.steps)), W=W, nc=nc)
+                extras=extras, launches=int(round(launches_per_step * args.steps)), W=W, nc=nc)
 
 
 def cpu_baseline(W, nc_hint, budget_s=12.0):
@@ -490,7 +550,8 @@ def one_step(args):
         params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)
         dwg.dwg_set_init(h, dwg.DWG_INIT_LEARNED, 1, params)
     else:
-        dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
+        dwg.dwg_set_init(h, {"random": dwg.DWG_INIT_RANDOM, "pca": dwg.DWG_INIT_PCA,
+                             "gauss": dwg.DWG_INIT_GAUSS}[args.init], 1)
     iso, stat = dwg.dwg_step(h)
     torch.cuda.synchronize()
     t = dwg.dwg_get_tuning(h)
@@ -544,39 +605,49 @@ def run_batch(args, rank=0, world=1, local=0):
     ck = clocks.stop()
     o = out.cpu().numpy()
     ags = [agreement(o[off[c]:off[c + 1]], nt[off[c]:off[c + 1]]) for c in range(nc)]
-    # the learned warm start on every cloud (one run)
+    # the other initialisations on every cloud (one run each): the learned
+    # warm start and the paper's PCA and Gauss-map options
     from paper_2405_13839_gb300 import train_init
     params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    dwg.dwg_set_init(hb, dwg.DWG_INIT_LEARNED, 1, params)
-    rc_l, iters_l = dwg.dwg_orient_batch(hb, out, nc)
-    torch.cuda.synchronize()
-    s_l = time.perf_counter() - t0
-    o = out.cpu().numpy()
-    ags_l = [agreement(o[off[c]:off[c + 1]], nt[off[c]:off[c + 1]]) for c in range(nc)]
+    inits = {}
+    for name, mode in (("learned", dwg.DWG_INIT_LEARNED), ("pca", dwg.DWG_INIT_PCA),
+                       ("gauss", dwg.DWG_INIT_GAUSS)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dwg.dwg_set_init(hb, mode, 1, params if name == "learned" else None)
+        _, its_i = dwg.dwg_orient_batch(hb, out, nc)
+        torch.cuda.synchronize()
+        s_i = time.perf_counter() - t0
+        o = out.cpu().numpy()
+        inits[name] = (s_i, list(its_i),
+                       [agreement(o[off[c]:off[c + 1]], nt[off[c]:off[c + 1]]) for c in range(nc)])
     dwg.dwg_destroy(hb)
     dev_s = sum(ms) / 1e3
     its = list(iters)
-    its_l = list(iters_l)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([dev_s, inter, s_l], dtype=torch.float64, device=dev)
+        t = torch.tensor([dev_s, inter] + [inits[k][0] for k in inits], dtype=torch.float64,
+                         device=dev)
         tmax = t.clone()
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         tsum = t.clone()
         dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        dev_s, inter, s_l = float(tmax[0]), float(tsum[1]), float(tmax[2])
+        dev_s, inter = float(tmax[0]), float(tsum[1])
         gathered = [None] * world
-        dist.all_gather_object(gathered, (ags, ags_l, its, its_l))
+        dist.all_gather_object(gathered, (ags, its, {k: v[1:] for k, v in inits.items()}))
         ags = [a for g in gathered for a in g[0]]
-        ags_l = [a for g in gathered for a in g[1]]
-        its = [i for g in gathered for i in g[2]]
-        its_l = [i for g in gathered for i in g[3]]
+        its = [i for g in gathered for i in g[1]]
+        inits = {k: (float(tmax[2 + j]), [i for g in gathered for i in g[2][k][0]],
+                     [a for g in gathered for a in g[2][k][1]])
+                 for j, k in enumerate(inits)}
         if rank != 0:
             return
-    iters, iters_l = its, its_l
+    iters = its
     nc = len(ags)
+    warm = {k: {"s": s_i, "iterations_mean": float(np.mean(it_i)), "iterations_max": int(max(it_i)),
+                "agreement_mean": float(np.mean(ag_i)), "agreement_min": min(ag_i),
+                "clouds_at_least_99pct": int(sum(a >= 0.99 for a in ag_i))}
+            for k, (s_i, it_i, ag_i) in inits.items()}
     line = {"metric": "GWN+grad interactions/s", "value": inter / dev_s, "unit": "interactions/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -594,11 +665,7 @@ def run_batch(args, rank=0, world=1, local=0):
                            "mean": float(np.mean(iters))},
             "agreement": {"min": min(ags), "mean": float(np.mean(ags)),
                           "clouds_at_least_99pct": int(sum(a >= 0.99 for a in ags))},
-            "warm_start": {"learned": {"s": s_l, "iterations_mean": float(np.mean(iters_l)),
-                                       "iterations_max": int(max(iters_l)),
-                                       "agreement_mean": float(np.mean(ags_l)),
-                                       "agreement_min": min(ags_l),
-                                       "clouds_at_least_99pct": int(sum(a >= 0.99 for a in ags_l))}},
+            "warm_start": warm,
             "clocks": ck}
     print(json.dumps(line))
 
@@ -690,6 +757,7 @@ def main():
                             "oriented on its own)" if W.get("labels") is not None else
                             "one global sign"),
         "warm_start": r["warm"],
+        "setup_and_variants": r["extras"],
         "interactions_per_step": r["value"] * r["dev_s"] / args.steps / world,
         "roofline": r["roof"], "cpu_baseline": cpu, "clocks": r["clocks"], "e2e": r["e2e"],
         "gpu_launches": r["launches"],

@@ -64,6 +64,8 @@ extern "C" {
 #define DWG_INIT_RANDOM 0
 #define DWG_INIT_GIVEN 1
 #define DWG_INIT_LEARNED 2
+#define DWG_INIT_PCA 3
+#define DWG_INIT_GAUSS 4
 
 /* Evaluation path: exact all-pairs sums, or the Barnes-Hut far field of
  * Sec. 5.2; AUTO takes all-pairs up to 65,536 points and the tree above
@@ -149,8 +151,57 @@ int dwg_set_update(dwg_handle h, int depth, int knn, int mode);
  */
 int dwg_set_tree(dwg_handle h, int path, float theta);
 
+/*
+ * Near-field regularisation of the kernel.
+ *   DWG_REG_SOFTEN (default): rho^2 = |p_j - q|^2 + eps^2 with the eps of
+ *     dwg_set_params (the paper's "small constant added to the denominator",
+ *     Sec. 3, read as Plummer softening).
+ *   DWG_REG_CLAMP: the modified Poisson kernel of Sec. 5.2 ("Poisson
+ *     Kernels"): rho = max(|p_j - q|, delta_j) with a radius per source and no
+ *     softening; inside the radius the term is <m_j, p_j - q> / delta_j^3
+ *     (times F(delta_j) when screened) and its gradient -m_j F / delta_j^3.
+ *     delta_j = the mean distance from p_j to those of its k nearest other
+ *     points (ties by smaller input index) whose distance lies in
+ *     [vmin, vmax]; if none does, the mean of all k distances clamped to
+ *     [vmin, vmax].  The paper uses k = 10, vmin = 0.0015, vmax = 0.015 in
+ *     its unit-box coordinates; vmin = vmax = 0 selects those values times
+ *     the largest extent of the points' bounding box.
+ *     Whether a pair lies inside is decided in float32 (|p_j - q|^2 from
+ *     float offsets against delta_j^2 rounded to float).
+ *     The modified kernel runs on the all-pairs path only: it is refused
+ *     while the path is DWG_PATH_TREE, DWG_PATH_AUTO then always picks
+ *     all-pairs, and dwg_autotune returns DWG_ERR_STATE.  Batch handles
+ *     refuse it (DWG_ERR_STATE).
+ *   k: [1, 31] (CLAMP only).  delta_out: float32 n, input order, host or
+ *   device, receives delta_j; may be NULL.
+ */
+#define DWG_REG_SOFTEN 0
+#define DWG_REG_CLAMP 1
+int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax,
+                           float *delta_out);
+
 /* Area weights a_i > 0 (float32, n, input order, host or device). */
 int dwg_set_weights(dwg_handle h, const float *a);
+
+/*
+ * Local-Voronoi area weights (Sec. 5.1, "Computing Area Weights"; the paper
+ * uses m = 15), computed on the device and installed as the handle's a_i.
+ * For each point p_i: its m nearest other points (ties by smaller input
+ * index; coincident copies count); the tangent plane through p_i whose
+ * normal is the smallest-eigenvalue eigenvector of the covariance of p_i and
+ * those neighbours (FP64); the neighbours projected onto it as the seeds of a
+ * 2D Voronoi diagram (a seed projecting onto p_i imposes nothing); a_i = the
+ * area of p_i's cell cut to the disk of radius half the largest projected
+ * neighbour distance (the cut bounds the cells of points on the hull of
+ * their neighbourhood and leaves interior cells of even samplings whole).
+ * A neighbourhood with no extent takes the mean of the other areas.
+ *   m:     in [3, 31].
+ *   a_out: float32 n (input order, host or device) receives the weights; may
+ *          be NULL.
+ * On a batch handle every cloud gets its own weights (a_out in the input
+ * layout).  Errors: DWG_ERR_INVALID (m), DWG_ERR_CUDA.
+ */
+int dwg_voronoi_weights(dwg_handle h, int m, float *a_out);
 
 /*
  * Initial normals for the next dwg_orient.  DWG_INIT_RANDOM draws uniform
@@ -167,6 +218,18 @@ int dwg_set_weights(dwg_handle h, const float *a);
  * dwg_mlp_forward); the initial normal of each point is the normalised
  * network output for its patch features (dwg_mlp_features); where the output
  * is zero or not finite the random normal from `seed` is kept.
+ * DWG_INIT_PCA (Sec. 5.1, "Normal Initialization"): the eigenvector of the
+ * smallest eigenvalue of the covariance of the 10 nearest input points (the
+ * point itself included; ties by smaller input index), computed in FP64 on
+ * the offsets from the point; PCA gives the line, and the direction is the
+ * one pointing away from the centre c of the bounding box (n . (p - c) > 0,
+ * the Gauss map's side; where that is 0: n_z > 0, then n_y > 0, then
+ * n_x > 0).  Where the covariance is zero (coincident points) the random
+ * normal from `seed` is kept.  normals is ignored.
+ * DWG_INIT_GAUSS (Sec. 5.1): n_i = (p_i - c) / |p_i - c| in FP64, c the centre
+ * of the points' bounding box (the paper's models sit in a box centred at the
+ * origin); a point at c keeps the random normal from `seed`.  normals is
+ * ignored.
  */
 int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals);
 
@@ -253,8 +316,8 @@ int dwg_get_corners(dwg_handle h, int64_t *keys_out, int64_t cap, int64_t *count
  *   its default octree depth is round(log2(n) / 2) clamped to [5, 10].
  *   dwg_set_params / dwg_set_update / dwg_set_tree / dwg_set_convergence on
  *   the batch handle apply to every cloud (dwg_set_params with eps = 0 keeps
- *   each cloud's own default softening); dwg_set_init takes DWG_INIT_RANDOM
- *   (cloud c uses seed + c).
+ *   each cloud's own default softening); dwg_set_init takes every mode but
+ *   DWG_INIT_GIVEN (cloud c uses seed + c).
  * dwg_orient_batch: runs every cloud until it converges (or max_iters); a
  *   converged cloud stops iterating while the others go on.  The whole loop
  *   is one CUDA graph launch; per iteration the all-pairs sums of every

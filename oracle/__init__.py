@@ -16,6 +16,7 @@ invariants, library routines or analytic shapes (tests/test_oracle_*.py).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -53,7 +54,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("eps", ctypes.c_double),
                 ("lmbda", ctypes.c_double), ("depth", ctypes.c_int),
                 ("knn", ctypes.c_int), ("mode", ctypes.c_int),
-                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("rule", ctypes.c_int)]
+                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("rule", ctypes.c_int),
+                ("delta", ctypes.c_void_p)]
 
 
 def _load():
@@ -64,7 +66,7 @@ def _load():
             P = ctypes.c_void_p
             i64 = ctypes.c_int64
             lib.dwgo_gwn.argtypes = [i64, P, P, P, i64, P, ctypes.c_int, ctypes.c_double,
-                                     ctypes.c_double, P, P]
+                                     ctypes.c_double, P, P, P]
             lib.dwgo_cube.argtypes = [i64, P, ctypes.c_int, P]
             lib.dwgo_cells.argtypes = [i64, P, ctypes.c_int, P]
             lib.dwgo_octree.argtypes = [i64, P, ctypes.c_int, P, i64]
@@ -108,17 +110,21 @@ def _ptr(a):
 
 
 def gwn(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0.0, lam=0.0,
-        grad=True):
-    """w and grad w at queries (Eq. 2/3; Eq. 5 when kernel is screened)."""
+        grad=True, delta=None):
+    """w and grad w at queries (Eq. 2/3; Eq. 5 when kernel is screened).
+    delta: per-source radii of the modified kernel (Sec. 5.2), which then
+    replaces the softening eps."""
     lib = _load()
     p = _d(points, 3)
     nn = _d(normals, 3)
     a = _d(weights).ravel()
     q = _d(queries, 3)
+    dl = None if delta is None else _d(delta).ravel()
     w = np.zeros(len(q))
     g = np.zeros((len(q), 3)) if grad else None
     lib.dwgo_gwn(len(p), _ptr(p), _ptr(nn), _ptr(a), len(q), _ptr(q), int(kernel),
-                 float(eps), float(lam), _ptr(w), _ptr(g) if grad else None)
+                 float(eps), float(lam), _ptr(dl) if dl is not None else None, _ptr(w),
+                 _ptr(g) if grad else None)
     return (w, g) if grad else w
 
 
@@ -207,9 +213,13 @@ def scatter_normals(points, face_rows, k, n_old):
 
 
 def params(kernel=KERNEL_PLAIN, eps=0.0, lam=0.0, depth=6, knn=10, mode=MODE_LEVELSET,
-           max_iters=30, tol=0.1, rule=0):
-    return _Params(int(kernel), float(eps), float(lam), int(depth), int(knn), int(mode),
-                   int(max_iters), float(tol), int(rule))
+           max_iters=30, tol=0.1, rule=0, delta=None):
+    """delta: per-point radii of the modified kernel (Sec. 5.2) or None."""
+    dl = None if delta is None else _d(delta).ravel()
+    prm = _Params(int(kernel), float(eps), float(lam), int(depth), int(knn), int(mode),
+                  int(max_iters), float(tol), int(rule), dl.ctypes.data if dl is not None else None)
+    prm._delta_keep = dl  # the struct points into this array
+    return prm
 
 
 def iterate(points, weights, n_old, prm):
@@ -304,3 +314,183 @@ def tree_gwn_group(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0
     if want_count:
         out.append(cnt)
     return tuple(out) if len(out) > 1 else w
+
+
+# ----------------------------------------------------------------------------
+# Initial normals (Sec. 5.1, "Normal Initialization")
+# ----------------------------------------------------------------------------
+PCA_K = 10
+
+
+def pca_normals(points, k=PCA_K):
+    """PCA initialisation: for each point, the eigenvector of the smallest
+    eigenvalue of the covariance of its k nearest input points (the point
+    itself included; brute force in FP64, ties by the smaller index), taken
+    on the offsets from the point.  PCA gives a line; the direction chosen
+    points away from the bounding-box centre c (n . (p - c) > 0, the side of
+    the Gauss map, which is centred the same way), and where that product is
+    zero the one with n_z > 0 (n_y > 0 where n_z = 0, then n_x > 0).
+
+    Returns (normals (n, 3) float64, gap (n,) float64): gap is the relative
+    eigen-gap (lambda_2 - lambda_1) / lambda_3 that bounds how well the
+    eigenvector is determined.  Rows whose covariance is zero are NaN with
+    gap 0 (the library keeps its random normal there)."""
+    p = _d(points, 3)
+    kk = min(int(k), len(p))
+    idx = knn(p, p, kk)
+    d = p[idx] - p[:, None, :]
+    e = d - d.mean(axis=1, keepdims=True)
+    C = np.einsum("nki,nkj->nij", e, e) / kk
+    lam, V = np.linalg.eigh(C)
+    n = V[:, :, 0].copy()
+    c = 0.5 * (p.min(axis=0) + p.max(axis=0))
+    side = np.sum(n * (p - c), axis=1)
+    axis_rule = (n[:, 2] < 0) | ((n[:, 2] == 0) & ((n[:, 1] < 0) | ((n[:, 1] == 0) & (n[:, 0] < 0))))
+    flip = np.where(side != 0.0, side < 0.0, axis_rule)
+    n[flip] *= -1.0
+    zero = ~np.any(C != 0.0, axis=(1, 2))
+    n[zero] = np.nan
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gap = np.where(lam[:, 2] > 0, (lam[:, 1] - lam[:, 0]) / lam[:, 2], 0.0)
+    return n, gap
+
+
+def gauss_map_normals(points):
+    """Gauss-map initialisation: n_i = (p_i - c) / |p_i - c| in FP64, c the
+    centre of the bounding box of the (float32) points.  Rows at c are NaN."""
+    p = _d(points, 3)
+    c = 0.5 * (p.min(axis=0) + p.max(axis=0))
+    d = p - c
+    l = np.sqrt(np.sum(d * d, axis=1))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        n = d / l[:, None]
+    n[l == 0] = np.nan
+    return n
+
+
+# ----------------------------------------------------------------------------
+# Area weights a_i (Sec. 5.1, "Computing Area Weights")
+# ----------------------------------------------------------------------------
+VORONOI_M = 15
+
+
+def _clip_halfplane(poly, a, b):
+    """Convex polygon (list of 2D points, counter-clockwise) intersected with
+    the half-plane a . x <= b."""
+    out = []
+    k = len(poly)
+    for t in range(k):
+        P, Q = poly[t], poly[(t + 1) % k]
+        fp, fq = a @ P - b, a @ Q - b
+        if fp <= 0:
+            out.append(P)
+        if (fp < 0 < fq) or (fq < 0 < fp):
+            out.append(P + (fp / (fp - fq)) * (Q - P))
+    return out
+
+
+def _disk_polygon_area(poly, R):
+    """Area of (convex polygon containing the origin) intersected with the
+    disk of radius R about the origin: per edge, the triangle (0, A, B) cut by
+    the circle, its inside part as triangles and its outside parts as circular
+    sectors."""
+    def cross(u, v):
+        return u[0] * v[1] - u[1] * v[0]
+
+    def sector(u, v):
+        return 0.5 * R * R * math.atan2(cross(u, v), u @ v)
+
+    total = 0.0
+    k = len(poly)
+    for t in range(k):
+        A, B = poly[t], poly[(t + 1) % k]
+        D = B - A
+        a, b, c = D @ D, A @ D, A @ A - R * R
+        disc = b * b - a * c
+        if a == 0.0:
+            continue
+        if disc <= 0.0:
+            total += sector(A, B)
+            continue
+        s = math.sqrt(disc)
+        t1, t2 = (-b - s) / a, (-b + s) / a
+        s1, s2 = min(max(t1, 0.0), 1.0), min(max(t2, 0.0), 1.0)
+        P1, P2 = A + s1 * D, A + s2 * D
+        total += sector(A, P1) + 0.5 * cross(P1, P2) + sector(P2, B)
+    return total
+
+
+def voronoi_weights(points, m=VORONOI_M):
+    """Local-Voronoi area weights, the paper's approximation of geodesic
+    Voronoi areas.  For each point p_i:
+      1. its m nearest other points (brute force in FP64, ties by the smaller
+         index; p_i itself is left out by index, coincident copies stay);
+      2. the tangent plane at p_i: normal = smallest-eigenvalue eigenvector of
+         the covariance of p_i and those neighbours;
+      3. the neighbours' offsets projected onto the plane (any orthonormal
+         basis: the area does not depend on it);
+      4. the 2D Voronoi cell of the origin among the projected seeds (seeds
+         that project onto the origin impose nothing), cut to the disk of
+         radius R_i = half the largest projected neighbour distance, which
+         bounds the cells of points on the hull of their neighbourhood;
+      5. a_i = its area.
+    A neighbourhood with no extent (zero area) takes the mean of the positive
+    areas.  Returns float64 (n,)."""
+    p = _d(points, 3)
+    n = len(p)
+    kk = min(int(m) + 1, n)
+    idx = knn(p, p, kk)
+    out = np.zeros(n)
+    for i in range(n):
+        nb = [j for j in idx[i] if j != i][: kk - 1]
+        d = p[nb] - p[i]
+        X = np.vstack([np.zeros(3), d])
+        X = X - X.mean(axis=0)
+        C = X.T @ X / len(X)
+        if not np.any(C != 0.0):
+            continue
+        nrm = np.linalg.eigh(C)[1][:, 0]
+        ax = np.zeros(3)
+        ax[int(np.argmin(np.abs(nrm)))] = 1.0
+        e1 = np.cross(nrm, ax)
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(nrm, e1)
+        q = np.stack([d @ e1, d @ e2], axis=1)
+        r = np.sqrt(np.sum(q * q, axis=1))
+        R = 0.5 * r.max()
+        if not R > 0.0:
+            continue
+        poly = [np.array(v, float) for v in ((-R, -R), (R, -R), (R, R), (-R, R))]
+        for j in range(len(q)):
+            if r[j] > 0.0:
+                poly = _clip_halfplane(poly, q[j], 0.5 * r[j] * r[j])
+        out[i] = _disk_polygon_area(poly, R) if len(poly) >= 3 else 0.0
+    good = out > 0.0
+    if good.any() and not good.all():
+        out[~good] = out[good].mean()
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Clamp radii of the modified Poisson kernel (Sec. 5.2, "Poisson Kernels")
+# ----------------------------------------------------------------------------
+def clamp_radii(points, k=10, vmin=0.0015, vmax=0.015):
+    """delta_i = mean distance from p_i to those of its k nearest other points
+    (ties by the smaller index) whose distance lies in [vmin, vmax]; if none
+    does, the mean of all k distances clamped to [vmin, vmax].  Distances in
+    FP64 from the float32 points; vmin and vmax as float32 values."""
+    p = _d(points, 3)
+    n = len(p)
+    kk = min(int(k) + 1, n)
+    idx = knn(p, p, kk)
+    lo, hi = float(np.float32(vmin)), float(np.float32(vmax))
+    out = np.zeros(n)
+    for i in range(n):
+        nb = [j for j in idx[i] if j != i][: kk - 1]
+        if not nb:
+            out[i] = lo
+            continue
+        d = np.sqrt(np.sum((p[nb] - p[i]) ** 2, axis=1))
+        sel = d[(d >= lo) & (d <= hi)]
+        out[i] = sel.mean() if len(sel) else min(max(d.mean(), lo), hi)
+    return out

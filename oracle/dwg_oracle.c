@@ -23,7 +23,14 @@
  *     of each face gradient onto its k nearest input points and
  *     normalisation (Eq. 7);
  *   - the convergence rule of Sec. 5.1: mean of the largest 1% of the
- *     per-point normal changes, in degrees, compared with eps (0.1 deg).
+ *     per-point normal changes, in degrees, compared with eps (0.1 deg);
+ *   - the modified Poisson kernel of Sec. 5.2 ("Poisson Kernels"): with a
+ *     per-source radius delta_j the denominator becomes delta_j^3 when
+ *     |p_j - q| < delta_j (no softening then).  Whether a pair is inside is
+ *     an integer decision taken from floating point, so it is taken in the
+ *     CUDA kernel's precision: |p_j - q|^2 in float32 (offsets rounded to
+ *     float, squares summed with fused multiply-adds) against delta_j^2
+ *     rounded to float32.  Everything else stays FP64.
  *
  * All arithmetic is double precision.  Build with -ffp-contract=off so that
  * a*b+c is never fused: the cell-quantisation step below must round exactly
@@ -40,6 +47,18 @@
 /* Eq. 2/3 and Eq. 5: w(q) and grad_q w(q)                                  */
 /* ------------------------------------------------------------------------ */
 
+/* Is source p within the clamp radius delta of q?  Decided like the CUDA
+ * kernel: float32 offsets, squares summed by fused multiply-adds in the
+ * order x, y, z, compared with delta^2 rounded to float32. */
+static int clamp_inside(const double *p, const double *q, double delta)
+{
+    float dx = (float)p[0] - (float)q[0];
+    float dy = (float)p[1] - (float)q[1];
+    float dz = (float)p[2] - (float)q[2];
+    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    return r2 < (float)(delta * delta);
+}
+
 /*
  * One source term and its gradient with respect to q.
  *   d = p - q, rho^2 = |d|^2 + eps^2, m = a n / (4 pi), phi = <m, d> / rho^3.
@@ -47,14 +66,23 @@
  *   screened: F = exp(-s rho)(1 + s rho), s = sqrt(lambda)
  *             t = F phi,              grad t = F grad(phi) + phi s^2 exp(-s rho) d
  * (grad_q rho = -d / rho and dF/drho = -s^2 rho exp(-s rho)).
+ * Modified kernel (delta > 0, eps unused): rho = |d| outside the radius; inside
+ * it rho = delta is constant, so t = F(delta) <m, d> / delta^3 and
+ * grad t = -F(delta) m / delta^3.
  */
 static void term(const double *p, const double *nrm, double a, const double *q,
-                 int screened, double eps, double s, double *t, double g[3])
+                 int screened, double eps, double delta, double s, double *t, double g[3])
 {
     double d[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
     double m[3] = {a * nrm[0] / (4.0 * DWGO_PI), a * nrm[1] / (4.0 * DWGO_PI),
                    a * nrm[2] / (4.0 * DWGO_PI)};
-    double rho2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps * eps;
+    int inside = delta > 0.0 && clamp_inside(p, q, delta);
+    double rho2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (delta > 0.0) {
+        if (inside) rho2 = delta * delta;
+    } else {
+        rho2 += eps * eps;
+    }
     double rho = sqrt(rho2);
     double rho3 = rho2 * rho;
     double phi = (m[0] * d[0] + m[1] * d[1] + m[2] * d[2]) / rho3;
@@ -65,8 +93,8 @@ static void term(const double *p, const double *nrm, double a, const double *q,
     }
     *t = F * phi;
     for (int k = 0; k < 3; ++k) {
-        double gphi = -m[k] / rho3 + 3.0 * phi * d[k] / rho2;
-        g[k] = F * gphi + phi * s * s * E * d[k];
+        double gphi = -m[k] / rho3 + (inside ? 0.0 : 3.0 * phi * d[k] / rho2);
+        g[k] = F * gphi + (inside ? 0.0 : phi * s * s * E * d[k]);
     }
 }
 
@@ -74,12 +102,14 @@ static void term(const double *p, const double *nrm, double a, const double *q,
  * w and grad w at m queries from n oriented, weighted points.
  *   p, nrm: n x 3 row-major; a: n weights (Sec. 3: Voronoi areas, or 1);
  *   q: m x 3; kernel 0 = plain (Eq. 2/3), 1 = screened (Eq. 5);
+ *   delta: n clamp radii of the modified kernel (Sec. 5.2), or NULL for the
+ *   softened kernel with eps;
  *   w: m outputs; g: m x 3 outputs or NULL.
  * Terms with p_j == q exactly (all three coordinates) are skipped.
  */
 void dwgo_gwn(int64_t n, const double *p, const double *nrm, const double *a,
               int64_t m, const double *q, int kernel, double eps, double lambda,
-              double *w, double *g)
+              const double *delta, double *w, double *g)
 {
     double s = sqrt(lambda > 0 ? lambda : 0.0);
     int screened = (kernel == 1);
@@ -92,7 +122,7 @@ void dwgo_gwn(int64_t n, const double *p, const double *nrm, const double *a,
             if (pj[0] == qi[0] && pj[1] == qi[1] && pj[2] == qi[2])
                 continue;
             double t, gt[3];
-            term(pj, nrm + 3 * j, a[j], qi, screened, eps, s, &t, gt);
+            term(pj, nrm + 3 * j, a[j], qi, screened, eps, delta ? delta[j] : 0.0, s, &t, gt);
             wi += t;
             gi[0] += gt[0];
             gi[1] += gt[1];
@@ -510,6 +540,7 @@ typedef struct {
     int max_iters;
     double tol;      /* degrees */
     int rule;        /* 0: top-1 % mean change (Sec. 5.1); 1: mean |n_new - n_old| (Fig. 6) */
+    const double *delta; /* n clamp radii of the modified kernel (Sec. 5.2), or NULL */
 } dwgo_params;
 
 /*
@@ -554,7 +585,7 @@ int64_t dwgo_iterate(int64_t n, const double *p, const double *a, const double *
                      double *gp, double *iso_out)
 {
     double *g = gp ? gp : (double *)malloc(sizeof(double) * 3 * (size_t)n);
-    dwgo_gwn(n, p, n_old, a, n, p, prm->kernel, prm->eps, prm->lambda, wp, g);
+    dwgo_gwn(n, p, n_old, a, n, p, prm->kernel, prm->eps, prm->lambda, prm->delta, wp, g);
     double iso = 0.0;
     for (int64_t i = 0; i < n; ++i) iso += wp[i];
     iso /= (double)n;
@@ -573,7 +604,8 @@ int64_t dwgo_iterate(int64_t n, const double *p, const double *a, const double *
         double *cpos = (double *)malloc(sizeof(double) * 3 * (size_t)nc);
         dwgo_corner_positions(nc, keys, d, cube, cpos);
         double *wc = (double *)malloc(sizeof(double) * (size_t)nc);
-        dwgo_gwn(n, p, n_old, a, nc, cpos, prm->kernel, prm->eps, prm->lambda, wc, NULL);
+        dwgo_gwn(n, p, n_old, a, nc, cpos, prm->kernel, prm->eps, prm->lambda, prm->delta, wc,
+                 NULL);
         nf = dwgo_faces(nl, leaves, d, cube, nc, keys, wc, iso, NULL, 0);
         double *faces = (double *)malloc(sizeof(double) * 6 * (size_t)(nf > 0 ? nf : 1));
         dwgo_faces(nl, leaves, d, cube, nc, keys, wc, iso, faces, nf);
@@ -807,7 +839,7 @@ static void dipole_term(const float *cf, const double *M, const double *q, int s
     double nrm_len = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
     if (nrm_len == 0.0) { *t = 0.0; g[0] = g[1] = g[2] = 0.0; return; }
     for (int k = 0; k < 3; ++k) one[k] = m[k] / nrm_len;
-    term(pc, one, nrm_len * 4.0 * DWGO_PI, q, screened, eps, s, t, g);
+    term(pc, one, nrm_len * 4.0 * DWGO_PI, q, screened, eps, 0.0, s, t, g);
 }
 
 static int far_test(const bh_tree *T, int64_t node, const double *q)
@@ -845,7 +877,7 @@ static void bh_query(const bh_tree *T, int64_t node, const double *p, const doub
             const double *pi = p + 3 * i;
             if (pi[0] == q[0] && pi[1] == q[1] && pi[2] == q[2]) continue;
             double t, gt[3];
-            term(pi, nrm + 3 * i, a[i], q, screened, eps, s, &t, gt);
+            term(pi, nrm + 3 * i, a[i], q, screened, eps, 0.0, s, &t, gt);
             *w += t;
             g[0] += gt[0]; g[1] += gt[1]; g[2] += gt[2];
             *count += 1.0;
@@ -974,7 +1006,7 @@ void dwgo_tree_gwn_group(int64_t n, const double *p, const double *nrm, const do
                     int64_t k = T.order[j];
                     const double *pk = p + 3 * k;
                     if (pk[0] == qi[0] && pk[1] == qi[1] && pk[2] == qi[2]) continue;
-                    term(pk, nrm + 3 * k, a[k], qi, screened, eps, s, &t, gt);
+                    term(pk, nrm + 3 * k, a[k], qi, screened, eps, 0.0, s, &t, gt);
                     wi += t;
                     gq[0] += gt[0]; gq[1] += gt[1]; gq[2] += gt[2];
                     ci += 1.0;

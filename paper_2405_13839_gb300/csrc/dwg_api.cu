@@ -43,6 +43,7 @@ void set_global_error(const std::string &msg)
 namespace dwg {
 bool use_tree(const Ctx *c)
 {
+    if (c->reg_mode == DWG_REG_CLAMP) return false;  // the modified kernel is all-pairs only
     if (c->path == DWG_PATH_TREE) return true;
     if (c->path == DWG_PATH_ALLPAIRS) return false;
     return c->n > 65536;
@@ -387,6 +388,7 @@ static int check_device_err(Ctx *c)
         if (herr & kErrNonfinite) return fail(c, DWG_ERR_NONFINITE, "non-finite or invalid input");
         if (herr & kErrOverflow) return fail(c, DWG_ERR_CUDA, "face buffer overflow");
         if (herr & kErrStack) return fail(c, DWG_ERR_CUDA, "kNN traversal stack overflow");
+        if (herr & kErrGeometry) return fail(c, DWG_ERR_CUDA, "Voronoi cell vertex overflow");
         return fail(c, DWG_ERR_CUDA, "device error flag set");
     }
     return DWG_OK;
@@ -396,10 +398,15 @@ static int check_device_err(Ctx *c)
 static int prepare_normals(Ctx *c)
 {
     if (c->normals_pending) {
-        if (c->init_mode == DWG_INIT_RANDOM || c->init_mode == DWG_INIT_LEARNED) {
+        if (c->init_mode != DWG_INIT_GIVEN) {
+            // the random draw is also the fallback of the other modes
             if (launch_random_normals(c->d_nrm, c->d_perm, c->n, c->seed, c->stream) !=
                 cudaSuccess)
                 return fail(c, DWG_ERR_CUDA, "random normals launch failed");
+            if (c->init_mode == DWG_INIT_PCA && launch_init_pca(c) != cudaSuccess)
+                return fail(c, DWG_ERR_CUDA, "PCA normals launch failed");
+            if (c->init_mode == DWG_INIT_GAUSS && launch_init_gauss(c) != cudaSuccess)
+                return fail(c, DWG_ERR_CUDA, "Gauss-map normals launch failed");
             if (c->init_mode == DWG_INIT_LEARNED) {
                 float *X = nullptr, *Y = nullptr;
                 double *cR = nullptr;
@@ -428,6 +435,8 @@ static int prepare_normals(Ctx *c)
         c->normals_pending = false;
     }
     if (launch_pack_sources(c->d_p4, c->d_nrm, c->n, c->npad, c->d_src, c->stream) != cudaSuccess)
+        return fail(c, DWG_ERR_CUDA, "pack launch failed");
+    if (c->reg_mode == DWG_REG_CLAMP && launch_pack_sources16(c) != cudaSuccess)
         return fail(c, DWG_ERR_CUDA, "pack launch failed");
     return DWG_OK;
 }
@@ -482,7 +491,8 @@ void dwg_destroy(dwg_handle h)
                     h->d_sel, h->d_sel_hist, h->d_sel_part,
                     h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err,
                     h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
-                    h->d_tree_mrec, h->d_tree_frec, h->d_counter, h->d_mlp_params};
+                    h->d_tree_mrec, h->d_tree_frec, h->d_counter, h->d_mlp_params,
+                    h->d_delta2, h->d_src16};
     for (void *p : bufs) cudaFree(p);
     free_lists(h->lists_p);
     free_lists(h->lists_c);
@@ -528,6 +538,7 @@ static int create_impl(dwg_ctx *c, const float *points, int64_t n)
         double L = ext > 0.0 ? ext * 1.125 : 1.0;
         for (int k = 0; k < 3; ++k) {
             double cen = (mn[k] + mx[k]) * 0.5;
+            c->bbox_c[k] = cen;
             c->cube_lo[k] = cen - L * 0.5;
         }
         c->cube_L = L;
@@ -678,6 +689,8 @@ int dwg_set_tree(dwg_handle h, int path, float theta)
     if (path != DWG_PATH_AUTO && path != DWG_PATH_ALLPAIRS && path != DWG_PATH_TREE)
         return fail(h, DWG_ERR_INVALID, "unknown path");
     if (!(theta > 0.f) || !(theta <= 1.f)) return fail(h, DWG_ERR_INVALID, "theta must be in (0, 1]");
+    if (path == DWG_PATH_TREE && h->reg_mode == DWG_REG_CLAMP)
+        return fail(h, DWG_ERR_STATE, "the modified kernel (DWG_REG_CLAMP) runs on the all-pairs path");
     h->path = path;
     h->tree_beta = 1.0f / theta;
     invalidate_graph(h);
@@ -702,6 +715,97 @@ int dwg_set_weights(dwg_handle h, const float *a)
     return rc;
 }
 
+int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax,
+                           float *delta_out)
+{
+    if (!h) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    if (mode != DWG_REG_SOFTEN && mode != DWG_REG_CLAMP)
+        return fail(h, DWG_ERR_INVALID, "mode must be DWG_REG_SOFTEN or DWG_REG_CLAMP");
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "batch handles use the softened kernel");
+    if (mode == DWG_REG_SOFTEN) {
+        if (h->reg_mode != mode) {
+            h->reg_mode = mode;
+            invalidate_graph(h);
+            ++h->bufgen;
+        }
+        return DWG_OK;
+    }
+    if (k < 1 || k > 31) return fail(h, DWG_ERR_INVALID, "k must be in [1, 31]");
+    if (vmin == 0.f && vmax == 0.f) {
+        // the paper's 0.0015 and 0.015 in a unit where the largest extent is 1
+        const double ext = h->cube_L / 1.125;
+        vmin = (float)(0.0015 * ext);
+        vmax = (float)(0.015 * ext);
+    }
+    if (!(vmin > 0.f) || !(vmax >= vmin) || !isfinite(vmax))
+        return fail(h, DWG_ERR_INVALID, "need 0 < vmin <= vmax (or both 0 for the defaults)");
+    if (h->path == DWG_PATH_TREE)
+        return fail(h, DWG_ERR_STATE, "the modified kernel runs on the all-pairs path (set "
+                                      "DWG_PATH_AUTO or DWG_PATH_ALLPAIRS first)");
+    if (!h->d_delta2) DWG_CUDA_TRY(h, cudaMalloc(&h->d_delta2, h->n * sizeof(float)));
+    if (!h->d_src16)
+        DWG_CUDA_TRY(h, cudaMalloc(&h->d_src16, h->npad * kSrcFloatsClamp * sizeof(float)));
+    float *d_out = nullptr;
+    auto run = [&]() -> int {
+        if (delta_out) DWG_CUDA_TRY(h, cudaMalloc(&d_out, h->n * sizeof(float)));
+        if (launch_clamp_delta(h, k, (double)vmin, (double)vmax, d_out) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "clamp radii launch failed");
+        int r = check_device_err(h);
+        if (r) return r;
+        if (delta_out) return download(h, delta_out, d_out, h->n * sizeof(float));
+        return DWG_OK;
+    };
+    int rc = run();
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = fail(h, DWG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaFree(d_out);
+    if (rc) return rc;
+    h->reg_mode = mode;
+    // the records are repacked (with delta^2) before the next evaluation
+    invalidate_graph(h);
+    ++h->bufgen;  // a captured graph holds the other kernels and records
+    return DWG_OK;
+}
+
+int dwg_voronoi_weights(dwg_handle h, int m, float *a_out)
+{
+    if (!h) return DWG_ERR_INVALID;
+    cudaSetDevice(h->device);
+    if (m < 3 || m > 31) return fail(h, DWG_ERR_INVALID, "m must be in [3, 31]");
+    if (h->is_batch) {
+        for (size_t c = 0; c < h->clouds.size(); ++c) {
+            int rc = dwg_voronoi_weights(h->clouds[c], m, a_out ? a_out + h->offsets[c] : nullptr);
+            if (rc) return fail(h, rc, h->clouds[c]->err);
+        }
+        return DWG_OK;
+    }
+    int rc;
+    double *scratch = nullptr;
+    float *d_out = nullptr;
+    auto run = [&]() -> int {
+        DWG_CUDA_TRY(h, cudaMalloc(&scratch, (h->n + 1) * sizeof(double)));
+        if (a_out) DWG_CUDA_TRY(h, cudaMalloc(&d_out, h->n * sizeof(float)));
+        if (launch_voronoi_weights(h, m, scratch, d_out) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "Voronoi weights launch failed");
+        int r = check_device_err(h);
+        if (r) return r;
+        h->tree_built = false;  // node centres depend on the weights
+        if (a_out) return download(h, a_out, d_out, h->n * sizeof(float));
+        return DWG_OK;
+    };
+    rc = run();
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = fail(h, DWG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaFree(scratch);
+    cudaFree(d_out);
+    return rc;
+}
+
 static int normals_from_caller(dwg_handle h, const float *normals, float4 *dst)
 {
     float *d = nullptr;
@@ -722,7 +826,7 @@ int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals)
     cudaSetDevice(h->device);
     if (h->is_batch) {
         if (mode == DWG_INIT_GIVEN)
-            return fail(h, DWG_ERR_STATE, "batch handles take DWG_INIT_RANDOM or DWG_INIT_LEARNED");
+            return fail(h, DWG_ERR_STATE, "batch handles take no DWG_INIT_GIVEN");
         // cloud c draws from seed + c
         for (size_t c = 0; c < h->clouds.size(); ++c) {
             int rc = dwg_set_init(h->clouds[c], mode, seed + c, normals);
@@ -732,7 +836,7 @@ int dwg_set_init(dwg_handle h, int mode, uint64_t seed, const float *normals)
         h->seed = seed;
         return DWG_OK;
     }
-    if (mode == DWG_INIT_RANDOM) {
+    if (mode == DWG_INIT_RANDOM || mode == DWG_INIT_PCA || mode == DWG_INIT_GAUSS) {
         h->init_mode = mode;
         h->seed = seed;
     } else if (mode == DWG_INIT_LEARNED) {
@@ -1003,6 +1107,9 @@ int dwg_autotune(dwg_handle h, int what, double w_budget, const char *cache_path
         !(what & (DWG_TUNE_SHAPES | DWG_TUNE_TREE)))
         return fail(h, DWG_ERR_INVALID,
                     "what: DWG_TUNE_SHAPES and/or DWG_TUNE_TREE, optionally DWG_TUNE_RELATIVE");
+    if (h->reg_mode == DWG_REG_CLAMP)
+        return fail(h, DWG_ERR_STATE, "the modified kernel has one evaluator shape and no tree: "
+                                      "nothing to tune");
     cudaSetDevice(h->device);
     invalidate_graph(h);
     if (h->is_batch) {
@@ -1039,6 +1146,8 @@ int dwg_get_tuning(dwg_handle h, dwg_tuning *out)
 int dwg_set_tuning(dwg_handle h, const dwg_tuning *t)
 {
     if (!h || !t) return DWG_ERR_INVALID;
+    if (h->reg_mode == DWG_REG_CLAMP && t->path == DWG_PATH_TREE)
+        return fail(h, DWG_ERR_STATE, "the modified kernel (DWG_REG_CLAMP) runs on the all-pairs path");
     invalidate_graph(h);
     if (h->is_batch) {
         for (dwg_ctx *c : h->clouds) {

@@ -90,8 +90,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 constexpr int kEvalThreads = 128;  // CTA size of the default shapes
 constexpr int kStages = 4;
 
-// One CTA's work: query tile `qtile` against source chunk `chunk`.
-template <int P, int NT, bool GRAD, bool SCREENED>
+// One CTA's work: query tile `qtile` against source chunk `chunk`.  With
+// CLAMP the records carry delta_j^2 and the kernel is the modified one of
+// Sec. 5.2: rho^2 = max(|p_j - q|^2, delta_j^2) (no softening), and inside the
+// radius the term's gradient keeps only its -F m / rho^3 part.
+template <int P, int NT, bool GRAD, bool SCREENED, bool CLAMP = false>
 __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t ntiles_total,
                                           const float4 *__restrict__ q, int64_t m,
                                           int tiles_per_chunk, float *__restrict__ part,
@@ -99,7 +102,9 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                                           int *__restrict__ err, int64_t qtile, int chunk)
 {
     constexpr int T = kSrcTile;
-    constexpr int TILE_FLOATS = T * kSrcFloats;
+    constexpr int RECF = CLAMP ? kSrcFloatsClamp : kSrcFloats;
+    constexpr int RQ = RECF / 4;  // 16-byte words per record
+    constexpr int TILE_FLOATS = T * RECF;
     constexpr uint32_t TILE_BYTES = TILE_FLOATS * 4;
     constexpr int QB = NT * 2 * P;
     constexpr int NA = GRAD ? 4 : 1;
@@ -171,9 +176,11 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
             const ulonglong2 *rec = reinterpret_cast<const ulonglong2 *>(sbuf[s]);
 #pragma unroll 2
             for (int j = 0; j < T; ++j) {
-                const ulonglong2 r0 = rec[3 * j + 0];  // (x,x) (y,y)
-                const ulonglong2 r1 = rec[3 * j + 1];  // (z,z) (mx,mx)
-                const ulonglong2 r2v = rec[3 * j + 2]; // (my,my) (mz,mz)
+                const ulonglong2 r0 = rec[RQ * j + 0];  // (x,x) (y,y)
+                const ulonglong2 r1 = rec[RQ * j + 1];  // (z,z) (mx,mx)
+                const ulonglong2 r2v = rec[RQ * j + 2]; // (my,my) (mz,mz)
+                f2 d2c = zero;
+                if (CLAMP) d2c = rec[RQ * j + 3].x;     // (d2,d2)
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     f2 dx = sub2(r0.x, qx[p]);
@@ -182,6 +189,8 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                     f2 rr = fma2(dx, dx, eps2);
                     rr = fma2(dy, dy, rr);
                     rr = fma2(dz, dz, rr);
+                    const f2 r2raw = rr;
+                    if (CLAMP) rr = max2(rr, d2c);
                     f2 inv = rsqrt2(rr);
                     f2 md = mul2(r1.y, dx);
                     md = fma2(r2v.x, dy, md);
@@ -193,6 +202,7 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                             f2 phi = mul2(md, i3);
                             tw[p] = add2(tw[p], phi);
                             f2 c = mul2(phi, i2);
+                            if (CLAMP) c = keep_ge(c, r2raw, d2c);
                             t1x[p] = fma2(c, dx, t1x[p]);
                             t1y[p] = fma2(c, dy, t1y[p]);
                             t1z[p] = fma2(c, dz, t1z[p]);
@@ -212,6 +222,7 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                             f2 fi3 = mul2(F, i3);
                             f2 cc = fma2(three, mul2(F, i2), mul2(s2v, e));
                             f2 c = mul2(phi, cc);
+                            if (CLAMP) c = keep_ge(c, r2raw, d2c);
                             t1x[p] = fma2(c, dx, t1x[p]);
                             t1y[p] = fma2(c, dy, t1y[p]);
                             t1z[p] = fma2(c, dz, t1z[p]);
@@ -288,14 +299,15 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
     }
 }
 
-template <int P, int NT, bool GRAD, bool SCREENED>
+template <int P, int NT, bool GRAD, bool SCREENED, bool CLAMP = false>
 __global__ void __launch_bounds__(NT)
     k_gwn(const float *__restrict__ src, int64_t ntiles_total, const float4 *__restrict__ q,
           int64_t m, int tiles_per_chunk, float *__restrict__ part, int64_t stride,
           EvalParams ep, int *__restrict__ err)
 {
-    gwn_block<P, NT, GRAD, SCREENED>(src, ntiles_total, q, m, tiles_per_chunk, part, stride, ep,
-                                     err, (int64_t)blockIdx.x, (int)blockIdx.y);
+    gwn_block<P, NT, GRAD, SCREENED, CLAMP>(src, ntiles_total, q, m, tiles_per_chunk, part,
+                                            stride, ep, err, (int64_t)blockIdx.x,
+                                            (int)blockIdx.y);
 }
 
 // Many clouds in one launch: CTA b runs work item items[b] of its cloud;
@@ -335,6 +347,37 @@ __global__ void k_pack_sources(const float4 *__restrict__ p4, const float4 *__re
     r[2] = make_float4(my, my, mz, mz);
 }
 
+// records of the modified kernel: the 12 floats above and (d2,d2,0,0);
+// padding records get d2 = 1 (with m = 0 they still contribute exactly 0)
+__global__ void k_pack_sources16(const float4 *__restrict__ p4, const float4 *__restrict__ nrm,
+                                 const float *__restrict__ delta2, int64_t n, int64_t npad,
+                                 float *__restrict__ src)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    float x = 0.f, y = 0.f, z = 0.f, mx = 0.f, my = 0.f, mz = 0.f, d2 = 1.f;
+    if (i < n) {
+        float4 p = p4[i];
+        float4 v = nrm[i];
+        float c = p.w * (float)(1.0 / (4.0 * kPi));
+        x = p.x; y = p.y; z = p.z;
+        mx = c * v.x; my = c * v.y; mz = c * v.z;
+        d2 = delta2[i];
+    }
+    float4 *r = reinterpret_cast<float4 *>(src + i * kSrcFloatsClamp);
+    r[0] = make_float4(x, x, y, y);
+    r[1] = make_float4(z, z, mx, mx);
+    r[2] = make_float4(my, my, mz, mz);
+    r[3] = make_float4(d2, d2, 0.f, 0.f);
+}
+
+cudaError_t launch_pack_sources16(const Ctx *c)
+{
+    k_pack_sources16<<<(unsigned)ceil_div(c->npad, 256), 256, 0, c->stream>>>(
+        c->d_p4, c->d_nrm, c->d_delta2, c->n, c->npad, c->d_src16);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_sources(const float4 *p4, const float4 *nrm, int64_t n, int64_t npad,
                                 float *src, cudaStream_t s)
 {
@@ -349,7 +392,7 @@ cudaError_t launch_pack_sources(const float4 *p4, const float4 *nrm, int64_t n, 
 EvalParams make_eval_params(const Ctx *c)
 {
     EvalParams ep;
-    ep.eps2 = c->eps * c->eps;
+    ep.eps2 = c->reg_mode == DWG_REG_CLAMP ? 0.f : c->eps * c->eps;
     bool scr = c->kernel == DWG_KERNEL_SCREENED && c->lambda > 0.f;
     ep.screened = scr ? 1 : 0;
     double s = scr ? sqrt((double)c->lambda) : 0.0;
@@ -418,6 +461,11 @@ static const GwnVariant kVarW[] = {
     DWG_GWN_VARIANT(4, 256, false), DWG_GWN_VARIANT(1, 128, false), DWG_GWN_VARIANT(1, 256, false),
     DWG_GWN_VARIANT(2, 64, false)};
 #undef DWG_GWN_VARIANT
+// the modified kernel runs in the default shapes only
+static const GwnVariant kVarClampGrad = {2, 128, {k_gwn<2, 128, true, false, true>,
+                                                  k_gwn<2, 128, true, true, true>}};
+static const GwnVariant kVarClampW = {4, 128, {k_gwn<4, 128, false, false, true>,
+                                               k_gwn<4, 128, false, true, true>}};
 constexpr int kNumVarGrad = (int)(sizeof(kVarGrad) / sizeof(kVarGrad[0]));
 constexpr int kNumVarW = (int)(sizeof(kVarW) / sizeof(kVarW[0]));
 
@@ -436,15 +484,22 @@ static const GwnVariant &variant(bool grad, int v)
     return kVarW[(v >= 0 && v < kNumVarW) ? v : 0];
 }
 
-// resident CTAs of a variant on the whole device (cached per device)
-static int variant_slots(bool grad, int v, bool scr, int dev)
+// variant v of the context's kernel (the modified kernel has one shape)
+static const GwnVariant &variant_of(const Ctx *c, bool grad, int v)
+{
+    if (c->reg_mode == DWG_REG_CLAMP) return grad ? kVarClampGrad : kVarClampW;
+    return variant(grad, v);
+}
+
+// resident CTAs of a variant on the whole device (cached per device; the
+// modified kernel's shape in slot 15)
+static int variant_slots(const GwnVariant &V, bool grad, int v, bool scr, int dev)
 {
     static int cached[2][2][16][64] = {};
     if (dev < 0 || dev >= 64) dev = 0;
     if (v < 0 || v >= 16) v = 0;
     int &slot = cached[grad][scr][v][dev];
     if (!slot) {
-        const GwnVariant &V = variant(grad, v);
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.k[scr ? 1 : 0], V.nt, 0) !=
                 cudaSuccess ||
@@ -461,10 +516,11 @@ static bool screened_of(const Ctx *c) { return c->kernel == DWG_KERNEL_SCREENED 
 
 int eval_chunks_variant(const Ctx *c, int64_t m, bool grad, int v)
 {
-    const GwnVariant &V = variant(grad, v);
+    const GwnVariant &V = variant_of(c, grad, v);
+    const int slot_id = c->reg_mode == DWG_REG_CLAMP ? 15 : v;
     int64_t QB = (int64_t)V.nt * 2 * V.p;
     return pick_chunks(ceil_div(m, QB), c->npad / kSrcTile,
-                       variant_slots(grad, v, screened_of(c), c->device));
+                       variant_slots(V, grad, slot_id, screened_of(c), c->device));
 }
 
 int eval_chunks(const Ctx *c, int64_t m, bool grad)
@@ -475,15 +531,16 @@ int eval_chunks(const Ctx *c, int64_t m, bool grad)
 int eval_launch_variant(Ctx *c, const float4 *q, int64_t m, bool grad, int v, int nchunks,
                         float *part, int64_t stride)
 {
-    const GwnVariant &V = variant(grad, v);
+    const GwnVariant &V = variant_of(c, grad, v);
     EvalParams ep = make_eval_params(c);
     int64_t QB = (int64_t)V.nt * 2 * V.p;
     int64_t qtiles = ceil_div(m, QB);
     int64_t ntiles = c->npad / kSrcTile;
     int tpc = (int)ceil_div(ntiles, nchunks);
     dim3 grid((unsigned)qtiles, (unsigned)nchunks);
-    V.k[ep.screened ? 1 : 0]<<<grid, V.nt, 0, c->stream>>>(c->d_src, ntiles, q, m, tpc, part,
-                                                             stride, ep, c->d_err);
+    const float *src = c->reg_mode == DWG_REG_CLAMP ? c->d_src16 : c->d_src;
+    V.k[ep.screened ? 1 : 0]<<<grid, V.nt, 0, c->stream>>>(src, ntiles, q, m, tpc, part, stride,
+                                                             ep, c->d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         c->err = std::string("gwn kernel launch: ") + cudaGetErrorString(e);
@@ -514,9 +571,10 @@ struct CubeQ {
 template <bool GRAD>
 __global__ void k_reduce_points(const float *__restrict__ part, int nchunks, int64_t m,
                                 int64_t stride, const float4 *__restrict__ q,
-                                const float *__restrict__ src, const uint64_t *__restrict__ codes,
-                                int64_t nsrc, int self_mode, CubeQ cq, EvalParams ep,
-                                float4 *__restrict__ out, double *__restrict__ wsum_blocks)
+                                const float *__restrict__ src, int rec_floats,
+                                const uint64_t *__restrict__ codes, int64_t nsrc, int self_mode,
+                                CubeQ cq, EvalParams ep, float4 *__restrict__ out,
+                                double *__restrict__ wsum_blocks)
 {
     constexpr int NA = GRAD ? 4 : 1;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -566,8 +624,19 @@ __global__ void k_reduce_points(const float *__restrict__ part, int nchunks, int
                 while (hi_j < nsrc && codes[hi_j] == ci) ++hi_j;
             }
             for (int64_t j = lo_j; j < hi_j; ++j) {
-                const float *r = src + j * kSrcFloats;
+                const float *r = src + j * rec_floats;
                 if (r[0] == qi.x && r[2] == qi.y && r[4] == qi.z) {
+                    if (rec_floats == kSrcFloatsClamp) {
+                        // modified kernel: this source's rho is its own delta_j
+                        const float d2 = r[12];
+                        const float dinv = rsqrt_mufu(d2);
+                        fi3 = dinv * dinv * dinv;
+                        if (ep.screened) {
+                            float rho = d2 * dinv;
+                            float e = ex2_mufu(rho * ep.nl2e_s);
+                            fi3 *= fmaf(e, rho * ep.s, e);
+                        }
+                    }
                     two_sum1(h[1], l[1], r[6] * fi3);
                     two_sum1(h[2], l[2], r[8] * fi3);
                     two_sum1(h[3], l[3], r[10] * fi3);
@@ -627,14 +696,17 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
     cq.inv_h21 = (double)(1 << kMortonBits) / c->cube_L;
     EvalParams ep = make_eval_params(c);
     unsigned blocks = (unsigned)ceil_div(m, 256);
+    const bool clamp = c->reg_mode == DWG_REG_CLAMP;
+    const float *src = clamp ? c->d_src16 : c->d_src;
+    const int recf = clamp ? kSrcFloatsClamp : kSrcFloats;
     if (grad)
-        k_reduce_points<true><<<blocks, 256, 0, c->stream>>>(part, nchunks, m, m, queries,
-                                                             c->d_src, c->d_codes, c->n, self_mode,
+        k_reduce_points<true><<<blocks, 256, 0, c->stream>>>(part, nchunks, m, m, queries, src,
+                                                             recf, c->d_codes, c->n, self_mode,
                                                              cq, ep, out, wsum_blocks);
     else
-        k_reduce_points<false><<<blocks, 256, 0, c->stream>>>(part, nchunks, m, m, queries,
-                                                              c->d_src, c->d_codes, c->n, 0, cq,
-                                                              ep, out, wsum_blocks);
+        k_reduce_points<false><<<blocks, 256, 0, c->stream>>>(part, nchunks, m, m, queries, src,
+                                                              recf, c->d_codes, c->n, 0, cq, ep,
+                                                              out, wsum_blocks);
     return cudaGetLastError();
 }
 
@@ -644,7 +716,7 @@ cudaError_t launch_reduce_points(Ctx *c, const float *part, int nchunks, int64_t
 int gwn_w_chunks_raw(int64_t m, int64_t npad, int device)
 {
     return pick_chunks(ceil_div(m, kEvalThreads * 2 * kPW), npad / kSrcTile,
-                       variant_slots(false, 0, false, device));
+                       variant_slots(kVarW[0], false, 0, false, device));
 }
 
 cudaError_t launch_gwn_w_raw(const float *src, int64_t npad, const float4 *q, int64_t m,

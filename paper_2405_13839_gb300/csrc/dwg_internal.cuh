@@ -20,6 +20,7 @@ constexpr int kMortonBits = 21;          // bits per axis of the point codes
 constexpr int kMaxDepth = 14;            // octree depth cap
 constexpr int kMaxK = 32;                // kNN cap
 constexpr int kSrcFloats = 12;           // duplicated source record (x,x,y,y,z,z,mx,mx,...)
+constexpr int kSrcFloatsClamp = 16;      // the same + (d2,d2,0,0), d2 = delta^2 (modified kernel)
 constexpr int kSrcTile = 128;            // sources per shared-memory tile
 constexpr int kBucket = 16;              // points per kNN bucket
 constexpr int kSelBins = 4096;           // radix-select bins (level 1 and 2)
@@ -29,6 +30,7 @@ constexpr int kErrTimeout = 1;
 constexpr int kErrNonfinite = 2;
 constexpr int kErrOverflow = 4;
 constexpr int kErrStack = 8;
+constexpr int kErrGeometry = 16;  // a Voronoi cell outgrew its vertex buffer
 
 // ---------------------------------------------------------------------------
 // iteration state on the device (one struct, updated by kernels)
@@ -127,10 +129,15 @@ struct Ctx {
     // geometry (sorted along the Morton curve)
     double cube_lo[3] = {0, 0, 0};
     double cube_L = 1.0;
+    double bbox_c[3] = {0, 0, 0};  // bounding-box centre (Gauss-map initialisation)
     float4 *d_p4 = nullptr;        // (x, y, z, a) sorted
     int64_t *d_perm = nullptr;     // sorted index -> input index
     uint64_t *d_codes = nullptr;   // 63-bit Morton codes, sorted
     float *d_src = nullptr;        // npad x kSrcFloats source records
+    // modified Poisson kernel (Sec. 5.2): rho = max(|p_j - q|, delta_j)
+    int reg_mode = 0;              // DWG_REG_SOFTEN or DWG_REG_CLAMP
+    float *d_delta2 = nullptr;     // n: delta_j^2, sorted order
+    float *d_src16 = nullptr;      // npad x kSrcFloatsClamp records (DWG_REG_CLAMP)
     float4 *d_nrm = nullptr;       // current normals, sorted
     float4 *d_nrm_init = nullptr;  // given initial normals, sorted
     float *d_dtheta = nullptr;
@@ -344,6 +351,17 @@ int select_blocks(int64_t n);
 cudaError_t launch_random_normals(float4 *nrm, const int64_t *perm, int64_t n, uint64_t seed,
                                   cudaStream_t s);
 cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t *idx_out);
+// PCA (kPcaK nearest points) and Gauss-map initial normals over d_nrm
+constexpr int kPcaK = 10;
+cudaError_t launch_init_pca(Ctx *c);
+cudaError_t launch_init_gauss(Ctx *c);
+// local-Voronoi area weights of the m nearest points into p4.w (scratch: n + 1
+// doubles; a_out: n floats in input order, device, or null)
+cudaError_t launch_voronoi_weights(Ctx *c, int m, double *scratch, float *a_out);
+// clamp radii of the modified kernel into d_delta2 (k in [1, 31]); delta_out:
+// n floats in input order (device) or null
+cudaError_t launch_clamp_delta(Ctx *c, int k, double vmin, double vmax, float *delta_out);
+cudaError_t launch_pack_sources16(const Ctx *c);
 // distance to the 10th nearest other point for m points sampled evenly
 cudaError_t launch_spacing(Ctx *c, int64_t m, float *d_out);
 cudaError_t launch_features(Ctx *c, float *X, bool by_input, double *cR);

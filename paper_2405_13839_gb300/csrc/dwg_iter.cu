@@ -11,8 +11,8 @@
 //                  not depend on the order of the atomic additions;
 //   k_normal_update  n_i <- -sum / |sum| (a point no face chose keeps its
 //                  normal), the per-point change in degrees, next sources;
-//   k_select       convergence statistic of Sec. 5.1: mean of the
-//                  ceil(n / 100) largest changes, by exact three-level radix
+//   k_sel_*        convergence statistic of Sec. 5.1: mean of the
+//                  ceil(n / 100) largest changes, by an exact multi-CTA radix
 //                  select on the float bits, then the loop condition.
 #include <algorithm>
 
@@ -473,14 +473,381 @@ cudaError_t launch_normals_from_y(Ctx *c, const float *Y)
 }
 
 // ---------------------------------------------------------------------------
+// PCA and Gauss-map initial normals (Sec. 5.1, "Normal Initialization")
+// ---------------------------------------------------------------------------
+// Unit eigenvector of the smallest eigenvalue of the symmetric 3 x 3 matrix a
+// (destroyed), by cyclic Jacobi rotations: each rotation is the symmetric
+// 2 x 2 Schur decomposition of Golub and Van Loan (Matrix Computations,
+// Sec. 8.5) applied to the (p, q) plane.  False for the zero matrix or a
+// non-finite result.
+__device__ bool sym3_min_eigvec(double a[3][3], double out[3])
+{
+    double fro = 0.0;
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) fro += a[r][k] * a[r][k];
+    if (!(fro > 0.0) || !isfinite(fro)) return false;
+    double v[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        if (off <= 1e-36 * fro) break;  // off-diagonal below double rounding of the entries
+        for (int r = 0; r < 3; ++r) {
+            const int p = r == 2 ? 1 : 0, q = r == 0 ? 1 : 2;  // (0,1), (0,2), (1,2)
+            if (a[p][q] == 0.0) continue;
+            const double tau = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+            // A <- J^T A J and V <- V J, J the identity but for J_pp = J_qq = c,
+            // J_pq = s, J_qp = -s
+            for (int k = 0; k < 3; ++k) {
+                const double x = a[k][p], y = a[k][q];
+                a[k][p] = c * x - s * y;
+                a[k][q] = s * x + c * y;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double x = a[p][k], y = a[q][k];
+                a[p][k] = c * x - s * y;
+                a[q][k] = s * x + c * y;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double x = v[k][p], y = v[k][q];
+                v[k][p] = c * x - s * y;
+                v[k][q] = s * x + c * y;
+            }
+        }
+    }
+    int m = 0;
+    if (a[1][1] < a[m][m]) m = 1;
+    if (a[2][2] < a[m][m]) m = 2;
+    const double l = sqrt(v[0][m] * v[0][m] + v[1][m] * v[1][m] + v[2][m] * v[2][m]);
+    if (!(l > 0.0) || !isfinite(l)) return false;
+    for (int k = 0; k < 3; ++k) out[k] = v[k][m] / l;
+    return true;
+}
+
+// PCA normal of sorted point i: the smallest-eigenvalue eigenvector of the
+// covariance of its kPcaK nearest points (itself included), in FP64 on the
+// offsets from p_i.  PCA fixes the line only; the direction is the one away
+// from the bounding-box centre c (the Gauss-map side, n . (p_i - c) > 0),
+// and +z, then +y, then +x where that dot product is zero.  Where the
+// covariance is zero the random normal already in nrm stays.
+__global__ void __launch_bounds__(128)
+    k_init_pca(KnnTree T, double cx, double cy, double cz, float4 *__restrict__ nrm, int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T.n) return;
+    const float4 pi = T.p4[i];
+    int bj[kPcaK];
+    knn_search<kPcaK, true>(T, F3{pi.x, pi.y, pi.z}, kPcaK, bj, err);
+    double d[kPcaK][3], mean[3] = {0.0, 0.0, 0.0};
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < kPcaK; ++t) {
+        if (bj[t] < 0) continue;
+        const float4 pj = T.p4[bj[t]];
+        d[cnt][0] = (double)pj.x - (double)pi.x;
+        d[cnt][1] = (double)pj.y - (double)pi.y;
+        d[cnt][2] = (double)pj.z - (double)pi.z;
+        for (int k = 0; k < 3; ++k) mean[k] += d[cnt][k];
+        ++cnt;
+    }
+    if (cnt < 1) return;
+    for (int k = 0; k < 3; ++k) mean[k] /= cnt;
+    double C[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int t = 0; t < cnt; ++t) {
+        const double e0 = d[t][0] - mean[0], e1 = d[t][1] - mean[1], e2 = d[t][2] - mean[2];
+        C[0][0] += e0 * e0; C[0][1] += e0 * e1; C[0][2] += e0 * e2;
+        C[1][1] += e1 * e1; C[1][2] += e1 * e2; C[2][2] += e2 * e2;
+    }
+    C[1][0] = C[0][1]; C[2][0] = C[0][2]; C[2][1] = C[1][2];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) C[r][k] /= cnt;
+    double e[3];
+    if (!sym3_min_eigvec(C, e)) return;
+    const double side = e[0] * ((double)pi.x - cx) + e[1] * ((double)pi.y - cy) +
+                        e[2] * ((double)pi.z - cz);
+    const bool flip = side != 0.0
+                          ? side < 0.0
+                          : (e[2] < 0.0 || (e[2] == 0.0 && (e[1] < 0.0 || (e[1] == 0.0 && e[0] < 0.0))));
+    const double sg = flip ? -1.0 : 1.0;
+    nrm[i] = make_float4((float)(sg * e[0]), (float)(sg * e[1]), (float)(sg * e[2]), 0.f);
+}
+
+// Gauss-map normal: the direction from the bounding-box centre c to p_i, in
+// FP64; a point at c keeps its random normal.
+__global__ void k_init_gauss(const float4 *__restrict__ p4, int64_t n, double cx, double cy,
+                             double cz, float4 *__restrict__ nrm)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 p = p4[i];
+    const double dx = (double)p.x - cx, dy = (double)p.y - cy, dz = (double)p.z - cz;
+    const double l = sqrt(dx * dx + dy * dy + dz * dz);
+    if (l > 0.0) nrm[i] = make_float4((float)(dx / l), (float)(dy / l), (float)(dz / l), 0.f);
+}
+
+cudaError_t launch_init_pca(Ctx *c)
+{
+    k_init_pca<<<(unsigned)ceil_div(c->n, 128), 128, 0, c->stream>>>(
+        knn_tree(c), c->bbox_c[0], c->bbox_c[1], c->bbox_c[2], c->d_nrm, c->d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_gauss(Ctx *c)
+{
+    k_init_gauss<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->stream>>>(
+        c->d_p4, c->n, c->bbox_c[0], c->bbox_c[1], c->bbox_c[2], c->d_nrm);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// local-Voronoi area weights (Sec. 5.1, "Computing Area Weights")
+// ---------------------------------------------------------------------------
+// A convex polygon of k vertices (counter-clockwise) clipped by the
+// half-plane ax x + ay y <= b; at most cap output vertices (a convex polygon
+// gains at most one per clip; *over is set if rounding asked for more).
+__device__ int vor_clip(const double *px, const double *py, int k, double ax, double ay, double b,
+                        double *ox, double *oy, int cap, bool *over)
+{
+    int o = 0;
+    for (int t = 0; t < k; ++t) {
+        const int u = t + 1 == k ? 0 : t + 1;
+        const double fp = ax * px[t] + ay * py[t] - b, fq = ax * px[u] + ay * py[u] - b;
+        if (fp <= 0.0) {
+            if (o < cap) { ox[o] = px[t]; oy[o] = py[t]; ++o; } else *over = true;
+        }
+        if ((fp < 0.0 && fq > 0.0) || (fq < 0.0 && fp > 0.0)) {
+            const double s = fp / (fp - fq);
+            if (o < cap) {
+                ox[o] = px[t] + s * (px[u] - px[t]);
+                oy[o] = py[t] + s * (py[u] - py[t]);
+                ++o;
+            } else {
+                *over = true;
+            }
+        }
+    }
+    return o;
+}
+
+// Area of a convex polygon containing the origin intersected with the disk of
+// radius R about the origin: each edge (A, B) spans the triangle (0, A, B);
+// the part of the edge inside the circle adds its triangle, the parts outside
+// add circular sectors R^2 * angle / 2.
+__device__ double vor_disk_area(const double *px, const double *py, int k, double R)
+{
+    double total = 0.0;
+    const double R2 = R * R;
+    for (int t = 0; t < k; ++t) {
+        const int u = t + 1 == k ? 0 : t + 1;
+        const double ax = px[t], ay = py[t], dx = px[u] - ax, dy = py[u] - ay;
+        const double a = dx * dx + dy * dy, b = ax * dx + ay * dy, c = ax * ax + ay * ay - R2;
+        if (a == 0.0) continue;
+        const double disc = b * b - a * c;
+        double s1 = 0.0, s2 = 0.0;
+        if (disc > 0.0) {
+            const double r = sqrt(disc);
+            s1 = fmin(fmax((-b - r) / a, 0.0), 1.0);
+            s2 = fmin(fmax((-b + r) / a, 0.0), 1.0);
+        }
+        const double x1 = ax + s1 * dx, y1 = ay + s1 * dy, x2 = ax + s2 * dx, y2 = ay + s2 * dy;
+        const double bx = px[u], by = py[u];
+        // no crossing: s1 = s2 = 0, one sector from A to B
+        total += 0.5 * R2 * atan2(ax * y1 - ay * x1, ax * x1 + ay * y1);
+        total += 0.5 * (x1 * y2 - y1 * x2);
+        total += 0.5 * R2 * atan2(x2 * by - y2 * bx, x2 * bx + y2 * by);
+    }
+    return total;
+}
+
+// Cell area of sorted point i: its m nearest other points, the PCA tangent
+// plane through it, the projected neighbours as Voronoi seeds, the cell of
+// the origin cut to the disk of half the largest projected distance.  A
+// neighbourhood with no extent gives 0 (the caller substitutes the mean).
+template <int KMAX, bool FIXED>
+__global__ void __launch_bounds__(128)
+    k_voronoi_area(KnnTree T, int m, double *__restrict__ area, int *err)
+{
+    constexpr int CAP = KMAX + 4;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T.n) return;
+    const float4 pi = T.p4[i];
+    int bj[KMAX];
+    knn_search<KMAX, FIXED>(T, F3{pi.x, pi.y, pi.z}, m + 1, bj, err);
+    double d[KMAX][3];
+    double mean[3] = {0.0, 0.0, 0.0};
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) {
+        const int j = bj[t];
+        if (t > m || j < 0 || j == (int)i || cnt == m) continue;
+        const float4 pj = T.p4[j];
+        d[cnt][0] = (double)pj.x - (double)pi.x;
+        d[cnt][1] = (double)pj.y - (double)pi.y;
+        d[cnt][2] = (double)pj.z - (double)pi.z;
+        for (int k = 0; k < 3; ++k) mean[k] += d[cnt][k];
+        ++cnt;
+    }
+    area[i] = 0.0;
+    if (cnt < 1) return;
+    for (int k = 0; k < 3; ++k) mean[k] /= (cnt + 1);  // p_i itself is the zero offset
+    double C[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) C[r][k] = mean[r] * mean[k];  // the zero offset's term
+    for (int t = 0; t < cnt; ++t)
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) C[r][k] += (d[t][r] - mean[r]) * (d[t][k] - mean[k]);
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) C[r][k] /= (cnt + 1);
+    double nv[3];
+    if (!sym3_min_eigvec(C, nv)) return;
+    // tangent basis: e1 = normalise(n x axis least aligned with n), e2 = n x e1
+    int ax = 0;
+    if (fabs(nv[1]) < fabs(nv[ax])) ax = 1;
+    if (fabs(nv[2]) < fabs(nv[ax])) ax = 2;
+    double e1[3] = {ax == 2 ? nv[1] : (ax == 1 ? -nv[2] : 0.0),
+                    ax == 0 ? nv[2] : (ax == 2 ? -nv[0] : 0.0),
+                    ax == 1 ? nv[0] : (ax == 0 ? -nv[1] : 0.0)};
+    const double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int k = 0; k < 3; ++k) e1[k] /= l1;
+    const double e2[3] = {nv[1] * e1[2] - nv[2] * e1[1], nv[2] * e1[0] - nv[0] * e1[2],
+                          nv[0] * e1[1] - nv[1] * e1[0]};
+    double qx[KMAX], qy[KMAX], R = 0.0;
+    for (int t = 0; t < cnt; ++t) {
+        qx[t] = d[t][0] * e1[0] + d[t][1] * e1[1] + d[t][2] * e1[2];
+        qy[t] = d[t][0] * e2[0] + d[t][1] * e2[1] + d[t][2] * e2[2];
+        R = fmax(R, sqrt(qx[t] * qx[t] + qy[t] * qy[t]));
+    }
+    R *= 0.5;
+    if (!(R > 0.0)) return;
+    double ax0[CAP], ay0[CAP], ax1[CAP], ay1[CAP];
+    ax0[0] = -R; ay0[0] = -R; ax0[1] = R; ay0[1] = -R;
+    ax0[2] = R;  ay0[2] = R;  ax0[3] = -R; ay0[3] = R;
+    int k = 4;
+    bool over = false;
+    for (int t = 0; t < cnt && k >= 3; ++t) {
+        const double r2 = qx[t] * qx[t] + qy[t] * qy[t];
+        if (!(r2 > 0.0)) continue;  // a seed on the origin imposes nothing
+        k = vor_clip(ax0, ay0, k, qx[t], qy[t], 0.5 * r2, ax1, ay1, CAP, &over);
+        for (int v = 0; v < k; ++v) {
+            ax0[v] = ax1[v];
+            ay0[v] = ay1[v];
+        }
+    }
+    if (over) atomicOr(err, kErrGeometry);
+    if (k >= 3) area[i] = vor_disk_area(ax0, ay0, k, R);
+}
+
+// mean of the positive areas (one block, fixed order)
+__global__ void k_area_mean(const double *__restrict__ area, int64_t n, double *out)
+{
+    __shared__ double ss[256];
+    __shared__ double sc[256];
+    double s = 0.0, c = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        if (area[i] > 0.0) { s += area[i]; c += 1.0; }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sc[0] > 0.0 ? ss[0] / sc[0] : 0.0;
+}
+
+// install a_i (zero areas take the mean) into p4.w; optionally write them in
+// input order
+__global__ void k_area_install(const double *__restrict__ area, const double *__restrict__ mean,
+                               const int64_t *__restrict__ perm, int64_t n, float4 *p4,
+                               float *a_out, int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = area[i] > 0.0 ? area[i] : mean[0];
+    const float f = (float)a;
+    if (!(f > 0.f) || !isfinite(f)) atomicOr(err, kErrNonfinite);
+    p4[i].w = f;
+    if (a_out) a_out[perm[i]] = f;
+}
+
+cudaError_t launch_voronoi_weights(Ctx *c, int m, double *scratch /* n + 1 */, float *a_out)
+{
+    const unsigned g = (unsigned)ceil_div(c->n, 128);
+    if (m == 15)
+        k_voronoi_area<16, true><<<g, 128, 0, c->stream>>>(knn_tree(c), m, scratch, c->d_err);
+    else
+        k_voronoi_area<32, false><<<g, 128, 0, c->stream>>>(knn_tree(c), m, scratch, c->d_err);
+    k_area_mean<<<1, 256, 0, c->stream>>>(scratch, c->n, scratch + c->n);
+    k_area_install<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->stream>>>(
+        scratch, scratch + c->n, c->d_perm, c->n, c->d_p4, a_out, c->d_err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// clamp radii of the modified Poisson kernel (Sec. 5.2, "Poisson Kernels")
+// ---------------------------------------------------------------------------
+// delta_i = mean distance (FP64) from p_i to those of its k nearest other
+// points whose distance lies in [vmin, vmax]; if none does, the mean of all
+// k distances clamped to [vmin, vmax].  Stored as delta^2 in float32 (sorted
+// order) and, when asked, delta in input order.
+template <int KMAX, bool FIXED>
+__global__ void __launch_bounds__(128)
+    k_clamp_delta(KnnTree T, int k, double vmin, double vmax, float *__restrict__ delta2,
+                  float *__restrict__ delta_out, int *err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T.n) return;
+    const float4 pi = T.p4[i];
+    int bj[KMAX];
+    knn_search<KMAX, FIXED>(T, F3{pi.x, pi.y, pi.z}, k + 1, bj, err);
+    double sum_in = 0.0, sum_all = 0.0;
+    int n_in = 0, cnt = 0;
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) {
+        const int j = bj[t];
+        if (t > k || j < 0 || j == (int)i || cnt == k) continue;
+        const float4 pj = T.p4[j];
+        const double dx = (double)pj.x - (double)pi.x, dy = (double)pj.y - (double)pi.y,
+                     dz = (double)pj.z - (double)pi.z;
+        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        sum_all += d;
+        ++cnt;
+        if (d >= vmin && d <= vmax) {
+            sum_in += d;
+            ++n_in;
+        }
+    }
+    double delta = vmin;
+    if (n_in > 0) delta = sum_in / n_in;
+    else if (cnt > 0) delta = fmin(fmax(sum_all / cnt, vmin), vmax);
+    delta2[i] = (float)(delta * delta);
+    if (delta_out) delta_out[T.perm[i]] = (float)delta;
+}
+
+cudaError_t launch_clamp_delta(Ctx *c, int k, double vmin, double vmax, float *delta_out)
+{
+    const unsigned g = (unsigned)ceil_div(c->n, 128);
+    if (k == 10)
+        k_clamp_delta<11, true><<<g, 128, 0, c->stream>>>(knn_tree(c), k, vmin, vmax, c->d_delta2,
+                                                           delta_out, c->d_err);
+    else
+        k_clamp_delta<32, false><<<g, 128, 0, c->stream>>>(knn_tree(c), k, vmin, vmax,
+                                                            c->d_delta2, delta_out, c->d_err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // normal update (Eq. 7) and per-point change
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
     k_normal_update(int mode, int64_t n, unsigned long long *__restrict__ acc, double inv_scale,
                     const float4 *__restrict__ wg, const float4 *__restrict__ p4,
                     float4 *__restrict__ nrm, float *__restrict__ src,
-                    float *__restrict__ dtheta, double *__restrict__ dn_blocks,
-                    const IterState *st)
+                    float *__restrict__ src16, float *__restrict__ dtheta,
+                    double *__restrict__ dn_blocks, const IterState *st)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch: normals stay
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -521,6 +888,11 @@ __global__ void __launch_bounds__(256)
         float mx = c * nx, my = c * ny, mz = c * nz;
         r[1] = make_float4(r[1].x, r[1].y, mx, mx);
         r[2] = make_float4(my, my, mz, mz);
+        if (src16) {  // the modified kernel's records (same first 12 floats)
+            float4 *r16 = reinterpret_cast<float4 *>(src16 + i * kSrcFloatsClamp);
+            r16[1] = make_float4(r16[1].x, r16[1].y, mx, mx);
+            r16[2] = make_float4(my, my, mz, mz);
+        }
     }
     __shared__ double sh[256];
     sh[threadIdx.x] = dn;
@@ -812,7 +1184,8 @@ cudaError_t launch_normal_update(Ctx *c)
 {
     k_normal_update<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->stream>>>(
         c->mode, c->n, c->d_acc, 1.0 / c->acc_scale, c->d_wg, c->d_p4, c->d_nrm, c->d_src,
-        c->d_dtheta, c->d_dn_blocks, c->d_state);
+        c->reg_mode == DWG_REG_CLAMP ? c->d_src16 : nullptr, c->d_dtheta, c->d_dn_blocks,
+        c->d_state);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,23 @@ __device__ __forceinline__ f2 ex22(f2 v)
     upk(v, a, b);
     return pk(ex2_mufu(a), ex2_mufu(b));
 }
+// lane-wise max (the clamp of the modified kernel: rho^2 = max(r^2, delta^2))
+__device__ __forceinline__ f2 max2(f2 a, f2 b)
+{
+    float a0, a1, b0, b1;
+    upk(a, a0, a1);
+    upk(b, b0, b1);
+    return pk(fmaxf(a0, b0), fmaxf(a1, b1));
+}
+// lane-wise: v where x >= t, else 0
+__device__ __forceinline__ f2 keep_ge(f2 v, f2 x, f2 t)
+{
+    float v0, v1, x0, x1, t0, t1;
+    upk(v, v0, v1);
+    upk(x, x0, x1);
+    upk(t, t0, t1);
+    return pk(x0 >= t0 ? v0 : 0.f, x1 >= t1 ? v1 : 0.f);
+}
 // (hi, lo) += t with Knuth's two-sum, both lanes at once
 __device__ __forceinline__ void two_sum_acc(f2 &hi, f2 &lo, f2 t)
 {

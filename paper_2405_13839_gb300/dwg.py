@@ -31,6 +31,10 @@ DWG_UPDATE_DIRECT = 1
 DWG_INIT_RANDOM = 0
 DWG_INIT_GIVEN = 1
 DWG_INIT_LEARNED = 2
+DWG_INIT_PCA = 3
+DWG_INIT_GAUSS = 4
+DWG_REG_SOFTEN = 0
+DWG_REG_CLAMP = 1
 MLP_PARAMS = 12675
 DWG_CONV_TOP1 = 0
 DWG_CONV_MEAN = 1
@@ -99,6 +103,8 @@ def _load() -> ctypes.CDLL:
         "dwg_set_update": ([H, I, I, I], I),
         "dwg_set_convergence": ([H, I], I),
         "dwg_set_weights": ([H, P], I),
+        "dwg_voronoi_weights": ([H, I, P], I),
+        "dwg_set_regularization": ([H, I, I, F, F, P], I),
         "dwg_set_tree": ([H, I, F], I),
         "dwg_create_batch": ([P, P, I, ctypes.POINTER(H)], I),
         "dwg_orient_batch": ([H, P, P], I),
@@ -243,9 +249,29 @@ def dwg_set_weights(h, a):
     return _raise(h, _lib.dwg_set_weights(h, _ptr(a)))
 
 
+def dwg_set_regularization(h, mode, k=10, vmin=0.0, vmax=0.0, delta_out=None):
+    """DWG_REG_SOFTEN, or DWG_REG_CLAMP (the modified kernel of Sec. 5.2 with
+    radii from the k nearest points filtered to [vmin, vmax]; 0, 0 = the
+    paper's values times the largest bounding-box extent).  delta_out
+    (float32 (n,), host or device) receives the radii."""
+    if delta_out is not None:
+        _check_f32(delta_out, None, "delta_out")
+    return _raise(h, _lib.dwg_set_regularization(h, int(mode), int(k), float(vmin), float(vmax),
+                                                 _ptr(delta_out)))
+
+
+def dwg_voronoi_weights(h, m=15, a_out=None):
+    """Local-Voronoi area weights of the m nearest points, installed as the
+    handle's a_i; a_out (float32 (n,), host or device) receives them."""
+    if a_out is not None:
+        _check_f32(a_out, None, "a_out")
+    return _raise(h, _lib.dwg_voronoi_weights(h, int(m), _ptr(a_out)))
+
+
 def dwg_set_init(h, mode, seed=1, normals=None):
     """normals: (n, 3) initial normals for DWG_INIT_GIVEN, or the flat float32
-    network parameters (12,675) for DWG_INIT_LEARNED."""
+    network parameters (12,675) for DWG_INIT_LEARNED; None for DWG_INIT_RANDOM,
+    DWG_INIT_PCA and DWG_INIT_GAUSS (seed: their random fallback)."""
     if normals is not None:
         _check_f32(normals, 3 if mode == DWG_INIT_GIVEN else None, "normals")
     return _raise(h, _lib.dwg_set_init(h, int(mode), int(seed) & 0xFFFFFFFFFFFFFFFF,

@@ -41,3 +41,12 @@ def test_create_without_gpu_fails_loudly(dwglib):
     with pytest.raises(dwglib.DWGError) as e:
         dwglib.dwg_create(np.zeros((4, 3), np.float32))
     assert e.value.code == dwglib.DWG_ERR_CUDA
+
+
+def test_binding_constants_match_the_header(dwglib):
+    hdr = open(os.path.join(ROOT, "include", "dwg.h")).read()
+    consts = dict(re.findall(r"^#define (DWG_[A-Z0-9_]+) (-?\d+)\s*$", hdr, flags=re.M))
+    assert "DWG_INIT_PCA" in consts and "DWG_CONV_MEAN" in consts
+    for name, value in consts.items():
+        if hasattr(dwglib, name):
+            assert getattr(dwglib, name) == int(value), name

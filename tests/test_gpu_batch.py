@@ -19,14 +19,15 @@ def _clouds():
     return np.ascontiguousarray(np.vstack(pts)), np.array(offs, np.int64)
 
 
-@pytest.mark.parametrize("path", [1, 2])
-def test_batch_equals_singles(dwglib, path):
+@pytest.mark.parametrize("path,init", [(1, 0), (2, 0), (1, 3), (2, 4)])
+def test_batch_equals_singles(dwglib, path, init):
+    """init: DWG_INIT_RANDOM (0), DWG_INIT_PCA (3), DWG_INIT_GAUSS (4)."""
     P, off = _clouds()
     nc = len(off) - 1
     hb = dwglib.dwg_create_batch(P, off)
     try:
         dwglib.dwg_set_tree(hb, path, 0.5)
-        dwglib.dwg_set_init(hb, dwglib.DWG_INIT_RANDOM, 11)
+        dwglib.dwg_set_init(hb, init, 11)
         out = np.zeros_like(P)
         rc, iters = dwglib.dwg_orient_batch(hb, out, nc)
         st = dwglib.dwg_get_stats(hb)
@@ -41,7 +42,7 @@ def test_batch_equals_singles(dwglib, path):
             depth = min(10, max(5, int(round(0.5 * np.log2(max(n, 2))))))
             dwglib.dwg_set_update(h, depth, 10, dwglib.DWG_UPDATE_LEVELSET)
             dwglib.dwg_set_tree(h, path, 0.5)
-            dwglib.dwg_set_init(h, dwglib.DWG_INIT_RANDOM, 11 + c)
+            dwglib.dwg_set_init(h, init, 11 + c)
             o = np.zeros_like(p)
             rc1, it1 = dwglib.dwg_orient(h, o)
         finally:
