@@ -396,6 +396,15 @@ int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
  *                    error stays within its per-query bound; the groups'
  *                    interaction lists at the points and the leaf corners
  *                    are built once and evaluated every iteration;
+ *   knn_lists:       1 (default): the faces' k-nearest-point searches (Eq. 7)
+ *                    scan a candidate list per octree leaf cell, built once
+ *                    per discretisation: the points within r_k(c) + 2 h of
+ *                    the cell centre c (h the half-diagonal), which contain
+ *                    the k nearest points of every position in the cell, so
+ *                    the scan returns exactly the tree search's result; cells
+ *                    with more than 128 candidates keep the tree search.
+ *                    0: every face walks the bucket tree.  Not tuned
+ *                    (dwg_autotune keeps the handle's value);
  *   w_err:           largest |w_tree - w_exact| the tuner saw on its sample
  *                    (0 for the exact path);
  *   ms_points, ms_corners: device time of one evaluation at the points and
@@ -442,6 +451,7 @@ typedef struct {
     int tree_leaf;
     float theta;
     int tree_group;
+    int knn_lists;
     double w_err;
     double ms_points, ms_corners;
     int from_cache;

@@ -194,6 +194,7 @@ static int ensure_iter_buffers(Ctx *c)
     if (c->mode == DWG_UPDATE_LEVELSET) {
         if (c->built_depth != c->depth) ++c->bufgen;
         int rc = build_discretization(c, c->depth);
+        if (!rc) rc = build_cell_lists(c);
         if (rc) return rc;
         const int nch_c = tree ? 1 : eval_chunks(c, c->ncorners, false);
         if (nch_c != c->nchunks_c) ++c->bufgen;
@@ -492,7 +493,7 @@ void dwg_destroy(dwg_handle h)
                     h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err,
                     h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
                     h->d_tree_mrec, h->d_tree_frec, h->d_counter, h->d_mlp_params,
-                    h->d_delta2, h->d_src16};
+                    h->d_delta2, h->d_src16, h->d_cell_off, h->d_cell_idx};
     for (void *p : bufs) cudaFree(p);
     free_lists(h->lists_p);
     free_lists(h->lists_c);

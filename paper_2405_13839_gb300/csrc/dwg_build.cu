@@ -492,6 +492,7 @@ __global__ void k_corner_assign(const uint64_t *__restrict__ keys, const int64_t
 
 static void free_disc(Ctx *c)
 {
+    free_cell_lists(c);  // they index the leaves
     cudaFree(c->d_leaves);
     cudaFree(c->d_leaf_corners);
     cudaFree(c->d_corner_keys);

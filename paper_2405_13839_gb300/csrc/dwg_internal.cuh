@@ -152,6 +152,12 @@ struct Ctx {
     int built_depth = -1;
     int64_t nleaves = 0, ncorners = 0, max_faces = 0;
     int4 *d_leaves = nullptr;          // (level, code lo32, code hi32, nonempty) per leaf
+    // per-leaf candidate lists of the faces' kNN (CSR over the leaves; a leaf
+    // with an empty range keeps the tree search)
+    int knn_lists = 1;
+    int64_t *d_cell_off = nullptr;     // nleaves + 1
+    int *d_cell_idx = nullptr;         // sorted point indices
+    int cells_k = 0;                   // k the lists were built for (0: none)
     int *d_leaf_corners = nullptr;     // nleaves x 8 corner indices
     uint64_t *d_corner_keys = nullptr; // Morton keys of corners (sorted)
     float4 *d_corner_pos = nullptr;
@@ -362,6 +368,10 @@ cudaError_t launch_voronoi_weights(Ctx *c, int m, double *scratch, float *a_out)
 // n floats in input order (device) or null
 cudaError_t launch_clamp_delta(Ctx *c, int k, double vmin, double vmax, float *delta_out);
 cudaError_t launch_pack_sources16(const Ctx *c);
+// per-leaf candidate lists for the faces' k nearest points (once per
+// discretisation and k; skipped when they would not fit comfortably)
+int build_cell_lists(Ctx *c);
+void free_cell_lists(Ctx *c);
 // distance to the 10th nearest other point for m points sampled evenly
 cudaError_t launch_spacing(Ctx *c, int64_t m, float *d_out);
 cudaError_t launch_features(Ctx *c, float *X, bool by_input, double *cR);

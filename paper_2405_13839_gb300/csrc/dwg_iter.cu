@@ -110,9 +110,10 @@ __device__ __forceinline__ bool tet_face(const F3 x[4], const float f[4], const 
     return true;
 }
 
-// Faces of the level set.  Each face record also carries, in the centroid's
-// w, the position in the Morton-sorted points of the face's leaf cell (found
-// once per cut leaf): the k-nearest search of its faces starts there.
+// Faces of the level set.  Each face record also carries its leaf's index
+// (in the area's w) and, in the centroid's w, the position in the
+// Morton-sorted points of the face's leaf cell (found once per cut leaf):
+// the k-nearest search of its faces starts there.
 __global__ void __launch_bounds__(256)
     k_mc_faces(const int *__restrict__ leaf_corners, const int4 *__restrict__ leaves, int64_t nl,
                const float4 *__restrict__ cpos, const float *__restrict__ wc,
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256)
             atomicOr(err, kErrOverflow);
             break;
         }
-        faces[2 * o] = make_float4(area[k].x, area[k].y, area[k].z, 0.f);
+        faces[2 * o] = make_float4(area[k].x, area[k].y, area[k].z, __int_as_float((int)l));
         faces[2 * o + 1] = make_float4(cen[k].x, cen[k].y, cen[k].z, __int_as_float(seed));
     }
 }
@@ -309,12 +310,40 @@ __device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *b
     }
 }
 
+// The k nearest of q among a candidate list that is known to contain them:
+// the same keys and insertion as knn_search, so the same result.
+template <int KMAX, bool FIXED>
+__device__ __forceinline__ void knn_scan(const KnnTree &T, F3 q, int k, const int *__restrict__ cand,
+                                         int64_t c0, int64_t c1, int *bj)
+{
+    uint64_t best[KMAX];
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) {
+        best[t] = ~0ull;
+        bj[t] = -1;
+    }
+    const int kk = FIXED ? KMAX : k;
+    float worst = INFINITY;
+    for (int64_t t = c0; t < c1; ++t) {
+        const int j = __ldg(&cand[t]);
+        const float d = pt_d2(__ldg(&T.p4[j]), q);
+        if (d > worst) continue;  // the tie-break index is only needed from here
+        const uint64_t key = knn_key(d, __ldg(&T.perm[j]));
+        if (key < best[kk - 1]) {
+            knn_insert<KMAX, FIXED>(key, j, k, best, bj);
+            if (best[kk - 1] != ~0ull) worst = __uint_as_float((uint32_t)(best[kk - 1] >> 32));
+        }
+    }
+}
+
 static KnnTree knn_tree(const Ctx *c);
 
 template <int KMAX, bool FIXED>
 __global__ void __launch_bounds__(128)
     k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
-                  KnnTree T, int k, double scale, unsigned long long *acc, int *err)
+                  KnnTree T, int k, const int64_t *__restrict__ cell_off,
+                  const int *__restrict__ cell_idx, double scale, unsigned long long *acc,
+                  int *err)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -322,7 +351,16 @@ __global__ void __launch_bounds__(128)
     if (f >= nf) return;
     float4 A = faces[2 * f], C = faces[2 * f + 1];
     int bj[KMAX];
-    knn_search<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, bj, err, (int64_t)__float_as_int(C.w));
+    int64_t c0 = 0, c1 = 0;
+    if (cell_off) {
+        const int leaf = __float_as_int(A.w);
+        c0 = __ldg(&cell_off[leaf]);
+        c1 = __ldg(&cell_off[leaf + 1]);
+    }
+    if (c1 > c0)
+        knn_scan<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, cell_idx, c0, c1, bj);
+    else
+        knn_search<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, bj, err, (int64_t)__float_as_int(C.w));
     long long vx = llrint((double)A.x * scale);
     long long vy = llrint((double)A.y * scale);
     long long vz = llrint((double)A.z * scale);
@@ -1160,13 +1198,187 @@ cudaError_t launch_knn_scatter(Ctx *c)
     // one thread per possible face; threads past the emitted count exit
     unsigned blocks = (unsigned)ceil_div(c->max_faces, 128);
     KnnTree T = knn_tree(c);
+    const bool lists = c->knn_lists && c->cells_k == c->knn && c->d_cell_off;
+    const int64_t *off = lists ? c->d_cell_off : nullptr;
+    const int *idx = lists ? c->d_cell_idx : nullptr;
     if (c->knn == 10)
         k_knn_scatter<10, true><<<blocks, 128, 0, c->stream>>>(
-            c->d_faces, c->d_state, c->max_faces, T, c->knn, c->acc_scale, c->d_acc, c->d_err);
+            c->d_faces, c->d_state, c->max_faces, T, c->knn, off, idx, c->acc_scale, c->d_acc,
+            c->d_err);
     else
         k_knn_scatter<32, false><<<blocks, 128, 0, c->stream>>>(
-            c->d_faces, c->d_state, c->max_faces, T, c->knn, c->acc_scale, c->d_acc, c->d_err);
+            c->d_faces, c->d_state, c->max_faces, T, c->knn, off, idx, c->acc_scale, c->d_acc,
+            c->d_err);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// per-leaf candidate lists of the faces' k nearest points
+// ---------------------------------------------------------------------------
+// A face lies in its leaf cell.  With c' the cell centre rounded to float and
+// h' >= |x - c'| for every x of the cell (half-diagonal plus the rounding of
+// c' and of a face centroid), the k nearest points of c' lie within r_k(c')
+// of c', so within r_k(c') + h' of any x: x's k nearest lie within
+// R = r_k(c') + 2 h' of c'.  R is widened by a relative 1e-4 and an absolute
+// 2^-17 of the coordinates so that float32 distance rounding cannot drop a
+// point; extra candidates cost time, never the result.
+constexpr int kCellCap = 128;
+
+__device__ __forceinline__ void cell_centre(int4 L, int d, const KnnTree &T, double cube_L,
+                                            F3 &cf, double &hp)
+{
+    const uint64_t code = (uint64_t)(uint32_t)L.y | ((uint64_t)(uint32_t)L.z << 32);
+    const double hd = cube_L / (double)(1ll << d);  // finest cell edge
+    const double e = hd * (double)(1ll << (d - L.x)); // this cell's edge
+    const double cx = T.cube_lo[0] + (double)(compact3(code) << (d - L.x)) * hd + 0.5 * e;
+    const double cy = T.cube_lo[1] + (double)(compact3(code >> 1) << (d - L.x)) * hd + 0.5 * e;
+    const double cz = T.cube_lo[2] + (double)(compact3(code >> 2) << (d - L.x)) * hd + 0.5 * e;
+    cf = F3{(float)cx, (float)cy, (float)cz};
+    const double mag = fabs(cx) + fabs(cy) + fabs(cz) + e;
+    hp = 0.5 * e * 1.7320508075688772 + ldexp(mag, -17);
+}
+
+template <int KMAX, bool FIXED>
+__global__ void __launch_bounds__(128)
+    k_cell_radius(const int4 *__restrict__ leaves, int64_t nl, int d, double cube_L, KnnTree T,
+                  int k, float *__restrict__ R2, int *err)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    F3 cf;
+    double hp;
+    cell_centre(leaves[l], d, T, cube_L, cf, hp);
+    int bj[KMAX];
+    knn_search<KMAX, FIXED>(T, cf, k, bj, err);
+    const int last = bj[(FIXED ? KMAX : k) - 1];
+    if (last < 0) {  // fewer than k points: every point is a candidate
+        R2[l] = INFINITY;
+        return;
+    }
+    const double rk = sqrt((double)pt_d2(T.p4[last], cf));
+    const double R = (rk + 2.0 * hp) * (1.0 + 1e-4) + ldexp(fabs((double)cf.x) + fabs((double)cf.y) +
+                                                             fabs((double)cf.z) + rk, -17);
+    R2[l] = __double2float_ru(R * R);
+}
+
+// points within the radius (FILL: write them; otherwise count, 0 above the cap)
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+    k_cell_lists(const int4 *__restrict__ leaves, int64_t nl, int d, double cube_L, KnnTree T,
+                 const float *__restrict__ R2, const int64_t *__restrict__ off,
+                 int *__restrict__ idx, int64_t *__restrict__ cnt, int *err)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    int64_t o0 = 0, room = 0;
+    if (FILL) {
+        o0 = off[l];
+        room = off[l + 1] - o0;
+        if (room <= 0) return;
+    }
+    F3 cf;
+    double hp;
+    cell_centre(leaves[l], d, T, cube_L, cf, hp);
+    const float r2 = R2[l];
+    const int64_t nleaf = (int64_t)1 << T.levels;
+    int stack[64];
+    int sp = 0;
+    int count = 0;
+    bool over = false;
+    stack[sp++] = 1;
+    while (sp > 0 && !over) {
+        const int node = stack[--sp];
+        if (box_d2(__ldg(&T.lo[node]), __ldg(&T.hi[node]), cf) > r2) continue;
+        if (node >= nleaf) {
+            const int64_t j0 = (int64_t)(node - nleaf) * kBucket;
+            const int64_t j1 = min(j0 + kBucket, T.n);
+            for (int64_t j = j0; j < j1; ++j) {
+                if (pt_d2(__ldg(&T.p4[j]), cf) > r2) continue;
+                if (FILL) {
+                    if (count < room) idx[o0 + count] = (int)j;
+                } else if (count == kCellCap) {
+                    over = true;
+                    break;
+                }
+                ++count;
+            }
+        } else {
+            if (sp + 2 > 64) {
+                atomicOr(err, kErrStack);
+                break;
+            }
+            stack[sp++] = 2 * node + 1;
+            stack[sp++] = 2 * node;
+        }
+    }
+    if (!FILL) cnt[l] = over ? 0 : count;
+    else if (count != room) atomicOr(err, kErrOverflow);  // the two passes must agree
+}
+
+void free_cell_lists(Ctx *c)
+{
+    cudaFree(c->d_cell_off);
+    cudaFree(c->d_cell_idx);
+    c->d_cell_off = nullptr;
+    c->d_cell_idx = nullptr;
+    c->cells_k = 0;
+}
+
+int build_cell_lists(Ctx *c)
+{
+    if (!c->knn_lists || c->nleaves < 1) return DWG_OK;
+    if (c->cells_k == c->knn && c->d_cell_off) return DWG_OK;
+    free_cell_lists(c);
+    ++c->bufgen;  // a captured graph holds the old pointers
+    const int64_t nl = c->nleaves;
+    const int d = c->built_depth;
+    KnnTree T = knn_tree(c);
+    float *R2 = nullptr;
+    int64_t *cnt = nullptr, *tot = nullptr;
+    auto body = [&]() -> int {
+        DWG_CUDA_TRY(c, cudaMalloc(&R2, nl * sizeof(float)));
+        DWG_CUDA_TRY(c, cudaMalloc(&cnt, nl * sizeof(int64_t)));
+        DWG_CUDA_TRY(c, cudaMalloc(&tot, sizeof(int64_t)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_cell_off, (nl + 1) * sizeof(int64_t)));
+        const unsigned g = (unsigned)ceil_div(nl, 128);
+        if (c->knn == 10)
+            k_cell_radius<10, true><<<g, 128, 0, c->stream>>>(c->d_leaves, nl, d, c->cube_L, T,
+                                                               c->knn, R2, c->d_err);
+        else
+            k_cell_radius<32, false><<<g, 128, 0, c->stream>>>(c->d_leaves, nl, d, c->cube_L, T,
+                                                                c->knn, R2, c->d_err);
+        k_cell_lists<false><<<g, 128, 0, c->stream>>>(c->d_leaves, nl, d, c->cube_L, T, R2,
+                                                      nullptr, nullptr, cnt, c->d_err);
+        int rc = scan_i64(c, cnt, c->d_cell_off, nl, tot);
+        if (rc) return rc;
+        int64_t total = 0;
+        DWG_CUDA_TRY(c, cudaMemcpyAsync(&total, tot, sizeof total, cudaMemcpyDeviceToHost,
+                                        c->stream));
+        DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        DWG_CUDA_TRY(c, cudaMemcpyAsync(c->d_cell_off + nl, tot, sizeof(int64_t),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+        // lists only where they fit comfortably (a quarter of the free memory)
+        size_t fr = 0, tt = 0;
+        cudaMemGetInfo(&fr, &tt);
+        if ((size_t)total * sizeof(int) > fr / 4) return DWG_ERR_OOM;
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_cell_idx, std::max<int64_t>(total, 1) * sizeof(int)));
+        k_cell_lists<true><<<g, 128, 0, c->stream>>>(c->d_leaves, nl, d, c->cube_L, T, R2,
+                                                     c->d_cell_off, c->d_cell_idx, nullptr,
+                                                     c->d_err);
+        DWG_CUDA_TRY(c, cudaGetLastError());
+        DWG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        c->cells_k = c->knn;
+        return DWG_OK;
+    };
+    int rc = body();
+    cudaFree(R2);
+    cudaFree(cnt);
+    cudaFree(tot);
+    if (rc) {
+        free_cell_lists(c);  // the tree search serves every face
+        if (rc == DWG_ERR_OOM) rc = DWG_OK;
+    }
+    return rc;
 }
 
 cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t *idx_out)

@@ -272,6 +272,7 @@ void tuning_of(const Ctx *c, dwg_tuning *t)
     t->tree_leaf = c->tree_leaf;
     t->theta = 1.0f / c->tree_beta;
     t->tree_group = c->tree_group;
+    t->knn_lists = c->knn_lists;
     t->w_err = c->tune_w_err;
     t->ms_points = c->tune_ms_points;
     t->ms_corners = c->tune_ms_corners;
@@ -303,7 +304,12 @@ int apply_tuning(Ctx *c, const dwg_tuning *t)
         c->err = "tuning: tree_group must be 0 or 1";
         return DWG_ERR_INVALID;
     }
+    if (t->knn_lists != 0 && t->knn_lists != 1) {
+        c->err = "tuning: knn_lists must be 0 or 1";
+        return DWG_ERR_INVALID;
+    }
     c->tree_group = t->tree_group;
+    c->knn_lists = t->knn_lists;
     c->path = t->path;
     c->var_grad = vg;
     c->var_w = vw;
@@ -361,6 +367,7 @@ int autotune(Ctx *c, int what, double budget, const char *cache_path, dwg_tuning
     }
     const std::string key = key_of(c, path_req, budget) + ", \"what\": " + std::to_string(what);
     dwg_tuning t;
+    tuning_of(c, &t);  // fields the cache does not hold keep the handle's values
     if (cache_lookup(cache_path, key, &t)) {
         if ((rc = apply_tuning(c, &t))) return rc;
         t.from_cache = 1;

@@ -70,7 +70,7 @@ class dwg_tuning(ctypes.Structure):
                 ("points_threads", ctypes.c_int), ("corners_pairs", ctypes.c_int),
                 ("corners_threads", ctypes.c_int), ("tree_leaf", ctypes.c_int),
                 ("theta", ctypes.c_float), ("tree_group", ctypes.c_int),
-                ("w_err", ctypes.c_double),
+                ("knn_lists", ctypes.c_int), ("w_err", ctypes.c_double),
                 ("ms_points", ctypes.c_double), ("ms_corners", ctypes.c_double),
                 ("from_cache", ctypes.c_int)]
 

@@ -396,3 +396,25 @@ def test_checkpoint_resume_is_bit_exact(dwglib, handle):
         totals.append(total)
     assert totals[0] >= 9 and totals[1] == totals[0]  # the split run resumed mid-way
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("kind,n,depth,k", [("torus", 20000, 7, 10), ("box", 6000, 6, 10),
+                                            ("torus", 20000, 8, 7), ("sphere", 3000, 9, 10)])
+def test_knn_cell_lists_equal_the_tree_search(dwglib, handle, kind, n, depth, k):
+    """The per-leaf candidate lists (knn_lists = 1) return exactly the tree
+    search's k nearest points: identical normals and iteration counts."""
+    p, _, a, eps = make_cloud(n, seed=21, kind=kind)
+    n0 = synth.random_unit_normals(n, seed=22).astype(np.float32)
+    res = []
+    for lists in (1, 0):
+        h = handle(p)
+        dwglib.dwg_set_weights(h, a)
+        dwglib.dwg_set_params(h, 1, eps, 10.0, 12, 0.1)
+        dwglib.dwg_set_update(h, depth, k, dwglib.DWG_UPDATE_LEVELSET)
+        dwglib.dwg_set_tuning(h, knn_lists=lists)
+        dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, n0)
+        out = np.zeros((n, 3), np.float32)
+        rc, it = dwglib.dwg_orient(h, out)
+        res.append((it, out))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
