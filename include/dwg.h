@@ -168,10 +168,15 @@ int dwg_set_tree(dwg_handle h, int path, float theta);
  *     the largest extent of the points' bounding box.
  *     Whether a pair lies inside is decided in float32 (|p_j - q|^2 from
  *     float offsets against delta_j^2 rounded to float).
- *     The modified kernel runs on the all-pairs path only: it is refused
- *     while the path is DWG_PATH_TREE, DWG_PATH_AUTO then always picks
- *     all-pairs, and dwg_autotune returns DWG_ERR_STATE.  Batch handles
- *     refuse it (DWG_ERR_STATE).
+ *     On the Barnes-Hut path a node opens unless the query is farther than
+ *     both r / theta and r + (the largest radius of its points) from its
+ *     centre, so far nodes never hold a point whose radius reaches the query
+ *     and keep the unclamped dipole; leaf points take the clamp.  The group
+ *     lists and the per-query walk implement it (without group lists, i.e.
+ *     when they do not fit in memory, the per-query walk serves).
+ *     dwg_autotune returns DWG_ERR_STATE while it is set (one evaluator
+ *     shape; set the tree's settings by hand).  Batch handles refuse it
+ *     (DWG_ERR_STATE).
  *   k: [1, 31] (CLAMP only).  delta_out: float32 n, input order, host or
  *   device, receives delta_j; may be NULL.
  */

@@ -89,11 +89,11 @@ def _load():
             lib.dwgo_morton_order.argtypes = [i64, P, P]
             lib.dwgo_tree_gwn.argtypes = [i64, P, P, P, i64, P, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P,
-                                          P, P]
+                                          P, P, P]
             lib.dwgo_tree_gwn_group.argtypes = [i64, P, P, P, i64, P, ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, P,
-                                                P, P]
+                                                P, P, P]
             _lib = lib
     return _lib
 
@@ -265,20 +265,24 @@ def morton_order(points):
 
 
 def tree_gwn(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0.0, lam=0.0,
-             beta=2.0, bucket=16, grad=True, want_count=False, want_bound=False):
+             beta=2.0, bucket=16, grad=True, want_count=False, want_bound=False, delta=None):
     """Barnes-Hut w (and grad w) at queries (Sec. 5.2); optional per-query
-    evaluation counts and first-order error bounds."""
+    evaluation counts and first-order error bounds.  delta: per-point radii
+    of the modified kernel (Sec. 5.2; eps unused then), which also widen the
+    opening radius to r + max delta."""
     lib = _load()
     p = _d(points, 3)
     nn = _d(normals, 3)
     a = _d(weights).ravel()
     q = _d(queries, 3)
+    dl = None if delta is None else _d(delta).ravel()
     w = np.zeros(len(q))
     g = np.zeros((len(q), 3)) if grad else None
     cnt = np.zeros(len(q)) if want_count else None
     bnd = np.zeros(len(q)) if want_bound else None
     lib.dwgo_tree_gwn(len(p), _ptr(p), _ptr(nn), _ptr(a), len(q), _ptr(q), int(kernel),
-                      float(eps), float(lam), float(beta), int(bucket), _ptr(w),
+                      float(eps), float(lam), float(beta), int(bucket),
+                      _ptr(dl) if dl is not None else None, _ptr(w),
                       _ptr(g) if grad else None, _ptr(cnt) if want_count else None,
                       _ptr(bnd) if want_bound else None)
     out = [w]
@@ -292,7 +296,7 @@ def tree_gwn(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0.0, la
 
 
 def tree_gwn_group(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0.0, lam=0.0,
-                   beta=2.0, bucket=16, group=64, grad=True, want_count=False):
+                   beta=2.0, bucket=16, group=64, grad=True, want_count=False, delta=None):
     """Barnes-Hut w (and grad w) with the opening test applied to groups of
     `group` consecutive queries (a conservative form of Sec. 5.2's test);
     optional per-query evaluation counts."""
@@ -304,8 +308,10 @@ def tree_gwn_group(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0
     w = np.zeros(len(q))
     g = np.zeros((len(q), 3)) if grad else None
     cnt = np.zeros(len(q)) if want_count else None
+    dl = None if delta is None else _d(delta).ravel()
     lib.dwgo_tree_gwn_group(len(p), _ptr(p), _ptr(nn), _ptr(a), len(q), _ptr(q), int(kernel),
                             float(eps), float(lam), float(beta), int(bucket), int(group),
+                            _ptr(dl) if dl is not None else None,
                             _ptr(w), _ptr(g) if grad else None,
                             _ptr(cnt) if want_count else None)
     out = [w]

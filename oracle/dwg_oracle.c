@@ -743,8 +743,13 @@ void dwgo_morton_order(int64_t n, const double *p, int64_t *order)
     free(ki);
 }
 
+/* delta (n, input order, or NULL): clamp radii of the modified kernel.  A
+ * node then opens unless the query is farther than both beta r and
+ * r + delta_max from its centre, delta_max the largest radius of its points
+ * (as sqrt of the float32-rounded delta^2 the kernel stores), so a far
+ * node never holds a point whose radius reaches the query. */
 static void bh_build(bh_tree *T, int64_t n, const double *p, const double *nrm, const double *a,
-                     int bucket, double beta)
+                     int bucket, double beta, const double *delta)
 {
     T->n = n;
     T->bucket = bucket;
@@ -812,11 +817,26 @@ static void bh_build(bh_tree *T, int64_t n, const double *p, const double *nrm, 
         }
         T->r[node] = rm;
     }
+    double *dmax = NULL;
+    if (delta) {
+        dmax = (double *)calloc((size_t)nn, sizeof(double));
+        for (int64_t b = 0; b < T->nleaf; ++b) {
+            int64_t node = T->nleaf + b, j0 = b * bucket, j1 = j0 + bucket < n ? j0 + bucket : n;
+            for (int64_t j = j0; j < j1; ++j) {
+                double d = sqrt((double)(float)(delta[T->order[j]] * delta[T->order[j]]));
+                if (d > dmax[node]) dmax[node] = d;
+            }
+        }
+        for (int64_t node = T->nleaf - 1; node >= 1; --node)
+            dmax[node] = dmax[2 * node] > dmax[2 * node + 1] ? dmax[2 * node] : dmax[2 * node + 1];
+    }
     for (int64_t node = 1; node < nn; ++node) {
         for (int k = 0; k < 3; ++k) T->cf[3 * node + k] = (float)T->c[3 * node + k];
         double br = beta * T->r[node];
+        if (dmax && T->r[node] + dmax[node] > br) br = T->r[node] + dmax[node];
         T->br2[node] = (float)(br * br);
     }
+    free(dmax);
     free(Sp);
 }
 
@@ -851,8 +871,8 @@ static int far_test(const bh_tree *T, int64_t node, const double *q)
 }
 
 static void bh_query(const bh_tree *T, int64_t node, const double *p, const double *nrm,
-                     const double *a, const double *q, int screened, double eps, double s,
-                     double *w, double g[3], double *count, double *bound)
+                     const double *a, const double *delta, const double *q, int screened,
+                     double eps, double s, double *w, double g[3], double *count, double *bound)
 {
     if (!(T->A[node] > 0.0)) return; /* empty */
     if (far_test(T, node, q)) {
@@ -877,15 +897,15 @@ static void bh_query(const bh_tree *T, int64_t node, const double *p, const doub
             const double *pi = p + 3 * i;
             if (pi[0] == q[0] && pi[1] == q[1] && pi[2] == q[2]) continue;
             double t, gt[3];
-            term(pi, nrm + 3 * i, a[i], q, screened, eps, 0.0, s, &t, gt);
+            term(pi, nrm + 3 * i, a[i], q, screened, eps, delta ? delta[i] : 0.0, s, &t, gt);
             *w += t;
             g[0] += gt[0]; g[1] += gt[1]; g[2] += gt[2];
             *count += 1.0;
         }
         return;
     }
-    bh_query(T, 2 * node, p, nrm, a, q, screened, eps, s, w, g, count, bound);
-    bh_query(T, 2 * node + 1, p, nrm, a, q, screened, eps, s, w, g, count, bound);
+    bh_query(T, 2 * node, p, nrm, a, delta, q, screened, eps, s, w, g, count, bound);
+    bh_query(T, 2 * node + 1, p, nrm, a, delta, q, screened, eps, s, w, g, count, bound);
 }
 
 /*
@@ -897,16 +917,18 @@ static void bh_query(const bh_tree *T, int64_t node, const double *p, const doub
  */
 void dwgo_tree_gwn(int64_t n, const double *p, const double *nrm, const double *a, int64_t m,
                    const double *q, int kernel, double eps, double lambda, double beta,
-                   int bucket, double *w, double *g, double *count, double *bound)
+                   int bucket, const double *delta, double *w, double *g, double *count,
+                   double *bound)
 {
     bh_tree T;
-    bh_build(&T, n, p, nrm, a, bucket, beta);
+    bh_build(&T, n, p, nrm, a, bucket, beta, delta);
     double s = sqrt(lambda > 0 ? lambda : 0.0);
     int screened = (kernel == 1);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < m; ++i) {
         double wi = 0.0, gi[3] = {0, 0, 0}, ci = 0.0, bi = 0.0;
-        bh_query(&T, 1, p, nrm, a, q + 3 * i, screened, eps, s, &wi, gi, &ci, bound ? &bi : NULL);
+        bh_query(&T, 1, p, nrm, a, delta, q + 3 * i, screened, eps, s, &wi, gi, &ci,
+                 bound ? &bi : NULL);
         w[i] = wi;
         if (g) { g[3 * i] = gi[0]; g[3 * i + 1] = gi[1]; g[3 * i + 2] = gi[2]; }
         if (count) count[i] = ci;
@@ -968,11 +990,11 @@ static void bh_group_lists(const bh_tree *T, int64_t node, const float lo[3], co
 
 void dwgo_tree_gwn_group(int64_t n, const double *p, const double *nrm, const double *a,
                          int64_t m, const double *q, int kernel, double eps, double lambda,
-                         double beta, int bucket, int group, double *w, double *g,
-                         double *count)
+                         double beta, int bucket, int group, const double *delta, double *w,
+                         double *g, double *count)
 {
     bh_tree T;
-    bh_build(&T, n, p, nrm, a, bucket, beta);
+    bh_build(&T, n, p, nrm, a, bucket, beta, delta);
     double s = sqrt(lambda > 0 ? lambda : 0.0);
     int screened = (kernel == 1);
     int64_t ngroups = (m + group - 1) / group;
@@ -1006,7 +1028,8 @@ void dwgo_tree_gwn_group(int64_t n, const double *p, const double *nrm, const do
                     int64_t k = T.order[j];
                     const double *pk = p + 3 * k;
                     if (pk[0] == qi[0] && pk[1] == qi[1] && pk[2] == qi[2]) continue;
-                    term(pk, nrm + 3 * k, a[k], qi, screened, eps, 0.0, s, &t, gt);
+                    term(pk, nrm + 3 * k, a[k], qi, screened, eps, delta ? delta[k] : 0.0, s,
+                         &t, gt);
                     wi += t;
                     gq[0] += gt[0]; gq[1] += gt[1]; gq[2] += gt[2];
                     ci += 1.0;

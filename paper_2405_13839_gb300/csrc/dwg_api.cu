@@ -43,7 +43,6 @@ void set_global_error(const std::string &msg)
 namespace dwg {
 bool use_tree(const Ctx *c)
 {
-    if (c->reg_mode == DWG_REG_CLAMP) return false;  // the modified kernel is all-pairs only
     if (c->path == DWG_PATH_TREE) return true;
     if (c->path == DWG_PATH_ALLPAIRS) return false;
     return c->n > 65536;
@@ -493,7 +492,7 @@ void dwg_destroy(dwg_handle h)
                     h->d_state, h->d_tr_iso, h->d_tr_stat, h->d_tr_dn, h->d_tr_faces, h->d_err,
                     h->d_tree_A, h->d_tree_C, h->d_tree_R, h->d_tree_M, h->d_tree_rec,
                     h->d_tree_mrec, h->d_tree_frec, h->d_counter, h->d_mlp_params,
-                    h->d_delta2, h->d_src16, h->d_cell_off, h->d_cell_idx};
+                    h->d_delta2, h->d_src16, h->d_cell_off, h->d_cell_idx, h->d_tree_dmax};
     for (void *p : bufs) cudaFree(p);
     free_lists(h->lists_p);
     free_lists(h->lists_c);
@@ -690,8 +689,6 @@ int dwg_set_tree(dwg_handle h, int path, float theta)
     if (path != DWG_PATH_AUTO && path != DWG_PATH_ALLPAIRS && path != DWG_PATH_TREE)
         return fail(h, DWG_ERR_INVALID, "unknown path");
     if (!(theta > 0.f) || !(theta <= 1.f)) return fail(h, DWG_ERR_INVALID, "theta must be in (0, 1]");
-    if (path == DWG_PATH_TREE && h->reg_mode == DWG_REG_CLAMP)
-        return fail(h, DWG_ERR_STATE, "the modified kernel (DWG_REG_CLAMP) runs on the all-pairs path");
     h->path = path;
     h->tree_beta = 1.0f / theta;
     invalidate_graph(h);
@@ -727,6 +724,7 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
     if (mode == DWG_REG_SOFTEN) {
         if (h->reg_mode != mode) {
             h->reg_mode = mode;
+            ++h->delta_gen;
             invalidate_graph(h);
             ++h->bufgen;
         }
@@ -741,9 +739,6 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
     }
     if (!(vmin > 0.f) || !(vmax >= vmin) || !isfinite(vmax))
         return fail(h, DWG_ERR_INVALID, "need 0 < vmin <= vmax (or both 0 for the defaults)");
-    if (h->path == DWG_PATH_TREE)
-        return fail(h, DWG_ERR_STATE, "the modified kernel runs on the all-pairs path (set "
-                                      "DWG_PATH_AUTO or DWG_PATH_ALLPAIRS first)");
     if (!h->d_delta2) DWG_CUDA_TRY(h, cudaMalloc(&h->d_delta2, h->n * sizeof(float)));
     if (!h->d_src16)
         DWG_CUDA_TRY(h, cudaMalloc(&h->d_src16, h->npad * kSrcFloatsClamp * sizeof(float)));
@@ -765,6 +760,7 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
     cudaFree(d_out);
     if (rc) return rc;
     h->reg_mode = mode;
+    ++h->delta_gen;  // tree opening radii and group lists depend on the radii
     // the records are repacked (with delta^2) before the next evaluation
     invalidate_graph(h);
     ++h->bufgen;  // a captured graph holds the other kernels and records
@@ -1147,8 +1143,6 @@ int dwg_get_tuning(dwg_handle h, dwg_tuning *out)
 int dwg_set_tuning(dwg_handle h, const dwg_tuning *t)
 {
     if (!h || !t) return DWG_ERR_INVALID;
-    if (h->reg_mode == DWG_REG_CLAMP && t->path == DWG_PATH_TREE)
-        return fail(h, DWG_ERR_STATE, "the modified kernel (DWG_REG_CLAMP) runs on the all-pairs path");
     invalidate_graph(h);
     if (h->is_batch) {
         for (dwg_ctx *c : h->clouds) {

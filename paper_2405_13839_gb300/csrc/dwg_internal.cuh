@@ -201,6 +201,9 @@ struct Ctx {
     int tree_levels = 0;               // 2^tree_levels leaves
     bool tree_built = false;
     double tree_beta_set = -1.0;
+    int tree_rec_dgen = -1;            // delta_gen the traversal records were built for
+    int delta_gen = 0;                 // bumped whenever the clamp radii change
+    double *d_tree_dmax = nullptr;     // largest clamp radius per node (modified kernel)
     double *d_tree_A = nullptr, *d_tree_C = nullptr, *d_tree_R = nullptr, *d_tree_M = nullptr;
     float4 *d_tree_rec = nullptr, *d_tree_mrec = nullptr;
     float4 *d_tree_frec = nullptr;     // node as a duplicated 48-byte source record

@@ -121,9 +121,33 @@ __global__ void k_tree_level_radius(int64_t first, const double *A, const double
     R[node] = rm;
 }
 
-// traversal record (c_f, (beta r)^2 as float; -1 marks an empty node)
+// Largest clamp radius of the modified kernel per node (sqrt of the stored
+// float delta^2, in double): leaves over their points, then level by level.
+__global__ void k_tree_leaf_dmax(const float *__restrict__ delta2, int64_t n, int64_t nleaf,
+                                 int bucket, double *Dmax)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    int64_t j0 = b * bucket, j1 = min(j0 + bucket, n);
+    double dm = 0.0;
+    for (int64_t j = j0; j < j1; ++j) dm = fmax(dm, sqrt((double)delta2[j]));
+    Dmax[nleaf + b] = dm;
+}
+
+__global__ void k_tree_level_dmax(int64_t first, double *Dmax)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= first) return;
+    int64_t node = first + t;
+    Dmax[node] = fmax(Dmax[2 * node], Dmax[2 * node + 1]);
+}
+
+// traversal record (c_f, (beta r)^2 as float; -1 marks an empty node).  With
+// the modified kernel's radii (Dmax non-null) the opening radius is
+// max(beta r, r + Dmax): a far node then never holds a point whose radius
+// reaches the query, and its dipole is the unclamped one.
 __global__ void k_tree_records(int64_t nn, const double *A, const double *C, const double *R,
-                               double beta, float4 *rec)
+                               double beta, const double *Dmax, float4 *rec)
 {
     int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= nn) return;
@@ -132,6 +156,7 @@ __global__ void k_tree_records(int64_t nn, const double *A, const double *C, con
         return;
     }
     double br = __dmul_rn(beta, R[node]);
+    if (Dmax) br = fmax(br, __dadd_rn(R[node], Dmax[node]));
     rec[node] = make_float4((float)C[3 * node], (float)C[3 * node + 1], (float)C[3 * node + 2],
                             (float)__dmul_rn(br, br));
 }
@@ -216,13 +241,18 @@ struct TreeAcc {
     int pending;
 };
 
-template <bool GRAD, bool SCREENED>
+// One term; with CLAMP the modified kernel of Sec. 5.2 (eps2 is 0 then):
+// rho^2 = max(|p - q|^2, d2), and inside the radius the gradient keeps only
+// its -F m / rho^3 part.  Far nodes pass d2 = 0.
+template <bool GRAD, bool SCREENED, bool CLAMP = false>
 __device__ __forceinline__ void tree_term(TreeAcc &A, float qx, float qy, float qz, float px,
                                           float py, float pz, float mx, float my, float mz,
-                                          const EvalParams &ep)
+                                          const EvalParams &ep, float d2 = 0.f)
 {
     float dx = px - qx, dy = py - qy, dz = pz - qz;
     float rr = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, ep.eps2)));
+    const bool outside = !CLAMP || rr >= d2;
+    if (CLAMP) rr = fmaxf(rr, d2);
     float inv = rsqrt_approx(rr);
     float md = fmaf(mz, dz, fmaf(my, dy, mx * dx));
     float i2 = inv * inv, i3 = i2 * inv;
@@ -230,7 +260,7 @@ __device__ __forceinline__ void tree_term(TreeAcc &A, float qx, float qy, float 
         float phi = md * i3;
         A.tw += phi;
         if (GRAD) {
-            float c = phi * i2;
+            float c = outside ? phi * i2 : 0.f;
             A.t1x = fmaf(c, dx, A.t1x); A.t1y = fmaf(c, dy, A.t1y); A.t1z = fmaf(c, dz, A.t1z);
             A.t2x = fmaf(mx, i3, A.t2x); A.t2y = fmaf(my, i3, A.t2y); A.t2z = fmaf(mz, i3, A.t2z);
         }
@@ -243,7 +273,7 @@ __device__ __forceinline__ void tree_term(TreeAcc &A, float qx, float qy, float 
         if (GRAD) {
             float fi3 = F * i3;
             float cc = fmaf(3.f, F * i2, ep.s2 * e);
-            float c = phi * cc;
+            float c = outside ? phi * cc : 0.f;
             A.t1x = fmaf(c, dx, A.t1x); A.t1y = fmaf(c, dy, A.t1y); A.t1z = fmaf(c, dz, A.t1z);
             A.t2x = fmaf(mx, fi3, A.t2x); A.t2y = fmaf(my, fi3, A.t2y); A.t2z = fmaf(mz, fi3, A.t2z);
         }
@@ -270,12 +300,13 @@ __device__ __forceinline__ void tree_fold(TreeAcc &A)
 constexpr int kTreeThreads = 128;
 constexpr int kTreeStack = 64;
 
-template <bool GRAD, bool SCREENED>
+template <bool GRAD, bool SCREENED, bool CLAMP = false>
 __global__ void __launch_bounds__(kTreeThreads)
     k_tree_gwn(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ rec,
                const float4 *__restrict__ mrec, const float *__restrict__ src, int64_t n,
                int levels, int bucket, EvalParams ep, float *__restrict__ part, int64_t stride,
-               unsigned long long *__restrict__ counter, int *err, const IterState *st)
+               unsigned long long *__restrict__ counter, int *err, const IterState *st,
+               const float *__restrict__ delta2 = nullptr)
 {
     if (st && cloud_idle(st)) return;  // finished cloud of a batch
     __shared__ int s_node[kTreeThreads / 32][kTreeStack];
@@ -310,7 +341,8 @@ __global__ void __launch_bounds__(kTreeThreads)
         const bool far = active && d2 > cr.w;
         if (far) {
             float4 mm = mrec[node];
-            tree_term<GRAD, SCREENED>(A, qq.x, qq.y, qq.z, cr.x, cr.y, cr.z, mm.x, mm.y, mm.z, ep);
+            tree_term<GRAD, SCREENED, CLAMP>(A, qq.x, qq.y, qq.z, cr.x, cr.y, cr.z, mm.x, mm.y,
+                                             mm.z, ep);
             ++evals;
         }
         const unsigned near = __ballot_sync(0xffffffffu, active && !far);
@@ -320,8 +352,9 @@ __global__ void __launch_bounds__(kTreeThreads)
                 if (near & lanebit) {
                     for (int64_t j = j0; j < j1; ++j) {
                         const float *r = src + j * kSrcFloats;
-                        tree_term<GRAD, SCREENED>(A, qq.x, qq.y, qq.z, r[0], r[2], r[4], r[6],
-                                                  r[8], r[10], ep);
+                        tree_term<GRAD, SCREENED, CLAMP>(A, qq.x, qq.y, qq.z, r[0], r[2], r[4],
+                                                         r[6], r[8], r[10], ep,
+                                                         CLAMP ? __ldg(&delta2[j]) : 0.f);
                     }
                     evals += (unsigned long long)(j1 - j0);
                 }
@@ -381,10 +414,13 @@ struct GrpAcc {
 
 // every lane: its two queries against `cnt` records of `buf`, the flush's
 // plain FP32 sums folded into the compensated totals
-template <bool GRAD, bool SCREENED>
+// With CLAMP the records are four 16-byte words, the fourth (d2, d2, 0, 0)
+// (d2 = 0 for far nodes), and the terms are those of the modified kernel.
+template <bool GRAD, bool SCREENED, bool CLAMP = false>
 __device__ __forceinline__ void grp_flush(GrpAcc &A, const float4 *buf, int cnt, f2 qx, f2 qy,
                                           f2 qz, const EvalParams &ep)
 {
+    constexpr int RW = CLAMP ? 4 : 3;
     const f2 eps2 = pk(ep.eps2, ep.eps2);
     const f2 three = pk(3.f, 3.f);
     const f2 zero = pk(0.f, 0.f);
@@ -395,15 +431,19 @@ __device__ __forceinline__ void grp_flush(GrpAcc &A, const float4 *buf, int cnt,
     const ulonglong2 *rec = reinterpret_cast<const ulonglong2 *>(buf);
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
-        const ulonglong2 r0 = rec[3 * j + 0];  // (x,x) (y,y)
-        const ulonglong2 r1 = rec[3 * j + 1];  // (z,z) (mx,mx)
-        const ulonglong2 r2v = rec[3 * j + 2]; // (my,my) (mz,mz)
+        const ulonglong2 r0 = rec[RW * j + 0];  // (x,x) (y,y)
+        const ulonglong2 r1 = rec[RW * j + 1];  // (z,z) (mx,mx)
+        const ulonglong2 r2v = rec[RW * j + 2]; // (my,my) (mz,mz)
+        f2 d2c = zero;
+        if (CLAMP) d2c = rec[RW * j + 3].x;     // (d2,d2)
         f2 dx = sub2(r0.x, qx);
         f2 dy = sub2(r0.y, qy);
         f2 dz = sub2(r1.x, qz);
         f2 rr = fma2(dx, dx, eps2);
         rr = fma2(dy, dy, rr);
         rr = fma2(dz, dz, rr);
+        const f2 r2raw = rr;
+        if (CLAMP) rr = max2(rr, d2c);
         f2 inv = rsqrt2(rr);
         f2 md = mul2(r1.y, dx);
         md = fma2(r2v.x, dy, md);
@@ -415,6 +455,7 @@ __device__ __forceinline__ void grp_flush(GrpAcc &A, const float4 *buf, int cnt,
                 f2 phi = mul2(md, i3);
                 tw = add2(tw, phi);
                 f2 c = mul2(phi, i2);
+                if (CLAMP) c = keep_ge(c, r2raw, d2c);
                 t1x = fma2(c, dx, t1x);
                 t1y = fma2(c, dy, t1y);
                 t1z = fma2(c, dz, t1z);
@@ -434,6 +475,7 @@ __device__ __forceinline__ void grp_flush(GrpAcc &A, const float4 *buf, int cnt,
                 f2 fi3 = mul2(F, i3);
                 f2 cc = fma2(three, mul2(F, i2), mul2(s2v, e));
                 f2 c = mul2(phi, cc);
+                if (CLAMP) c = keep_ge(c, r2raw, d2c);
                 t1x = fma2(c, dx, t1x);
                 t1y = fma2(c, dy, t1y);
                 t1z = fma2(c, dz, t1z);
@@ -721,7 +763,9 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// global address of record r of the group's stream
+// global address of record r of the group's stream (point records of
+// NEAR_W 16-byte words: 3, or 4 with the modified kernel's radius)
+template <int NEAR_W = 3>
 __device__ __forceinline__ const float4 *lst_record(int64_t r, int64_t nf, int64_t f0, int64_t e0,
                                                     const int *__restrict__ far_ids,
                                                     const int *__restrict__ near_ids,
@@ -732,7 +776,7 @@ __device__ __forceinline__ const float4 *lst_record(int64_t r, int64_t nf, int64
     if (r < nf) return frec + 3 * (int64_t)far_ids[f0 + r];
     const int64_t rr = r - nf;  // leaves hold 2^lg_bucket points
     const int64_t leaf = near_ids[e0 + (rr >> lg_bucket)];
-    return src4 + 3 * (((leaf - nleaf) << lg_bucket) + (rr & ((1 << lg_bucket) - 1)));
+    return src4 + NEAR_W * (((leaf - nleaf) << lg_bucket) + (rr & ((1 << lg_bucket) - 1)));
 }
 
 // Work items: a group's stream is cut into items of at most kItemRecords
@@ -761,7 +805,7 @@ __global__ void k_tree_item_table(const int64_t *__restrict__ item_off, int64_t 
         items[i] = make_int2((int)g, (int)(j * kItemRecords));
 }
 
-template <bool GRAD, bool SCREENED>
+template <bool GRAD, bool SCREENED, bool CLAMP = false>
 __global__ void __launch_bounds__(32 * kGrpWarps)
     k_tree_eval_lists(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ frec,
                       const float *__restrict__ src, int64_t n, int levels, int bucket,
@@ -773,7 +817,8 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
 {
     if (st && cloud_idle(st)) return;  // finished cloud of a batch
     constexpr int NA = GRAD ? 4 : 1;
-    __shared__ float4 buf_all[kGrpWarps][2][kLstChunk * 3];
+    constexpr int RW = CLAMP ? 4 : 3;  // 16-byte words per staged record
+    __shared__ float4 buf_all[kGrpWarps][2][kLstChunk * RW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t it = (int64_t)blockIdx.x * kGrpWarps + wid;
     if (it >= nitems) return;
@@ -800,11 +845,15 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
         for (int h = 0; h < 2; ++h) {
             const int t = lane + 32 * h;
             if (r0 + t < r_end) {
-                const float4 *from =
-                    lst_record(r0 + t, nf, f0, e0, far_ids, near_ids, frec, src4, nleaf, lg_bucket);
-                cp_async16(b + 3 * t + 0, from + 0);
-                cp_async16(b + 3 * t + 1, from + 1);
-                cp_async16(b + 3 * t + 2, from + 2);
+                const float4 *from = lst_record<RW>(r0 + t, nf, f0, e0, far_ids, near_ids, frec,
+                                                    src4, nleaf, lg_bucket);
+                cp_async16(b + RW * t + 0, from + 0);
+                cp_async16(b + RW * t + 1, from + 1);
+                cp_async16(b + RW * t + 2, from + 2);
+                if (CLAMP) {
+                    if (r0 + t < nf) b[RW * t + 3] = make_float4(0.f, 0.f, 0.f, 0.f);  // far node
+                    else cp_async16(b + RW * t + 3, from + 3);
+                }
             }
         }
         cp_async_commit();
@@ -816,7 +865,7 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
         cp_async_wait1();        // chunk k has landed (this lane's copies)
         __syncwarp();            // ... and every lane's
         const int cnt = (int)min((int64_t)kLstChunk, r_end - r_begin - k * kLstChunk);
-        grp_flush<GRAD, SCREENED>(A, buf_all[wid][k & 1], cnt, qx, qy, qz, ep);
+        grp_flush<GRAD, SCREENED, CLAMP>(A, buf_all[wid][k & 1], cnt, qx, qy, qz, ep);
         __syncwarp();  // buffer k & 1 is reused by the copy of chunk k + 2
     }
     // the item's sums: ipart[((it * NA + a) * 2 + h) * 64 + slot]
@@ -912,7 +961,9 @@ static uint64_t lists_key(const Ctx *c)
 {
     uint32_t bb;
     memcpy(&bb, &c->tree_beta, sizeof bb);
-    return (c->tree_gen * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)bb << 8) ^ (uint64_t)c->built_depth;
+    const uint64_t dg = c->reg_mode == DWG_REG_CLAMP ? (uint64_t)c->delta_gen + 1 : 0;
+    return (c->tree_gen * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)bb << 8) ^
+           (uint64_t)c->built_depth ^ (dg * 0xC2B2AE3D27D4EB4Full);
 }
 
 int tree_lists(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool *built)
@@ -1009,7 +1060,9 @@ void free_tree(Ctx *c)
     cudaFree(c->d_tree_rec);
     cudaFree(c->d_tree_mrec);
     cudaFree(c->d_tree_frec);
+    cudaFree(c->d_tree_dmax);
     c->d_tree_frec = nullptr;
+    c->d_tree_dmax = nullptr;
     c->d_tree_A = c->d_tree_C = c->d_tree_R = c->d_tree_M = nullptr;
     c->d_tree_rec = c->d_tree_mrec = nullptr;
     c->tree_built = false;
@@ -1065,12 +1118,24 @@ int build_tree(Ctx *c)
 
 int tree_records(Ctx *c)
 {
-    if (c->tree_beta_set == (double)c->tree_beta) return DWG_OK;
-    const int64_t nn = (int64_t)2 << c->tree_levels;
+    const bool clamp = c->reg_mode == DWG_REG_CLAMP;
+    const int dgen = clamp ? c->delta_gen : -1;
+    if (c->tree_beta_set == (double)c->tree_beta && c->tree_rec_dgen == dgen) return DWG_OK;
+    const int64_t nleaf = (int64_t)1 << c->tree_levels, nn = 2 * nleaf;
+    if (clamp) {
+        if (!c->d_tree_dmax) DWG_CUDA_TRY(c, cudaMalloc(&c->d_tree_dmax, nn * sizeof(double)));
+        k_tree_leaf_dmax<<<(unsigned)ceil_div(nleaf, 256), 256, 0, c->stream>>>(
+            c->d_delta2, c->n, nleaf, c->tree_leaf, c->d_tree_dmax);
+        for (int64_t first = nleaf / 2; first >= 1; first /= 2)
+            k_tree_level_dmax<<<(unsigned)ceil_div(first, 256), 256, 0, c->stream>>>(
+                first, c->d_tree_dmax);
+    }
     k_tree_records<<<(unsigned)ceil_div(nn, 256), 256, 0, c->stream>>>(
-        nn, c->d_tree_A, c->d_tree_C, c->d_tree_R, (double)c->tree_beta, c->d_tree_rec);
+        nn, c->d_tree_A, c->d_tree_C, c->d_tree_R, (double)c->tree_beta,
+        clamp ? c->d_tree_dmax : nullptr, c->d_tree_rec);
     DWG_CUDA_TRY(c, cudaGetLastError());
     c->tree_beta_set = (double)c->tree_beta;
+    c->tree_rec_dgen = dgen;
     return DWG_OK;
 }
 
@@ -1104,15 +1169,16 @@ static cudaError_t launch_group_t(Ctx *c, const float4 *q, int64_t m, float *par
     return cudaGetLastError();
 }
 
-template <bool GRAD, bool SCREENED>
+template <bool GRAD, bool SCREENED, bool CLAMP = false>
 static cudaError_t launch_lists_t(Ctx *c, const TreeLists &L, float *part, int64_t stride,
                                   const IterState *st)
 {
     EvalParams ep = make_eval_params(c);
-    k_tree_eval_lists<GRAD, SCREENED><<<(unsigned)ceil_div(L.nitems, kGrpWarps), 32 * kGrpWarps,
-                                         0, c->stream>>>(
-        L.q, L.m, c->d_tree_frec, c->d_src, c->n, c->tree_levels, c->tree_leaf, L.d_far_off,
-        L.d_far, L.d_near_off, L.d_near, L.d_items, L.nitems, ep, L.d_ipart, c->d_counter, st);
+    k_tree_eval_lists<GRAD, SCREENED, CLAMP><<<(unsigned)ceil_div(L.nitems, kGrpWarps),
+                                                32 * kGrpWarps, 0, c->stream>>>(
+        L.q, L.m, c->d_tree_frec, CLAMP ? c->d_src16 : c->d_src, c->n, c->tree_levels,
+        c->tree_leaf, L.d_far_off, L.d_far, L.d_near_off, L.d_near, L.d_items, L.nitems, ep,
+        L.d_ipart, c->d_counter, st);
     k_tree_combine<GRAD><<<(unsigned)ceil_div(L.m, 256), 256, 0, c->stream>>>(
         L.d_ipart, L.d_item_off, L.m, part, stride, st);
     return cudaGetLastError();
@@ -1124,6 +1190,13 @@ cudaError_t launch_tree_iter(Ctx *c, TreeLists &L, const float4 *q, int64_t m, b
     if (!(c->tree_group && L.valid && L.q == q && L.m == m && L.key == lists_key(c)))
         return launch_tree_gwn(c, q, m, grad, part, stride, st);
     const bool scr = make_eval_params(c).screened != 0;
+    if (c->reg_mode == DWG_REG_CLAMP) {
+        if (grad)
+            return scr ? launch_lists_t<true, true, true>(c, L, part, stride, st)
+                       : launch_lists_t<true, false, true>(c, L, part, stride, st);
+        return scr ? launch_lists_t<false, true, true>(c, L, part, stride, st)
+                   : launch_lists_t<false, false, true>(c, L, part, stride, st);
+    }
     if (grad)
         return scr ? launch_lists_t<true, true>(c, L, part, stride, st)
                    : launch_lists_t<true, false>(c, L, part, stride, st);
@@ -1131,10 +1204,31 @@ cudaError_t launch_tree_iter(Ctx *c, TreeLists &L, const float4 *q, int64_t m, b
                : launch_lists_t<false, false>(c, L, part, stride, st);
 }
 
+// the per-query walk with the modified kernel (also its path when the
+// group lists are not available: the on-the-fly group walk has no clamp)
+template <bool GRAD, bool SCREENED>
+static cudaError_t launch_walk_clamp(Ctx *c, const float4 *q, int64_t m, float *part,
+                                     int64_t stride, const IterState *st)
+{
+    EvalParams ep = make_eval_params(c);
+    k_tree_gwn<GRAD, SCREENED, true><<<(unsigned)ceil_div(m, kTreeThreads), kTreeThreads, 0,
+                                       c->stream>>>(
+        q, m, c->d_tree_rec, c->d_tree_mrec, c->d_src, c->n, c->tree_levels, c->tree_leaf, ep,
+        part, stride, c->d_counter, c->d_err, st, c->d_delta2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float *part,
                             int64_t stride, const IterState *st)
 {
     EvalParams ep = make_eval_params(c);
+    if (c->reg_mode == DWG_REG_CLAMP) {
+        if (grad)
+            return ep.screened ? launch_walk_clamp<true, true>(c, q, m, part, stride, st)
+                               : launch_walk_clamp<true, false>(c, q, m, part, stride, st);
+        return ep.screened ? launch_walk_clamp<false, true>(c, q, m, part, stride, st)
+                           : launch_walk_clamp<false, false>(c, q, m, part, stride, st);
+    }
     if (c->tree_group) {
         if (grad)
             return ep.screened ? launch_group_t<true, true>(c, q, m, part, stride, st)

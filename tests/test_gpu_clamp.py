@@ -187,15 +187,7 @@ def test_clamp_refusals(dwglib):
             with pytest.raises(dwglib.DWGError) as e:
                 dwglib.dwg_set_regularization(h, dwglib.DWG_REG_CLAMP, *args)
             assert e.value.code == dwglib.DWG_ERR_INVALID, args
-        dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
-        with pytest.raises(dwglib.DWGError) as e:
-            dwglib.dwg_set_regularization(h, dwglib.DWG_REG_CLAMP, 10, 0.01, 0.1)
-        assert e.value.code == dwglib.DWG_ERR_STATE
-        dwglib.dwg_set_tree(h, dwglib.DWG_PATH_AUTO, 0.5)
         dwglib.dwg_set_regularization(h, dwglib.DWG_REG_CLAMP, 10, 0.01, 0.1)
-        with pytest.raises(dwglib.DWGError) as e:
-            dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
-        assert e.value.code == dwglib.DWG_ERR_STATE
         with pytest.raises(dwglib.DWGError) as e:
             dwglib.dwg_autotune(h, dwglib.DWG_TUNE_SHAPES)
         assert e.value.code == dwglib.DWG_ERR_STATE
@@ -209,3 +201,102 @@ def test_clamp_refusals(dwglib):
         assert e.value.code == dwglib.DWG_ERR_STATE
     finally:
         dwglib.dwg_destroy(hb)
+
+
+@pytest.mark.parametrize("group", [0, 1])
+@pytest.mark.parametrize("grad,kernel,lam", [(True, 1, 30.0), (False, 1, 30.0), (True, 0, 0.0)])
+def test_clamp_tree_walk_matches_oracle_tree(dwglib, oracle_mod, group, grad, kernel, lam):
+    """Barnes-Hut with the modified kernel at arbitrary queries: the per-query
+    walk (with either test form set: arbitrary queries have no group lists,
+    and the modified kernel's fallback is the per-query walk) against the
+    oracle's per-query tree with the same radii and opening rule."""
+    n = 30000
+    p, _, a = _torus(n, 17)
+    n0 = synth.random_unit_normals(n, seed=5).astype(np.float32)
+    vmin, vmax = 0.005, 0.05
+    q = np.vstack([p[:4096], synth.uniform_box(2048, [-1.4, -1.4, -0.5], [1.4, 1.4, 0.5],
+                                                seed=9)]).astype(np.float32)
+    h = dwglib.dwg_create(p)
+    try:
+        dwglib.dwg_set_weights(h, a)
+        dwglib.dwg_set_params(h, kernel, 0.01, lam, 30, 0.1)
+        dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.4)
+        dwglib.dwg_set_tuning(h, tree_leaf=32, tree_group=group)
+        dwglib.dwg_set_regularization(h, dwglib.DWG_REG_CLAMP, 10, vmin, vmax)
+        dwglib.dwg_set_normals(h, n0)
+        w = np.zeros(len(q), np.float32)
+        g = np.zeros((len(q), 3), np.float32) if grad else None
+        dwglib.dwg_eval_gwn(h, q, w, g)
+    finally:
+        dwglib.dwg_destroy(h)
+    delta = oracle_mod.clamp_radii(p, 10, vmin, vmax)
+    beta = float(1.0 / np.float32(0.4))
+    out = oracle_mod.tree_gwn(p, n0, a, q, kernel=kernel, lam=lam, beta=beta, bucket=32,
+                              delta=delta, grad=grad)
+    wo, go = (out if grad else (out, None))
+    dw = np.abs(w - wo) / np.maximum(1.0, np.abs(wo))
+    assert dw.max() <= 1e-5, dw.max()
+    if grad:
+        sg = s_g_clamp(p, n0, a, q, delta)
+        tol = 1e-5 * np.maximum(1.0, np.linalg.norm(go, axis=1)) + 16 * U32 * sg
+        assert np.all(np.abs(g - go).max(axis=1) <= tol)
+
+
+@pytest.mark.parametrize("kernel,lam,leaf", [(1, 30.0, 32), (0, 0.0, 16)])
+def test_clamp_group_lists_step_matches_oracle_group_tree(dwglib, oracle_mod, kernel, lam, leaf):
+    """One iteration on the Barnes-Hut path with the group test and the
+    modified kernel evaluates the group lists (w and grad w at the points, in
+    Morton order, 64 per group): the oracle's group tree with the same radii
+    on the Morton-ordered points."""
+    n = 20000
+    p, _, a = _torus(n, 23)
+    nrm = synth.random_unit_normals(n, seed=13).astype(np.float32)
+    vmin, vmax = 0.005, 0.05
+    h = dwglib.dwg_create(p)
+    try:
+        dwglib.dwg_set_weights(h, a)
+        dwglib.dwg_set_params(h, kernel, 0.01, lam, 30, 0.1)
+        dwglib.dwg_set_update(h, 6, 10, dwglib.DWG_UPDATE_LEVELSET)
+        dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+        dwglib.dwg_set_tuning(h, tree_group=1, tree_leaf=leaf)
+        dwglib.dwg_set_regularization(h, dwglib.DWG_REG_CLAMP, 10, vmin, vmax)
+        dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, nrm)
+        w = np.zeros(n, np.float32)
+        g = np.zeros((n, 3), np.float32)
+        dwglib.dwg_step(h, w, g)
+    finally:
+        dwglib.dwg_destroy(h)
+    delta = oracle_mod.clamp_radii(p, 10, vmin, vmax)
+    order = oracle_mod.morton_order(p)
+    wo_s, go_s = oracle_mod.tree_gwn_group(p, nrm, a, p[order], kernel=kernel, lam=lam,
+                                           beta=2.0, bucket=leaf, group=64, delta=delta)
+    wo = np.empty(n)
+    go = np.empty((n, 3))
+    wo[order] = wo_s
+    go[order] = go_s
+    sel = np.arange(0, n, 7)
+    check_wg(w[sel], g[sel], wo[sel], go[sel], s_g_clamp(p, nrm, a, p[sel], delta))
+
+
+def test_clamp_tree_orientation(dwglib, oracle_mod):
+    """The whole iteration on the Barnes-Hut path with the modified kernel
+    orients the torus."""
+    n = 40000
+    p, nt, a = _torus(n, 19)
+    h = dwglib.dwg_create(p)
+    try:
+        dwglib.dwg_set_weights(h, a)
+        dwglib.dwg_set_params(h, 1, 0.01, 30.0, 60, 0.5)
+        dwglib.dwg_set_update(h, 7, 10, dwglib.DWG_UPDATE_LEVELSET)
+        dwglib.dwg_set_convergence(h, dwglib.DWG_CONV_MEAN)
+        dwglib.dwg_set_tree(h, dwglib.DWG_PATH_TREE, 0.5)
+        dwglib.dwg_set_regularization(h, dwglib.DWG_REG_CLAMP, 10, 0.0, 0.0)
+        dwglib.dwg_set_init(h, dwglib.DWG_INIT_RANDOM, 3)
+        out = np.zeros((n, 3), np.float32)
+        rc, it = dwglib.dwg_orient(h, out)
+        st = dwglib.dwg_get_stats(h)
+    finally:
+        dwglib.dwg_destroy(h)
+    assert rc == dwglib.DWG_OK, it
+    assert _agreement(out, nt) >= 0.99
+    assert st["interactions"] > 0

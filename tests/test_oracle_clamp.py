@@ -105,3 +105,56 @@ def test_clamp_radii_skip_self_keep_copies():
     assert d[0] == 1.0 and d[1] == 1.0
     # point 2: both copies at distance 1
     assert d[2] == 1.0
+
+
+def _cloud(n=3000, seed=31):
+    p, nt = synth.torus(n, seed=seed, noise=0.002)
+    a = np.full(n, 4 * np.pi ** 2 * 0.3 / n)
+    delta = oracle.clamp_radii(p, 10, 0.01, 0.1)
+    q = np.vstack([p[:300], synth.uniform_box(200, [-1.4, -1.4, -0.5], [1.4, 1.4, 0.5], seed=seed)])
+    return p, nt, a, delta, q
+
+
+@pytest.mark.parametrize("lam", [0.0, 30.0])
+def test_tree_with_every_node_open_is_the_exact_sum(lam):
+    p, nt, a, delta, q = _cloud()
+    kern = oracle.KERNEL_SCREENED if lam else oracle.KERNEL_PLAIN
+    w0, g0 = oracle.gwn(p, nt, a, q, kernel=kern, lam=lam, delta=delta)
+    w1, g1 = oracle.tree_gwn(p, nt, a, q, kernel=kern, lam=lam, beta=1e9, bucket=16, delta=delta)
+    np.testing.assert_allclose(w1, w0, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g1, g0, rtol=1e-11, atol=1e-9)
+
+
+def test_radii_larger_than_the_cloud_open_every_node():
+    """With every delta beyond the cloud's size no node can be far (the opening
+    radius is at least r + max delta), whatever beta: the exact sum again."""
+    p, nt, a, _, q = _cloud(1500)
+    big = np.full(len(p), 10.0)
+    w0 = oracle.gwn(p, nt, a, q, delta=big, grad=False)
+    w1, cnt = oracle.tree_gwn(p, nt, a, q, beta=2.0, bucket=16, delta=big, grad=False,
+                              want_count=True)
+    np.testing.assert_allclose(w1, w0, rtol=1e-12, atol=1e-12)
+    q_in = np.all(np.isin(q, p), axis=1)
+    assert np.all(cnt[~q_in] == len(p))
+
+
+def test_tree_error_within_the_first_order_bound():
+    """Far nodes hold no point within its radius of the query, so the plain
+    kernel's far field is the unsoftened dipole and the first-order bound
+    A r / (2 pi (d - r)^3) holds for the modified kernel too."""
+    p, nt, a, delta, q = _cloud()
+    w0 = oracle.gwn(p, nt, a, q, delta=delta, grad=False)
+    for beta in (2.0, 3.0):
+        w1, bnd = oracle.tree_gwn(p, nt, a, q, beta=beta, bucket=16, delta=delta, grad=False,
+                                  want_bound=True)
+        assert np.all(np.abs(w1 - w0) <= bnd + 1e-9 * (1 + np.abs(w0))), beta
+
+
+def test_group_of_one_equals_the_per_query_test():
+    p, nt, a, delta, q = _cloud(2000)
+    w1, g1, c1 = oracle.tree_gwn(p, nt, a, q, kernel=oracle.KERNEL_SCREENED, lam=30.0, beta=2.5,
+                                 bucket=32, delta=delta, want_count=True)
+    w2, g2, c2 = oracle.tree_gwn_group(p, nt, a, q, kernel=oracle.KERNEL_SCREENED, lam=30.0,
+                                       beta=2.5, bucket=32, group=1, delta=delta, want_count=True)
+    assert np.array_equal(c1, c2)
+    np.testing.assert_allclose(w2, w1, rtol=1e-12, atol=1e-12)
