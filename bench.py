@@ -347,6 +347,21 @@ def setup_and_variants(dwg, torch, dev, W, reps=3):
                 out[f"eval_points_{key}"] = {"ms": ms, "interactions_per_s": n * n / (ms / 1e3)}
             out["eval_points_basis"] = ("dwg_eval_gwn at the n points, w and grad w, all-pairs, "
                                         "call wall time incl. the reduce (median of 3)")
+        else:
+            # the Barnes-Hut path: one whole iteration (group lists, MC, kNN) each way
+            dwg.dwg_set_weights(h, torch.from_numpy(W["weights"]).to(dev))
+            dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lam"], 30, 0.1)
+            dwg.dwg_set_update(h, W["depth"], 10, dwg.DWG_UPDATE_LEVELSET)
+            dwg.dwg_set_tree(h, dwg.DWG_PATH_TREE, 0.5)
+            for reg in (dwg.DWG_REG_SOFTEN, dwg.DWG_REG_CLAMP):
+                dwg.dwg_set_regularization(h, reg, 10, 0.0, 0.0)
+                dwg.dwg_set_init(h, dwg.DWG_INIT_RANDOM, 1)
+                dwg.dwg_step(h)  # builds the lists for this kernel
+                ms = timed(lambda: dwg.dwg_step(h))
+                key = "softened" if reg == dwg.DWG_REG_SOFTEN else "modified_kernel"
+                out[f"tree_step_{key}_ms"] = ms
+            out["tree_step_basis"] = ("dwg_step on the Barnes-Hut path (theta 0.5, leaf 16, group "
+                                      "lists), one iteration, median of 3")
     finally:
         dwg.dwg_destroy(h)
     out["basis"] = "median of 3 calls, host wall time around synchronous C-ABI calls"
