@@ -75,6 +75,9 @@ def parse():
                     help="run one iteration of the workload and exit (for profiler captures)")
     ap.add_argument("--init", default="random", choices=["random", "learned", "pca", "gauss"],
                     help="initial normals of --one-step (learned: the warm-start network runs)")
+    ap.add_argument("--reg", default="soften", choices=["soften", "clamp"],
+                    help="near-field regularisation of --one-step (clamp: the modified kernel of "
+                         "Sec. 5.2 with the paper's radii)")
     return ap.parse_args()
 
 
@@ -562,6 +565,8 @@ def one_step(args):
     h = dwg.dwg_create(W["points"])
     configure(dwg, h, W, W["weights"])
     tune(dwg, h, W, args)
+    if args.reg == "clamp":
+        dwg.dwg_set_regularization(h, dwg.DWG_REG_CLAMP, 10, 0.0, 0.0)
     if args.init == "learned":
         from paper_2405_13839_gb300 import train_init
         params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)

@@ -399,11 +399,20 @@ def test_checkpoint_resume_is_bit_exact(dwglib, handle):
 
 
 @pytest.mark.parametrize("kind,n,depth,k", [("torus", 20000, 7, 10), ("box", 6000, 6, 10),
-                                            ("torus", 20000, 8, 7), ("sphere", 3000, 9, 10)])
+                                            ("torus", 20000, 8, 7), ("sphere", 3000, 9, 10),
+                                            ("cluster", 12000, 6, 10)])
 def test_knn_cell_lists_equal_the_tree_search(dwglib, handle, kind, n, depth, k):
     """The per-leaf candidate lists (knn_lists = 1) return exactly the tree
-    search's k nearest points: identical normals and iteration counts."""
-    p, _, a, eps = make_cloud(n, seed=21, kind=kind)
+    search's k nearest points: identical normals and iteration counts.  The
+    cluster case (4,000 points in a ball of radius 0.02 on a sphere) has
+    cells with more than 128 candidates, which keep the tree search."""
+    if kind == "cluster":
+        p, _, a, eps = make_cloud(n - 4000, seed=21, kind="sphere")
+        c = synth.uniform_box(4000, [-0.02] * 3, [0.02] * 3, seed=23) + np.float32([1.0, 0, 0])
+        p = np.vstack([p, c]).astype(np.float32)
+        a = np.full(n, 4 * np.pi / n, np.float32)
+    else:
+        p, _, a, eps = make_cloud(n, seed=21, kind=kind)
     n0 = synth.random_unit_normals(n, seed=22).astype(np.float32)
     res = []
     for lists in (1, 0):
