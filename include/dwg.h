@@ -185,6 +185,18 @@ int dwg_set_tree(dwg_handle h, int path, float theta);
 int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax,
                            float *delta_out);
 
+/*
+ * Failure-detection self-check (not in the paper).  Every device-side wait of
+ * the library (bulk-copy mbarriers, tensor-core commits) gives up after a
+ * bounded number of polls, records the timeout in the handle's error flag
+ * and lets the kernel return, so a stalled copy surfaces as DWG_ERR_TIMEOUT
+ * on the host with the context intact.  This call exercises that path: one
+ * CTA waits, through the evaluators' bounded wait, on an mbarrier that
+ * expects an arrival nothing sends, for `polls` polls (in [1, 2^20]); it
+ * returns DWG_ERR_TIMEOUT, clears the flag, and the handle stays usable.
+ */
+int dwg_selfcheck_wait(dwg_handle h, int polls);
+
 /* Area weights a_i > 0 (float32, n, input order, host or device). */
 int dwg_set_weights(dwg_handle h, const float *a);
 

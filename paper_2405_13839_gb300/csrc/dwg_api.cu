@@ -767,6 +767,17 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
     return DWG_OK;
 }
 
+int dwg_selfcheck_wait(dwg_handle h, int polls)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (polls < 1 || polls > (1 << 20)) return fail(h, DWG_ERR_INVALID, "polls must be in [1, 2^20]");
+    cudaSetDevice(h->device);
+    if (launch_wait_selfcheck(h, polls) != cudaSuccess)
+        return fail(h, DWG_ERR_CUDA, "self-check launch failed");
+    DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return check_device_err(h);  // DWG_ERR_TIMEOUT, and the flag is cleared
+}
+
 int dwg_voronoi_weights(dwg_handle h, int m, float *a_out)
 {
     if (!h) return DWG_ERR_INVALID;

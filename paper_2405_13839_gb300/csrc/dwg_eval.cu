@@ -75,13 +75,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Returns false when the wait gave up (about 2^24 polls, well beyond any
-// copy latency); the caller then reports DWG_ERR_TIMEOUT.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Returns false when the wait gave up (by default about 2^24 polls, well
+// beyond any copy latency); the caller then reports DWG_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  int limit = 1 << 24)
 {
-    for (int it = 0; it < (1 << 24); ++it)
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// Self-check of the wait limit: an mbarrier that expects one arrival which
+// never comes (no copy is issued), waited on with `polls` polls through the
+// evaluators' bounded wait; the timeout is recorded like a stalled copy's.
+__global__ void k_wait_selfcheck(int polls, int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, polls)) atomicOr(err, kErrTimeout);
+    __syncthreads();
+}
+
+cudaError_t launch_wait_selfcheck(Ctx *c, int polls)
+{
+    k_wait_selfcheck<<<1, 32, 0, c->stream>>>(polls, c->d_err);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -371,6 +371,9 @@ cudaError_t launch_voronoi_weights(Ctx *c, int m, double *scratch, float *a_out)
 // n floats in input order (device) or null
 cudaError_t launch_clamp_delta(Ctx *c, int k, double vmin, double vmax, float *delta_out);
 cudaError_t launch_pack_sources16(const Ctx *c);
+// one CTA waiting on an mbarrier nothing arrives at, `polls` polls (the
+// failure-detection self-check)
+cudaError_t launch_wait_selfcheck(Ctx *c, int polls);
 // per-leaf candidate lists for the faces' k nearest points (once per
 // discretisation and k; skipped when they would not fit comfortably)
 int build_cell_lists(Ctx *c);

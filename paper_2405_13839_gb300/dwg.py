@@ -104,6 +104,7 @@ def _load() -> ctypes.CDLL:
         "dwg_set_convergence": ([H, I], I),
         "dwg_set_weights": ([H, P], I),
         "dwg_voronoi_weights": ([H, I, P], I),
+        "dwg_selfcheck_wait": ([H, I], I),
         "dwg_set_regularization": ([H, I, I, F, F, P], I),
         "dwg_set_tree": ([H, I, F], I),
         "dwg_create_batch": ([P, P, I, ctypes.POINTER(H)], I),
@@ -258,6 +259,11 @@ def dwg_set_regularization(h, mode, k=10, vmin=0.0, vmax=0.0, delta_out=None):
         _check_f32(delta_out, None, "delta_out")
     return _raise(h, _lib.dwg_set_regularization(h, int(mode), int(k), float(vmin), float(vmax),
                                                  _ptr(delta_out)))
+
+
+def dwg_selfcheck_wait(h, polls=1024):
+    """Exercise the device-side wait limit; raises DWGError(DWG_ERR_TIMEOUT)."""
+    return _raise(h, _lib.dwg_selfcheck_wait(h, int(polls)))
 
 
 def dwg_voronoi_weights(h, m=15, a_out=None):

@@ -427,3 +427,32 @@ def test_knn_cell_lists_equal_the_tree_search(dwglib, handle, kind, n, depth, k)
         res.append((it, out))
     assert res[0][0] == res[1][0]
     assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_wait_limit_reports_timeout_and_the_handle_stays_usable(dwglib, handle):
+    """Failure detection without a fault: a device-side wait that nothing
+    completes gives up after its poll limit, the host sees DWG_ERR_TIMEOUT,
+    and the same handle then evaluates and orients exactly as before."""
+    p, _, a, eps = make_cloud(2000, seed=41, kind="sphere")
+    n0 = synth.random_unit_normals(2000, seed=42).astype(np.float32)
+    q = synth.uniform_box(300, [-1.5] * 3, [1.5] * 3, seed=43)
+    h = handle(p)
+    dwglib.dwg_set_weights(h, a)
+    dwglib.dwg_set_params(h, 0, eps, 0.0, 30, 0.1)
+    dwglib.dwg_set_normals(h, n0)
+    w0 = np.zeros(len(q), np.float32)
+    dwglib.dwg_eval_gwn(h, q, w0)
+    for polls in (1, 1024):
+        with pytest.raises(dwglib.DWGError) as e:
+            dwglib.dwg_selfcheck_wait(h, polls)
+        assert e.value.code == dwglib.DWG_ERR_TIMEOUT
+    w1 = np.zeros(len(q), np.float32)
+    dwglib.dwg_eval_gwn(h, q, w1)
+    assert np.array_equal(w0, w1)
+    dwglib.dwg_set_update(h, 6, 10, dwglib.DWG_UPDATE_LEVELSET)
+    dwglib.dwg_set_init(h, dwglib.DWG_INIT_GIVEN, 0, n0)
+    rc, it = dwglib.dwg_orient(h, np.zeros((2000, 3), np.float32))
+    assert rc in (dwglib.DWG_OK, dwglib.DWG_NOT_CONVERGED) and it >= 1
+    with pytest.raises(dwglib.DWGError) as e:
+        dwglib.dwg_selfcheck_wait(h, 0)
+    assert e.value.code == dwglib.DWG_ERR_INVALID
