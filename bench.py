@@ -548,11 +548,23 @@ def cpu_baseline(W, nc_hint, budget_s=12.0):
     per_q_g = tg / m
     per_q_w = tw / m
     rate = (2 * m * n) / (tg + tw)
+    cores = oracle.set_threads(0)
+    # one thread on a sample an eighth of the size
+    m1 = max(8, m // 8)
+    oracle.set_threads(1)
+    try:
+        t = time.perf_counter()
+        oracle.gwn(p, n0, a, p[rng_pts[:m1]], kernel=kern, eps=eps, lam=lam)
+        oracle.gwn(p, n0, a, C[rng_cor[:m1]], kernel=kern, eps=eps, lam=lam, grad=False)
+        rate1 = (2 * m1 * n) / (time.perf_counter() - t)
+    finally:
+        oracle.set_threads(cores)
     # extrapolated time of one iteration of the full workload
     it_s = n * per_q_g + len(C) * per_q_w
-    return {"value": rate, "unit": "interactions/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": rate, "unit": "interactions/s", "cores": cores, "kind": "oracle",
             "sample": f"w+grad at {m} sampled points and w at {m} sampled octree corners, "
                       f"each against all {n} sources (FP64, OpenMP)",
+            "single_thread": {"value": rate1, "sample": f"{m1} points and {m1} corners"},
             "extrapolated_s_per_iteration": it_s, "corners": int(len(C))}
 
 

@@ -78,6 +78,8 @@ def _load():
                                        P, i64]
             lib.dwgo_faces.restype = i64
             lib.dwgo_knn.argtypes = [i64, P, i64, P, ctypes.c_int, P]
+            lib.dwgo_set_threads.argtypes = [ctypes.c_int]
+            lib.dwgo_set_threads.restype = ctypes.c_int
             lib.dwgo_top1_mean.argtypes = [i64, P]
             lib.dwgo_top1_mean.restype = ctypes.c_double
             lib.dwgo_scatter_normals.argtypes = [i64, P, i64, P, ctypes.c_int, P, P]
@@ -185,6 +187,12 @@ def faces(leaves, depth, cube_info, keys, wc, iso):
     lib.dwgo_faces(len(L), _ptr(L), int(depth), _ptr(c), len(k), _ptr(k), _ptr(w),
                    float(iso), _ptr(out), nf)
     return out
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's parallel loops (n <= 0: the default);
+    returns the count in effect."""
+    return _load().dwgo_set_threads(int(n))
 
 
 def knn(points, queries, k):

@@ -40,6 +40,22 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads of the parallel loops (n <= 0: the OpenMP default); returns the
+ * count in effect, 1 without OpenMP */
+int dwgo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define DWGO_PI 3.14159265358979323846
 
