@@ -482,6 +482,15 @@ def run_ours(args, rank, world, local):
                           f" / {ops} FP32 ops per interaction",
             "kernel_ms": {k: round(v, 4) for k, v in kms.items()},
             "share": {k: round(v / iter_ms, 4) for k, v in kms.items()}}
+    # the same denominator measured: packed-FMA and MUFU rsqrt microbenchmarks
+    try:
+        ffma, rsq = dwg.dwg_measure_fp32_peaks(local)
+        roof["fp32_measured"] = {
+            "ffma_lane_ops_per_s": ffma, "rsqrt_per_s": rsq,
+            "derived_lane_ops_per_s": lanes, "ffma_over_derived": ffma / lanes,
+            "peak_from_measured": ffma / ops / 1e9, "frac_of_measured": achieved / (ffma / ops)}
+    except Exception as e:  # reported beside the derived peak, never instead of it
+        roof["fp32_measured"] = {"error": str(e)}
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -186,6 +186,18 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
                            float *delta_out);
 
 /*
+ * FP32 issue microbenchmarks of a device (not in the paper): the measured
+ * denominators of the evaluators' roofline.  ffma_lane_ops_per_s: FP32 lane
+ * operations per second of packed fused multiply-adds (fma.rn.f32x2; one
+ * packed instruction = 2 lane operations), 8 independent chains per thread,
+ * 8 CTAs of 256 threads per SM; rsqrt_per_s: MUFU reciprocal square roots per
+ * second, the same way.  Each is the faster of two timed launches of a few
+ * milliseconds after a warm-up.  Returns DWG_ERR_INVALID for a bad device or
+ * NULL outputs, DWG_ERR_CUDA on a CUDA error.
+ */
+int dwg_measure_fp32_peaks(int device, double *ffma_lane_ops_per_s, double *rsqrt_per_s);
+
+/*
  * Failure-detection self-check (not in the paper).  Every device-side wait of
  * the library (bulk-copy mbarriers, tensor-core commits) gives up after a
  * bounded number of polls, records the timeout in the handle's error flag

@@ -767,6 +767,15 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
     return DWG_OK;
 }
 
+int dwg_measure_fp32_peaks(int device, double *ffma_lane_ops_per_s, double *rsqrt_per_s)
+{
+    if (!ffma_lane_ops_per_s || !rsqrt_per_s) return DWG_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return DWG_ERR_INVALID;
+    return measure_fp32_peaks(device, ffma_lane_ops_per_s, rsqrt_per_s);
+}
+
 int dwg_selfcheck_wait(dwg_handle h, int polls)
 {
     if (!h) return DWG_ERR_INVALID;

@@ -107,6 +107,100 @@ cudaError_t launch_wait_selfcheck(Ctx *c, int polls)
 }
 
 // ---------------------------------------------------------------------------
+// FP32 issue microbenchmarks (the denominators of the evaluators' roofline)
+// ---------------------------------------------------------------------------
+// Packed FMA: each thread runs 8 independent chains of fma.rn.f32x2, `iters`
+// times; one packed instruction is 2 FP32 lane operations.  The chains
+// converge to a fixed point, so no value overflows; the result is written
+// only under a condition that never holds, which keeps the work.
+__global__ void __launch_bounds__(256) k_peak_ffma(int iters, float seed, float *sink)
+{
+    f2 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = pk(seed + k + threadIdx.x * 1e-3f, seed - k);
+    const f2 a = pk(0.5f, 0.5f), b = pk(0.25f, 0.25f);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma2(x[k], a, b);
+    }
+    float s0 = 0.f, s1 = 0.f, lo, hi;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        upk(x[k], lo, hi);
+        s0 += lo;
+        s1 += hi;
+    }
+    if (s0 + s1 == -1.f) sink[blockIdx.x] = s0;
+}
+
+// MUFU reciprocal square root: 8 independent chains y <- rsqrt(y) (a fixed
+// point at 1), `iters` times.
+__global__ void __launch_bounds__(256) k_peak_rsqrt(int iters, float seed, float *sink)
+{
+    float y[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) y[k] = seed + 0.1f * k + threadIdx.x * 1e-4f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) y[k] = rsqrt_mufu(y[k]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += y[k];
+    if (s == -1.f) sink[blockIdx.x] = s;
+}
+
+int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops)
+{
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (sms < 1) return DWG_ERR_CUDA;
+    const int blocks = sms * 8, threads = 256;
+    float *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = DWG_OK;
+    auto timed = [&](bool ffma, int iters, double *ms) -> bool {
+        cudaEventRecord(e0);
+        if (ffma) k_peak_ffma<<<blocks, threads>>>(iters, 1.0f, sink);
+        else k_peak_rsqrt<<<blocks, threads>>>(iters, 1.5f, sink);
+        cudaEventRecord(e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        *ms = f;
+        return true;
+    };
+    if (cudaMalloc(&sink, blocks * sizeof(float)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = DWG_ERR_CUDA;
+    } else {
+        const int it_f = 1 << 16, it_r = 1 << 13;
+        double ms_f = 0.0, ms_r = 0.0, w = 0.0;
+        // a short warm-up launch each, then two timed launches each; the
+        // shorter time is taken
+        bool ok = timed(true, it_f / 8, &w) && timed(false, it_r / 8, &w);
+        double best_f = 1e30, best_r = 1e30;
+        for (int r = 0; ok && r < 2; ++r) {
+            ok = timed(true, it_f, &ms_f) && timed(false, it_r, &ms_r);
+            best_f = std::min(best_f, ms_f);
+            best_r = std::min(best_r, ms_r);
+        }
+        if (!ok || cudaGetLastError() != cudaSuccess) {
+            rc = DWG_ERR_CUDA;
+        } else {
+            const double thr = (double)blocks * threads;
+            *ffma_lane_ops = thr * it_f * 8.0 * 2.0 / (best_f * 1e-3);
+            *rsqrt_ops = thr * it_r * 8.0 / (best_r * 1e-3);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
 // the evaluation kernel
 // ---------------------------------------------------------------------------
 constexpr int kEvalThreads = 128;  // CTA size of the default shapes

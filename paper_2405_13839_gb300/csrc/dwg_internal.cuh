@@ -374,6 +374,9 @@ cudaError_t launch_pack_sources16(const Ctx *c);
 // one CTA waiting on an mbarrier nothing arrives at, `polls` polls (the
 // failure-detection self-check)
 cudaError_t launch_wait_selfcheck(Ctx *c, int polls);
+// measured FP32 issue rates of this device: packed-FMA lane operations and
+// MUFU rsqrt per second
+int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops);
 // per-leaf candidate lists for the faces' k nearest points (once per
 // discretisation and k; skipped when they would not fit comfortably)
 int build_cell_lists(Ctx *c);

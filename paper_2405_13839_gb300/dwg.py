@@ -105,6 +105,8 @@ def _load() -> ctypes.CDLL:
         "dwg_set_weights": ([H, P], I),
         "dwg_voronoi_weights": ([H, I, P], I),
         "dwg_selfcheck_wait": ([H, I], I),
+        "dwg_measure_fp32_peaks": ([I, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)], I),
         "dwg_set_regularization": ([H, I, I, F, F, P], I),
         "dwg_set_tree": ([H, I, F], I),
         "dwg_create_batch": ([P, P, I, ctypes.POINTER(H)], I),
@@ -259,6 +261,14 @@ def dwg_set_regularization(h, mode, k=10, vmin=0.0, vmax=0.0, delta_out=None):
         _check_f32(delta_out, None, "delta_out")
     return _raise(h, _lib.dwg_set_regularization(h, int(mode), int(k), float(vmin), float(vmax),
                                                  _ptr(delta_out)))
+
+
+def dwg_measure_fp32_peaks(device=0):
+    """(packed-FMA FP32 lane operations per second, MUFU rsqrt per second)."""
+    f = ctypes.c_double()
+    r = ctypes.c_double()
+    _raise(None, _lib.dwg_measure_fp32_peaks(int(device), ctypes.byref(f), ctypes.byref(r)))
+    return f.value, r.value
 
 
 def dwg_selfcheck_wait(h, polls=1024):
