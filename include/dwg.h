@@ -186,6 +186,29 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
                            float *delta_out);
 
 /*
+ * The w_bar level set of the handle's current normals as a triangle mesh
+ * (Alg. 1's Marching Cubes step; the level set the method outputs beside the
+ * normals).  With the handle's path and settings: w at the input points and
+ * w_bar = their mean (FP64), w at the corners of the octree leaves of the
+ * dwg_set_update depth (built if needed, in either update mode), then per
+ * leaf the six-tetrahedron marching tetrahedra of the iteration: a cut
+ * tetrahedron gives one triangle (one or three corners above w_bar) or two
+ * (two above), with vertices at the linear-interpolation points of its cut
+ * edges, wound so that (v1 - v0) x (v2 - v0) points toward decreasing w
+ * (outward for outward normals).  Leaves of different sizes are not
+ * stitched (no crack fixing).
+ *   tri_out: float32 cap x 9 (x0 y0 z0 x1 y1 z1 x2 y2 z2), host or device, or
+ *            NULL to count only; order unspecified.
+ *   *count:  the number of triangles, written in every case; when it exceeds
+ *            cap nothing else is written.
+ *   iso_out: (host, may be NULL) w_bar.
+ * The iteration state is reset (as by the next dwg_orient).  Batch handles:
+ * DWG_ERR_STATE.
+ */
+int dwg_extract_level_set(dwg_handle h, float *tri_out, int64_t cap, int64_t *count,
+                          double *iso_out);
+
+/*
  * FP32 issue microbenchmarks of a device (not in the paper): the measured
  * denominators of the evaluators' roofline.  ffma_lane_ops_per_s: FP32 lane
  * operations per second of packed fused multiply-adds (fma.rn.f32x2; one

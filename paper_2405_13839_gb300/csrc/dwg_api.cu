@@ -170,6 +170,26 @@ static unsigned nblk(int64_t n, int b = 256) { return (unsigned)ceil_div(n, b); 
 // ---------------------------------------------------------------------------
 // buffers
 // ---------------------------------------------------------------------------
+// octree of the handle's depth, its corners and their partial sums
+static int ensure_levelset_buffers(Ctx *c, bool tree)
+{
+    if (c->built_depth != c->depth) ++c->bufgen;
+    int rc = build_discretization(c, c->depth);
+    if (rc) return rc;
+    const int nch_c = tree ? 1 : eval_chunks(c, c->ncorners, false);
+    if (nch_c != c->nchunks_c) ++c->bufgen;
+    c->nchunks_c = nch_c;
+    size_t need_c = (size_t)c->nchunks_c * 2 * (size_t)c->ncorners;
+    if (need_c > c->part_c_cap) {
+        cudaFree(c->d_part_c);
+        c->d_part_c = nullptr;
+        ++c->bufgen;
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_part_c, need_c * sizeof(float)));
+        c->part_c_cap = need_c;
+    }
+    return DWG_OK;
+}
+
 static int ensure_iter_buffers(Ctx *c)
 {
     const bool tree = use_tree(c);
@@ -191,21 +211,9 @@ static int ensure_iter_buffers(Ctx *c)
         c->part_p_cap = need_p;
     }
     if (c->mode == DWG_UPDATE_LEVELSET) {
-        if (c->built_depth != c->depth) ++c->bufgen;
-        int rc = build_discretization(c, c->depth);
+        int rc = ensure_levelset_buffers(c, tree);
         if (!rc) rc = build_cell_lists(c);
         if (rc) return rc;
-        const int nch_c = tree ? 1 : eval_chunks(c, c->ncorners, false);
-        if (nch_c != c->nchunks_c) ++c->bufgen;
-        c->nchunks_c = nch_c;
-        size_t need_c = (size_t)c->nchunks_c * 2 * (size_t)c->ncorners;
-        if (need_c > c->part_c_cap) {
-            cudaFree(c->d_part_c);
-            c->d_part_c = nullptr;
-            ++c->bufgen;
-            DWG_CUDA_TRY(c, cudaMalloc(&c->d_part_c, need_c * sizeof(float)));
-            c->part_c_cap = need_c;
-        }
     }
     // group form of the Barnes-Hut test: interaction lists, built once
     if (tree && c->tree_group) {
@@ -765,6 +773,79 @@ int dwg_set_regularization(dwg_handle h, int mode, int k, float vmin, float vmax
     invalidate_graph(h);
     ++h->bufgen;  // a captured graph holds the other kernels and records
     return DWG_OK;
+}
+
+static int read_state(dwg_handle h, IterState *st);
+
+int dwg_extract_level_set(dwg_handle h, float *tri_out, int64_t cap, int64_t *count,
+                          double *iso_out)
+{
+    if (!h || !count || cap < 0) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "extract the level set per cloud handle");
+    cudaSetDevice(h->device);
+    int rc = engine_prepare(h);  // buffers, tree, records from the current normals
+    if (rc) return rc;
+    const bool tree = use_tree(h);
+    if ((rc = ensure_levelset_buffers(h, tree))) return rc;
+    unsigned long long *d_cnt = nullptr;
+    float *d_tri = nullptr;
+    auto body = [&]() -> int {
+        DWG_CUDA_TRY(h, cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+        k_iter_reset<<<1, 1, 0, h->stream>>>(h->d_state, h->max_iters, nullptr);
+        LAUNCH_CHECK(h);
+        // w at the points -> w_bar; w at the corners
+        if (tree) {
+            if (launch_tree_moments(h) != cudaSuccess ||
+                launch_tree_iter(h, h->lists_p, h->d_p4, h->n, true, h->d_part_p, h->n,
+                                 h->d_state) != cudaSuccess ||
+                launch_tree_iter(h, h->lists_c, h->d_corner_pos, h->ncorners, false, h->d_part_c,
+                                 h->ncorners, h->d_state) != cudaSuccess)
+                return fail(h, DWG_ERR_CUDA, "tree launch failed");
+        } else {
+            int r = eval_launch(h, h->d_p4, h->n, true, h->nchunks_p, h->d_part_p, h->n);
+            if (!r) r = eval_launch(h, h->d_corner_pos, h->ncorners, false, h->nchunks_c,
+                                    h->d_part_c, h->ncorners);
+            if (r) return r;
+        }
+        if (launch_reduce_points(h, h->d_part_p, h->nchunks_p, h->n, h->d_p4, 1, true, h->d_wg,
+                                 h->d_wsum_blocks) != cudaSuccess ||
+            launch_iso(h) != cudaSuccess ||
+            launch_reduce_w(h, h->d_part_c, h->nchunks_c, h->ncorners, h->d_wc) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "reduce launch failed");
+        DWG_CUDA_TRY(h, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), h->stream));
+        if (launch_mc_tris(h, nullptr, 0, d_cnt) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "level-set launch failed");
+        unsigned long long nt = 0;
+        DWG_CUDA_TRY(h, cudaMemcpyAsync(&nt, d_cnt, sizeof nt, cudaMemcpyDeviceToHost, h->stream));
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        *count = (int64_t)nt;
+        if (iso_out) {
+            IterState st;
+            int r = read_state(h, &st);
+            if (r) return r;
+            *iso_out = st.iso;
+        }
+        if (!tri_out || (int64_t)nt > cap || nt == 0) return check_device_err(h);
+        float *dst = tri_out;
+        if (!is_device_ptr(tri_out)) {
+            DWG_CUDA_TRY(h, cudaMalloc(&d_tri, nt * 9 * sizeof(float)));
+            dst = d_tri;
+        }
+        DWG_CUDA_TRY(h, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), h->stream));
+        if (launch_mc_tris(h, dst, (int64_t)nt, d_cnt) != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, "level-set launch failed");
+        if (d_tri) {
+            int r = download(h, tri_out, d_tri, nt * 9 * sizeof(float));
+            if (r) return r;
+        }
+        DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return check_device_err(h);
+    };
+    rc = body();
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d_cnt);
+    cudaFree(d_tri);
+    return rc;
 }
 
 int dwg_measure_fp32_peaks(int device, double *ffma_lane_ops_per_s, double *rsqrt_per_s)

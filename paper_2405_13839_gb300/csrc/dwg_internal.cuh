@@ -377,6 +377,8 @@ cudaError_t launch_wait_selfcheck(Ctx *c, int polls);
 // measured FP32 issue rates of this device: packed-FMA lane operations and
 // MUFU rsqrt per second
 int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops);
+// the level set's triangles (count only with out null; counter: device)
+cudaError_t launch_mc_tris(Ctx *c, float *out, int64_t cap, unsigned long long *counter);
 // per-leaf candidate lists for the faces' k nearest points (once per
 // discretisation and k; skipped when they would not fit comfortably)
 int build_cell_lists(Ctx *c);

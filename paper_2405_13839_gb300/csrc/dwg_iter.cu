@@ -110,6 +110,129 @@ __device__ __forceinline__ bool tet_face(const F3 x[4], const float f[4], const 
     return true;
 }
 
+// Triangles of one tetrahedron's piece of the level set (0, 1 or 2), on the
+// same edge points as tet_face, wound so that (v1 - v0) x (v2 - v0) points
+// toward decreasing w (outward for outward normals).
+__device__ __forceinline__ int tet_tris(const F3 x[4], const float f[4], const bool ab[4],
+                                        F3 T[2][3])
+{
+    int na = (int)ab[0] + (int)ab[1] + (int)ab[2] + (int)ab[3];
+    if (na == 0 || na == 4) return 0;
+    F3 P[4];
+    int nt;
+    if (na == 1 || na == 3) {
+        bool want = (na == 1);
+        int lone = 0;
+        for (int i = 0; i < 4; ++i)
+            if (ab[i] == want) lone = i;
+        int np = 0;
+        for (int i = 0; i < 4; ++i)
+            if (i != lone) P[np++] = lerp0(x[lone], f[lone], x[i], f[i]);
+        T[0][0] = P[0]; T[0][1] = P[1]; T[0][2] = P[2];
+        nt = 1;
+    } else {
+        int a0 = -1, a1 = -1, b0 = -1, b1 = -1;
+        for (int i = 0; i < 4; ++i) {
+            if (ab[i]) { if (a0 < 0) a0 = i; else a1 = i; }
+            else { if (b0 < 0) b0 = i; else b1 = i; }
+        }
+        P[0] = lerp0(x[a0], f[a0], x[b0], f[b0]);  // a cycle of the quad
+        P[1] = lerp0(x[a0], f[a0], x[b1], f[b1]);
+        P[2] = lerp0(x[a1], f[a1], x[b1], f[b1]);
+        P[3] = lerp0(x[a1], f[a1], x[b0], f[b0]);
+        T[0][0] = P[0]; T[0][1] = P[1]; T[0][2] = P[2];
+        T[1][0] = P[0]; T[1][1] = P[2]; T[1][2] = P[3];
+        nt = 2;
+    }
+    F3 ca = {0, 0, 0}, cb = {0, 0, 0};
+    for (int i = 0; i < 4; ++i) {
+        if (ab[i]) { ca.x += x[i].x; ca.y += x[i].y; ca.z += x[i].z; }
+        else { cb.x += x[i].x; cb.y += x[i].y; cb.z += x[i].z; }
+    }
+    float ia = 1.f / na, ib = 1.f / (4 - na);
+    F3 down = {cb.x * ib - ca.x * ia, cb.y * ib - ca.y * ia, cb.z * ib - ca.z * ia};
+    F3 nrm = nt == 1 ? cross(P[1] - P[0], P[2] - P[0]) : cross(P[2] - P[0], P[3] - P[1]);
+    if (nrm.x * down.x + nrm.y * down.y + nrm.z * down.z < 0.f)
+        for (int t = 0; t < nt; ++t) {
+            F3 v = T[t][1];
+            T[t][1] = T[t][2];
+            T[t][2] = v;
+        }
+    return nt;
+}
+
+// The level set as triangles: the same corner values and decisions as
+// k_mc_faces.  Without FILL only the count; with FILL each leaf writes its
+// triangles (9 floats) at an index from the counter, those below cap.
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+    k_mc_tris(const int *__restrict__ leaf_corners, int64_t nl, const float4 *__restrict__ cpos,
+              const float *__restrict__ wc, const IterState *st, float *__restrict__ out,
+              int64_t cap, unsigned long long *counter)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    const double iso = st->iso;
+    F3 x[8];
+    float f[8];
+    bool ab[8];
+    for (int v = 0; v < 8; ++v) {
+        int ci = leaf_corners[l * 8 + v];
+        x[v] = f3(cpos[ci]);
+        double df = (double)wc[ci] - iso;
+        f[v] = (float)df;
+        ab[v] = df > 0.0;
+    }
+    F3 T[12][3];
+    int nt = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        F3 xt[4];
+        float ft[4];
+        bool at[4];
+        for (int i = 0; i < 4; ++i) {
+            int v = c_tets[t][i];
+            xt[i] = x[v];
+            ft[i] = f[v];
+            at[i] = ab[v];
+        }
+        F3 tt[2][3];
+        const int k = tet_tris(xt, ft, at, tt);
+        for (int j = 0; j < k; ++j) {
+            T[nt][0] = tt[j][0];
+            T[nt][1] = tt[j][1];
+            T[nt][2] = tt[j][2];
+            ++nt;
+        }
+    }
+    if (nt == 0) return;
+    const unsigned long long base = atomicAdd(counter, (unsigned long long)nt);
+    if (!FILL) return;
+    for (int j = 0; j < nt; ++j) {
+        const unsigned long long o = base + j;
+        if (o >= (unsigned long long)cap) break;
+        float *r = out + 9 * o;
+        for (int v = 0; v < 3; ++v) {
+            r[3 * v + 0] = T[j][v].x;
+            r[3 * v + 1] = T[j][v].y;
+            r[3 * v + 2] = T[j][v].z;
+        }
+    }
+}
+
+cudaError_t launch_mc_tris(Ctx *c, float *out, int64_t cap, unsigned long long *counter)
+{
+    const unsigned g = (unsigned)ceil_div(c->nleaves, 256);
+    if (out)
+        k_mc_tris<true><<<g, 256, 0, c->stream>>>(c->d_leaf_corners, c->nleaves, c->d_corner_pos,
+                                                  c->d_wc, c->d_state, out, cap, counter);
+    else
+        k_mc_tris<false><<<g, 256, 0, c->stream>>>(c->d_leaf_corners, c->nleaves,
+                                                   c->d_corner_pos, c->d_wc, c->d_state, nullptr,
+                                                   0, counter);
+    return cudaGetLastError();
+}
+
 // Faces of the level set.  Each face record also carries its leaf's index
 // (in the area's w) and, in the centroid's w, the position in the
 // Morton-sorted points of the face's leaf cell (found once per cut leaf):

@@ -105,6 +105,8 @@ def _load() -> ctypes.CDLL:
         "dwg_set_weights": ([H, P], I),
         "dwg_voronoi_weights": ([H, I, P], I),
         "dwg_selfcheck_wait": ([H, I], I),
+        "dwg_extract_level_set": ([H, P, I64, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double)],
+                                  I),
         "dwg_measure_fp32_peaks": ([I, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)], I),
         "dwg_set_regularization": ([H, I, I, F, F, P], I),
@@ -269,6 +271,20 @@ def dwg_measure_fp32_peaks(device=0):
     r = ctypes.c_double()
     _raise(None, _lib.dwg_measure_fp32_peaks(int(device), ctypes.byref(f), ctypes.byref(r)))
     return f.value, r.value
+
+
+def dwg_extract_level_set(h, tri_out=None):
+    """The level set of the current normals as triangles.  Returns (count,
+    iso); with tri_out (float32 (cap, 9), host or device) fills it when
+    count <= cap."""
+    cnt = ctypes.c_int64()
+    iso = ctypes.c_double()
+    cap = 0 if tri_out is None else int(tri_out.shape[0])
+    if tri_out is not None:
+        _check_f32(tri_out, 9, "tri_out")
+    _raise(h, _lib.dwg_extract_level_set(h, _ptr(tri_out), cap, ctypes.byref(cnt),
+                                         ctypes.byref(iso)))
+    return cnt.value, iso.value
 
 
 def dwg_selfcheck_wait(h, polls=1024):
