@@ -336,6 +336,18 @@ def setup_and_variants(dwg, torch, dev, W, reps=3):
             out[f"init_{name}_ms"] = timed(init)
         out["clamp_radii_ms"] = timed(lambda: dwg.dwg_set_regularization(
             h, dwg.DWG_REG_CLAMP, 10, 0.0, 0.0))
+        dwg.dwg_set_regularization(h, dwg.DWG_REG_SOFTEN)
+        # the level set of the analytic normals as triangles, into device memory
+        dwg.dwg_set_weights(h, torch.from_numpy(W["weights"]).to(dev))
+        dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lam"], 30, 0.1)
+        dwg.dwg_set_update(h, W["depth"], 10, dwg.DWG_UPDATE_LEVELSET)
+        nt_ok = np.nan_to_num(W["normals_true"]).astype(np.float32)
+        nt_ok[np.linalg.norm(nt_ok, axis=1) == 0] = [0.0, 0.0, 1.0]
+        dwg.dwg_set_init(h, dwg.DWG_INIT_GIVEN, 0, nt_ok)
+        ntri, _ = dwg.dwg_extract_level_set(h)
+        tri = torch.empty((max(ntri, 1), 9), dtype=torch.float32, device=dev)
+        out["level_set_triangles"] = int(ntri)
+        out["level_set_extract_ms"] = timed(lambda: dwg.dwg_extract_level_set(h, tri))
         if n <= 200_000:
             dwg.dwg_set_weights(h, torch.from_numpy(W["weights"]).to(dev))
             dwg.dwg_set_params(h, W["kernel"], W["eps"], W["lam"], 30, 0.1)
