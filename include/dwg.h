@@ -246,7 +246,8 @@ int dwg_set_weights(dwg_handle h, const float *a);
  * area of p_i's cell cut to the disk of radius half the largest projected
  * neighbour distance (the cut bounds the cells of points on the hull of
  * their neighbourhood and leaves interior cells of even samplings whole).
- * A neighbourhood with no extent takes the mean of the other areas.
+ * A neighbourhood with no extent takes the mean of the other areas (1, the
+ * paper's default weight, when no area is positive).
  *   m:     in [3, 31].
  *   a_out: float32 n (input order, host or device) receives the weights; may
  *          be NULL.

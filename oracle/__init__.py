@@ -449,7 +449,8 @@ def voronoi_weights(points, m=VORONOI_M):
          bounds the cells of points on the hull of their neighbourhood;
       5. a_i = its area.
     A neighbourhood with no extent (zero area) takes the mean of the positive
-    areas.  Returns float64 (n,)."""
+    areas, or 1 (the paper's default weight) when there are none.  Returns
+    float64 (n,)."""
     p = _d(points, 3)
     n = len(p)
     kk = min(int(m) + 1, n)
@@ -480,8 +481,9 @@ def voronoi_weights(points, m=VORONOI_M):
                 poly = _clip_halfplane(poly, q[j], 0.5 * r[j] * r[j])
         out[i] = _disk_polygon_area(poly, R) if len(poly) >= 3 else 0.0
     good = out > 0.0
-    if good.any() and not good.all():
-        out[~good] = out[good].mean()
+    if not good.all():
+        # none positive (one point, or copies of one): the default a_i = 1
+        out[~good] = out[good].mean() if good.any() else 1.0
     return out
 
 

@@ -916,7 +916,9 @@ __global__ void k_area_mean(const double *__restrict__ area, int64_t n, double *
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = sc[0] > 0.0 ? ss[0] / sc[0] : 0.0;
+    // no positive area at all (a cloud of one point, or all copies of one):
+    // the paper's default weight 1
+    if (threadIdx.x == 0) out[0] = sc[0] > 0.0 ? ss[0] / sc[0] : 1.0;
 }
 
 // install a_i (zero areas take the mean) into p4.w; optionally write them in

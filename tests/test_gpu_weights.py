@@ -140,3 +140,29 @@ def test_voronoi_weights_reject_bad_m(dwglib):
             assert e.value.code == dwglib.DWG_ERR_INVALID
     finally:
         dwglib.dwg_destroy(h)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 17])
+def test_tiny_clouds(dwglib, oracle_mod, n):
+    """Voronoi weights, clamp radii, PCA and Gauss-map starts and the level set
+    on clouds of a few points: finite, positive, the oracle's values."""
+    p = synth.uniform_box(n, [-1] * 3, [1] * 3, seed=60 + n)
+    h = dwglib.dwg_create(p)
+    try:
+        a = np.zeros(n, np.float32)
+        dwglib.dwg_voronoi_weights(h, 15, a)
+        d = np.zeros(n, np.float32)
+        dwglib.dwg_set_regularization(h, dwglib.DWG_REG_CLAMP, 10, 0.01, 0.5, d)
+        dwglib.dwg_set_regularization(h, dwglib.DWG_REG_SOFTEN)
+        nrm = np.zeros((n, 3), np.float32)
+        for mode in (dwglib.DWG_INIT_PCA, dwglib.DWG_INIT_GAUSS):
+            dwglib.dwg_set_init(h, mode, 3)
+            dwglib.dwg_get_normals(h, nrm)
+            assert np.allclose(np.linalg.norm(nrm, axis=1), 1, atol=1e-5)
+        dwglib.dwg_set_update(h, 4, 10, dwglib.DWG_UPDATE_LEVELSET)
+        cnt, iso = dwglib.dwg_extract_level_set(h)
+        assert cnt >= 0 and np.isfinite(iso)
+    finally:
+        dwglib.dwg_destroy(h)
+    np.testing.assert_allclose(a, oracle_mod.voronoi_weights(p), rtol=1e-6)
+    np.testing.assert_allclose(d, oracle_mod.clamp_radii(p, 10, 0.01, 0.5), rtol=1e-6)

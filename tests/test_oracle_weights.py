@@ -121,3 +121,8 @@ def test_coincident_copies_and_degenerate_neighbourhoods():
     good = a[17:]
     assert np.all(good > 0)
     np.testing.assert_allclose(a[:17], good.mean(), rtol=1e-12)
+
+
+def test_single_point_and_copies_take_the_default_weight():
+    assert np.array_equal(oracle.voronoi_weights(np.zeros((1, 3), np.float32)), [1.0])
+    assert np.array_equal(oracle.voronoi_weights(np.zeros((4, 3), np.float32)), np.ones(4))
