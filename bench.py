@@ -541,7 +541,7 @@ def run_ours(args, rank, world, local):
                 extras=extras, launches=int(round(launches_per_step * args.steps)), W=W, nc=nc)
 
 
-def cpu_baseline(W, nc_hint, budget_s=12.0):
+def cpu_baseline(W, nc_hint, budget_s=12.0, single_thread=True):
     """The oracle timed on a bounded sample: w and grad w at sampled points and
     w at sampled octree corners, against all N sources (FP64, all host cores)."""
     import oracle
@@ -570,22 +570,24 @@ def cpu_baseline(W, nc_hint, budget_s=12.0):
     per_q_w = tw / m
     rate = (2 * m * n) / (tg + tw)
     cores = oracle.set_threads(0)
-    # one thread on a sample an eighth of the size
-    m1 = max(8, m // 8)
-    oracle.set_threads(1)
-    try:
-        t = time.perf_counter()
-        oracle.gwn(p, n0, a, p[rng_pts[:m1]], kernel=kern, eps=eps, lam=lam)
-        oracle.gwn(p, n0, a, C[rng_cor[:m1]], kernel=kern, eps=eps, lam=lam, grad=False)
-        rate1 = (2 * m1 * n) / (time.perf_counter() - t)
-    finally:
-        oracle.set_threads(cores)
+    rate1, m1 = None, 0
+    if single_thread:  # one thread on a sample an eighth of the size
+        m1 = max(8, m // 8)
+        oracle.set_threads(1)
+        try:
+            t = time.perf_counter()
+            oracle.gwn(p, n0, a, p[rng_pts[:m1]], kernel=kern, eps=eps, lam=lam)
+            oracle.gwn(p, n0, a, C[rng_cor[:m1]], kernel=kern, eps=eps, lam=lam, grad=False)
+            rate1 = (2 * m1 * n) / (time.perf_counter() - t)
+        finally:
+            oracle.set_threads(cores)
     # extrapolated time of one iteration of the full workload
     it_s = n * per_q_g + len(C) * per_q_w
     return {"value": rate, "unit": "interactions/s", "cores": cores, "kind": "oracle",
             "sample": f"w+grad at {m} sampled points and w at {m} sampled octree corners, "
                       f"each against all {n} sources (FP64, OpenMP)",
-            "single_thread": {"value": rate1, "sample": f"{m1} points and {m1} corners"},
+            "single_thread": ({"value": rate1, "sample": f"{m1} points and {m1} corners"}
+                              if single_thread else None),
             "extrapolated_s_per_iteration": it_s, "corners": int(len(C))}
 
 
@@ -756,12 +758,12 @@ def main():
         W = workload(args)
         n = len(W["points"])
         for _ in range(args.warmup):
-            cpu_baseline(W, None, budget_s=1.0)
+            cpu_baseline(W, None, budget_s=1.0, single_thread=False)
         vals = []
         t0 = time.perf_counter()
         last = None
         for _ in range(args.steps):
-            last = cpu_baseline(W, None, budget_s=8.0)
+            last = cpu_baseline(W, None, budget_s=8.0, single_thread=False)
             vals.append(last["value"])
         wall = time.perf_counter() - t0
         v = statistics.median(vals)
