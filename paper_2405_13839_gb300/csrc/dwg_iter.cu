@@ -14,6 +14,14 @@
 //   k_sel_*        convergence statistic of Sec. 5.1: mean of the
 //                  ceil(n / 100) largest changes, by an exact multi-CTA radix
 //                  select on the float bits, then the loop condition.
+// and the once-per-cloud steps around it:
+//   k_cell_radius, k_cell_lists  per-leaf candidate lists of the faces'
+//                  k-nearest search (exact; built once per discretisation);
+//   k_init_pca, k_init_gauss     PCA and Gauss-map initial normals (Sec. 5.1);
+//   k_voronoi_area              local-Voronoi area weights (Sec. 5.1);
+//   k_clamp_delta               clamp radii of the modified kernel (Sec. 5.2);
+//   k_mc_tris                   the level set as triangles (the output);
+//   k_features                  patch features of the learned warm start.
 #include <algorithm>
 
 #include "dwg_internal.cuh"
