@@ -431,6 +431,8 @@ def run_ours(args, rank, world, local):
         it_list.append(it)
         rc_list.append(rc)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()  # the timed region is bracketed by barriers on both sides
     wall = time.perf_counter() - t0
     ck = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
@@ -659,6 +661,9 @@ def run_batch(args, rank=0, world=1, local=0):
         st = dwg.dwg_get_stats(hb)
         ms.append(st["ms_orient"])
         inter += st["interactions"]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ck = clocks.stop()
     o = out.cpu().numpy()
     ags = [agreement(o[off[c]:off[c + 1]], nt[off[c]:off[c + 1]]) for c in range(nc)]
