@@ -328,11 +328,14 @@ def setup_and_variants(dwg, torch, dev, W, reps=3):
             return round(statistics.median(ts), 3)
 
         out["voronoi_weights_ms"] = timed(lambda: dwg.dwg_voronoi_weights(h, 15))
+        from paper_2405_13839_gb300 import train_init
+        params = np.load(train_init.DEFAULT_WEIGHTS).astype(np.float32)
         for name, mode in (("random", dwg.DWG_INIT_RANDOM), ("pca", dwg.DWG_INIT_PCA),
-                           ("gauss", dwg.DWG_INIT_GAUSS)):
+                           ("gauss", dwg.DWG_INIT_GAUSS), ("learned", dwg.DWG_INIT_LEARNED)):
             def init(mode=mode):
-                dwg.dwg_set_init(h, mode, 1)
+                dwg.dwg_set_init(h, mode, 1, params if mode == dwg.DWG_INIT_LEARNED else None)
                 dwg.dwg_get_normals(h, nrm)
+            # learned: kNN-16 features and the tcgen05 network included
             out[f"init_{name}_ms"] = timed(init)
         out["clamp_radii_ms"] = timed(lambda: dwg.dwg_set_regularization(
             h, dwg.DWG_REG_CLAMP, 10, 0.0, 0.0))
