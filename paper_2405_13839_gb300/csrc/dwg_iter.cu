@@ -1014,7 +1014,7 @@ cudaError_t launch_clamp_delta(Ctx *c, int k, double vmin, double vmax, float *d
 // normal update (Eq. 7) and per-point change
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-    k_normal_update(int mode, int64_t n, unsigned long long *__restrict__ acc, double inv_scale,
+    k_normal_update(int mode, int64_t n, unsigned long long *__restrict__ acc,
                     const float4 *__restrict__ wg, const float4 *__restrict__ p4,
                     float4 *__restrict__ nrm, float *__restrict__ src,
                     float *__restrict__ src16, float *__restrict__ dtheta,
@@ -1027,16 +1027,19 @@ __global__ void __launch_bounds__(256)
         float4 o = nrm[i];
         float nx = o.x, ny = o.y, nz = o.z;
         if (mode == DWG_UPDATE_LEVELSET) {
+            // -sum / |sum| does not depend on the fixed-point scale: the
+            // integer sums go to float (relative rounding 2^-24) and are
+            // normalised in FP32 (FP64 runs at a small fraction of FP32 here)
             unsigned long long *a = acc + 3 * i;
-            double ax = (double)(long long)a[0] * inv_scale;
-            double ay = (double)(long long)a[1] * inv_scale;
-            double az = (double)(long long)a[2] * inv_scale;
+            const float ax = __ll2float_rn((long long)a[0]);
+            const float ay = __ll2float_rn((long long)a[1]);
+            const float az = __ll2float_rn((long long)a[2]);
             a[0] = 0ull; a[1] = 0ull; a[2] = 0ull;
-            double len = sqrt(ax * ax + ay * ay + az * az);
-            if (len > 0.0) {
-                nx = (float)(-ax / len);
-                ny = (float)(-ay / len);
-                nz = (float)(-az / len);
+            const float len = sqrtf(fmaf(az, az, fmaf(ay, ay, ax * ax)));
+            if (len > 0.f && isfinite(len)) {
+                nx = -ax / len;
+                ny = -ay / len;
+                nz = -az / len;
             }
         } else {
             float4 g = wg[i];
@@ -1528,7 +1531,7 @@ cudaError_t launch_knn_query(Ctx *c, const float4 *q, int64_t m, int k, int64_t 
 cudaError_t launch_normal_update(Ctx *c)
 {
     k_normal_update<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->stream>>>(
-        c->mode, c->n, c->d_acc, 1.0 / c->acc_scale, c->d_wg, c->d_p4, c->d_nrm, c->d_src,
+        c->mode, c->n, c->d_acc, c->d_wg, c->d_p4, c->d_nrm, c->d_src,
         c->reg_mode == DWG_REG_CLAMP ? c->d_src16 : nullptr, c->d_dtheta, c->d_dn_blocks,
         c->d_state);
     return cudaGetLastError();

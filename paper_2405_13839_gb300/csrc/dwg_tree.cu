@@ -164,20 +164,43 @@ __global__ void k_tree_records(int64_t nn, const double *A, const double *C, con
 // ---------------------------------------------------------------------------
 // moments (per iteration): M = sum a n, then m = M / (4 pi) as float
 // ---------------------------------------------------------------------------
-__global__ void k_tree_leaf_moments(const float4 *__restrict__ p4, const float4 *__restrict__ nrm,
-                                    int64_t n, int64_t nleaf, int bucket, double *M)
+// A CTA stages kMomTile consecutive points (weight and normal, 16 bytes
+// each) in shared memory with coalesced loads, then one thread per leaf sums
+// its points in Morton order in FP64.  a * n of two floats is exact in
+// double, so fma(a, n, m) rounds exactly like m + a * n.
+constexpr int kMomThreads = 128;
+constexpr int kMomTile = 2048;  // points per CTA (a multiple of every leaf size)
+
+__global__ void __launch_bounds__(kMomThreads)
+    k_tree_leaf_moments(const float4 *__restrict__ p4, const float4 *__restrict__ nrm, int64_t n,
+                        int64_t nleaf, int bucket, double *M)
 {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float4 an[kMomTile];  // (nx, ny, nz, a)
+    const int64_t p0 = (int64_t)blockIdx.x * kMomTile;
+    for (int t = threadIdx.x; t < kMomTile; t += kMomThreads) {
+        const int64_t j = p0 + t;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < n) {
+            v = nrm[j];
+            v.w = p4[j].w;
+        }
+        an[t] = v;
+    }
+    __syncthreads();
+    const int per = kMomTile / bucket;  // leaves of this tile
+    if (threadIdx.x >= per) return;
+    const int64_t b = (int64_t)blockIdx.x * per + threadIdx.x;
     if (b >= nleaf) return;
-    int64_t node = nleaf + b, j0 = b * bucket, j1 = min(j0 + bucket, n);
+    const int64_t j0 = b * bucket, j1 = min(j0 + bucket, n);
     double mx = 0.0, my = 0.0, mz = 0.0;
     for (int64_t j = j0; j < j1; ++j) {
-        double a = (double)p4[j].w;
-        float4 v = nrm[j];
-        mx = __dadd_rn(mx, __dmul_rn(a, (double)v.x));
-        my = __dadd_rn(my, __dmul_rn(a, (double)v.y));
-        mz = __dadd_rn(mz, __dmul_rn(a, (double)v.z));
+        const float4 v = an[j - p0];
+        const double a = (double)v.w;
+        mx = fma(a, (double)v.x, mx);
+        my = fma(a, (double)v.y, my);
+        mz = fma(a, (double)v.z, mz);
     }
+    const int64_t node = nleaf + b;
     M[3 * node] = mx;
     M[3 * node + 1] = my;
     M[3 * node + 2] = mz;
@@ -1143,8 +1166,9 @@ cudaError_t launch_tree_moments(Ctx *c)
 {
     const int64_t nleaf = (int64_t)1 << c->tree_levels, nn = 2 * nleaf;
     const int B = 256;
-    k_tree_leaf_moments<<<(unsigned)ceil_div(nleaf, B), B, 0, c->stream>>>(
-        c->d_p4, c->d_nrm, c->n, nleaf, c->tree_leaf, c->d_tree_M);
+    k_tree_leaf_moments<<<(unsigned)ceil_div(nleaf * c->tree_leaf, kMomTile), kMomThreads, 0,
+                          c->stream>>>(c->d_p4, c->d_nrm, c->n, nleaf, c->tree_leaf,
+                                       c->d_tree_M);
     for (int lv = c->tree_levels - 1; lv >= 0; --lv) {
         int64_t first = (int64_t)1 << lv;
         k_tree_level_moments<<<(unsigned)ceil_div(first, B), B, 0, c->stream>>>(first, c->d_tree_M);
