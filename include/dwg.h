@@ -14,6 +14,12 @@
  *      points and normalise (Eq. 7);
  *   4. stop when the mean of the largest 1% of the per-point normal changes
  *      is at most tol degrees (Sec. 5.1, "Model-independent Parameters").
+ * Around it, the options of Sec. 5.1-5.2: local-Voronoi area weights
+ * (dwg_voronoi_weights), random, PCA, Gauss-map, given or learned initial
+ * normals (dwg_set_init), the modified Poisson kernel with per-point clamp
+ * radii (dwg_set_regularization), exact or Barnes-Hut evaluation
+ * (dwg_set_tree); and the outputs: the normals (dwg_orient) and the w_bar
+ * level set as triangles (dwg_extract_level_set).
  * Every step runs in this library's CUDA kernels on one GPU; there is no CPU
  * fallback.  A call that needs the GPU and finds none returns DWG_ERR_CUDA.
  *
