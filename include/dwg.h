@@ -461,7 +461,7 @@ int dwg_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
  *                    the cell centre c (h the half-diagonal), which contain
  *                    the k nearest points of every position in the cell, so
  *                    the scan returns exactly the tree search's result; cells
- *                    with more than 128 candidates keep the tree search.
+ *                    with more than 256 candidates keep the tree search.
  *                    0: every face walks the bucket tree.  Not tuned
  *                    (dwg_autotune keeps the handle's value);
  *   w_err:           largest |w_tree - w_exact| the tuner saw on its sample

@@ -1358,7 +1358,7 @@ cudaError_t launch_knn_scatter(Ctx *c)
 // R = r_k(c') + 2 h' of c'.  R is widened by a relative 1e-4 and an absolute
 // 2^-17 of the coordinates so that float32 distance rounding cannot drop a
 // point; extra candidates cost time, never the result.
-constexpr int kCellCap = 128;
+constexpr int kCellCap = 256;
 
 __device__ __forceinline__ void cell_centre(int4 L, int d, const KnnTree &T, double cube_L,
                                             F3 &cf, double &hp)

@@ -405,7 +405,7 @@ def test_knn_cell_lists_equal_the_tree_search(dwglib, handle, kind, n, depth, k)
     """The per-leaf candidate lists (knn_lists = 1) return exactly the tree
     search's k nearest points: identical normals and iteration counts.  The
     cluster case (4,000 points in a ball of radius 0.02 on a sphere) has
-    cells with more than 128 candidates, which keep the tree search."""
+    cells with more than 256 candidates, which keep the tree search."""
     if kind == "cluster":
         p, _, a, eps = make_cloud(n - 4000, seed=21, kind="sphere")
         c = synth.uniform_box(4000, [-0.02] * 3, [0.02] * 3, seed=23) + np.float32([1.0, 0, 0])
