@@ -354,3 +354,37 @@ def test_direct_step_and_dtheta(oracle_mod):
     ang = np.degrees(np.arccos(np.clip(np.sum(n0 * r["normals"], axis=1), -1, 1)))
     np.testing.assert_allclose(r["dtheta"], ang, atol=1e-6)
     assert r["iso"] == pytest.approx(r["w"].mean(), rel=1e-14)
+
+
+def test_oracle_rounding_against_extended_precision(oracle_mod):
+    """Precision check (not an independent pin: the same definition, Eq. 2/3/5
+    and their gradients, evaluated in numpy's extended long double): on 150
+    points the FP64 oracle's w and grad w agree to 1e-12 of the sum of the
+    terms' magnitudes, for the plain and the screened kernel."""
+    import math
+    if np.finfo(np.longdouble).eps >= np.finfo(np.float64).eps:
+        pytest.skip("long double is no wider than double here")
+    p = synth.uniform_box(150, [-1] * 3, [1] * 3, seed=71).astype(np.float64)
+    nrm = synth.random_unit_normals(150, seed=72)
+    a = synth.uniform(73, 0, 150) + 0.5
+    q = synth.uniform_box(40, [-1.3] * 3, [1.3] * 3, seed=74).astype(np.float64)
+    eps = 0.05
+    L = np.longdouble
+    for lam in (0.0, 25.0):
+        kern = oracle_mod.KERNEL_SCREENED if lam else oracle_mod.KERNEL_PLAIN
+        w, g = oracle_mod.gwn(p, nrm, a, q, kernel=kern, eps=eps, lam=lam)
+        s = np.sqrt(L(lam))
+        for i in range(len(q)):
+            d = p.astype(L) - q[i].astype(L)
+            m = a.astype(L)[:, None] * nrm.astype(L) / (L(4) * L(math.pi))
+            rho2 = np.sum(d * d, axis=1) + L(eps) * L(eps)
+            rho = np.sqrt(rho2)
+            phi = np.sum(m * d, axis=1) / (rho2 * rho)
+            E = np.exp(-s * rho)
+            F = E * (1 + s * rho) if lam else np.ones_like(rho)
+            t = F * phi
+            gphi = -m / (rho2 * rho)[:, None] + 3 * (phi / rho2)[:, None] * d
+            gt = F[:, None] * gphi + ((phi * s * s * E)[:, None] * d if lam else 0)
+            assert abs(w[i] - float(t.sum())) <= 1e-12 * float(np.abs(t).sum())
+            tol = 1e-12 * float(np.abs(gt).sum(axis=0).max())
+            assert np.max(np.abs(g[i] - gt.sum(axis=0).astype(np.float64))) <= tol
