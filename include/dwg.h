@@ -136,6 +136,19 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
 int dwg_set_convergence(dwg_handle h, int rule);
 
 /*
+ * Compensation of the exact all-pairs evaluator's sums of the Eq. 2/3 and
+ * Eq. 5 terms, which are computed in FP32 here (the paper states no
+ * precision and has no counterpart to this switch).  on = 1 (the
+ * default): each thread sums 128 sources in plain FP32 and folds that tile
+ * sum into a two-sum (hi, lo) pair; on = 0: the tile sums are added in plain
+ * FP32 instead.  The switch exists to measure what the compensation buys
+ * against the FP64 oracle; it applies to the all-pairs evaluator's default
+ * shapes, softened kernel (the modified kernel and the Barnes-Hut path keep
+ * their compensated sums).  Batch handles: DWG_ERR_STATE.
+ */
+int dwg_set_compensation(dwg_handle h, int on);
+
+/*
  * Discretisation and update rule.
  *   depth: octree depth d in [1, 14] (Sec. 5.1 recommends 8-10 up to 1M
  *          points, 11-13 beyond).
@@ -522,6 +535,34 @@ int dwg_get_tuning(dwg_handle h, dwg_tuning *out);
 int dwg_set_tuning(dwg_handle h, const dwg_tuning *t);
 
 /*
+ * The Barnes-Hut hierarchy the far field of Sec. 5.2 ("Octree Traversal")
+ * walks, as built for the handle's current leaf size, opening angle and
+ * regularisation, so that a caller can check it against the points.  The
+ * hierarchy is a complete binary tree over leaves of `leaf` consecutive
+ * points in Morton order: node 1 is the root, node k has children 2k and
+ * 2k + 1, the nodes >= nodes / 2 are the leaves, and leaf b holds the sorted
+ * points [b leaf, (b + 1) leaf) (empty past n).  Outputs (host or device;
+ * each may be NULL except nodes_out and leaf_out):
+ *   nodes_out   number of node slots (2 x the number of leaves; slot 0 unused),
+ *   leaf_out    points per leaf,
+ *   perm_out    int64 n: input index of each sorted point,
+ *   area_out    double nodes: A = sum of the node's area weights,
+ *   centre_out  double nodes x 3: area-weighted centre c,
+ *   radius_out  double nodes: r, at least the largest
+ *               distance of a node's point from c (exact for a leaf; for an
+ *               inner node the largest |c_child - c| + r_child),
+ *   record_out  float nodes x 4: the traversal record (c as float, the
+ *               squared opening radius as float: (r / theta)^2, with the
+ *               modified kernel max(r / theta, r + largest clamp radius)^2;
+ *               -1 for an empty node).  A node is far for query q when
+ *               |q - c|^2 > that value.
+ * When cap < nodes only nodes_out and leaf_out are written.  Batch handles:
+ * DWG_ERR_STATE.
+ */
+int dwg_get_tree(dwg_handle h, int64_t cap, int64_t *nodes_out, int *leaf_out, int64_t *perm_out,
+                 double *area_out, double *centre_out, double *radius_out, float *record_out);
+
+/*
  * k nearest input points (1 <= k <= 32) of m query points (float32 m x 3):
  * idx_out (int64 m x k, input-order indices, nearest first; ties in squared
  * float32 distance go to the smaller input index; -1 when n < k).
@@ -539,14 +580,16 @@ int dwg_knn(dwg_handle h, const float *queries, int64_t m, int k, int64_t *idx_o
  * point of a run).  This call performs no device allocation and calls no
  * allocating library routine.
  *
- * It computes exactly what dwg_eval_gwn computes without grad_out (Eq. 2/3,
- * or Eq. 5 for DWG_KERNEL_SCREENED, softened by eps, FP32 terms with
- * compensated sums) for the cloud given here, without a handle:
+ * It computes the same w as dwg_eval_gwn with grad_out NULL (plain or
+ * screened kernel, softened by eps, FP32 terms with compensated sums) for the
+ * cloud given here, without a handle:
  *   points   float32 n x 3, normals float32 n x 3 (normalised here; zero
  *            vectors rejected), weights float32 n or NULL (a_i = 1),
  *   queries  float32 m x 3, w_out float32 m,
- * all in DEVICE memory of the current device (host pointers are rejected
- * with DWG_ERR_INVALID); kernel, eps, screening as in dwg_set_params;
+ * all in DEVICE memory of the current device (host pointers and pointers
+ * into another GPU's memory are rejected with DWG_ERR_INVALID); the caller
+ * sizes every array as stated (the library cannot check device lengths);
+ * kernel, eps, screening as in dwg_set_params;
  * stream: the cudaStream_t to run on (NULL: the legacy default stream).
  * The call returns after w_out is written (it synchronises the stream).
  *

@@ -55,6 +55,10 @@ static int fail(Ctx *c, int code, const std::string &msg)
     return code;
 }
 
+// Memory that the library's kernels may read or write directly: device
+// memory of the current device, or managed memory.  A pointer into another
+// GPU's memory is not (without peer access a kernel could not touch it); such
+// buffers, like host memory, are staged with cudaMemcpy.
 static bool is_device_ptr(const void *p)
 {
     if (!p) return false;
@@ -64,20 +68,37 @@ static bool is_device_ptr(const void *p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
-// Copy bytes from a caller buffer (host or device) into device memory.
+// Memory the host may read with memcpy (pageable or page-locked host memory).
+static bool is_host_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+// Copy bytes between a caller buffer (host memory, or device memory of any
+// GPU) and the handle's device memory; the unified address space tells the
+// copy which kind it is.
 static int upload(Ctx *c, void *dst, const void *src, size_t bytes)
 {
-    cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    DWG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+    DWG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
     return DWG_OK;
 }
 static int download(Ctx *c, void *dst, const void *src, size_t bytes)
 {
-    cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    DWG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+    DWG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
     return DWG_OK;
 }
 
@@ -673,6 +694,18 @@ int dwg_set_convergence(dwg_handle h, int rule)
     h->conv_rule = rule;
     invalidate_graph(h);
     for (dwg_ctx *c : h->clouds) dwg_set_convergence(c, rule);
+    return DWG_OK;
+}
+
+int dwg_set_compensation(dwg_handle h, int on)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "set the compensation per cloud handle");
+    if (h->compensated != (on != 0)) {
+        h->compensated = on != 0;
+        invalidate_graph(h);
+        ++h->bufgen;  // a captured graph holds the other kernels
+    }
     return DWG_OK;
 }
 
@@ -1341,6 +1374,29 @@ int dwg_get_corners(dwg_handle h, int64_t *keys_out, int64_t cap, int64_t *count
                : DWG_OK;
 }
 
+int dwg_get_tree(dwg_handle h, int64_t cap, int64_t *nodes_out, int *leaf_out, int64_t *perm_out,
+                 double *area_out, double *centre_out, double *radius_out, float *record_out)
+{
+    if (!h || !nodes_out || !leaf_out) return DWG_ERR_INVALID;
+    if (h->is_batch) return fail(h, DWG_ERR_STATE, "read the tree of a cloud handle");
+    cudaSetDevice(h->device);
+    int rc;
+    if ((rc = build_tree(h)) || (rc = tree_records(h))) return rc;
+    const int64_t nn = (int64_t)2 << h->tree_levels;
+    *nodes_out = nn;
+    *leaf_out = h->tree_leaf;
+    if (cap < nn) return DWG_OK;
+    if (perm_out && (rc = download(h, perm_out, h->d_perm, h->n * sizeof(int64_t)))) return rc;
+    if (area_out && (rc = download(h, area_out, h->d_tree_A, nn * sizeof(double)))) return rc;
+    if (centre_out && (rc = download(h, centre_out, h->d_tree_C, 3 * nn * sizeof(double))))
+        return rc;
+    if (radius_out && (rc = download(h, radius_out, h->d_tree_R, nn * sizeof(double)))) return rc;
+    if (record_out && (rc = download(h, record_out, h->d_tree_rec, nn * sizeof(float4))))
+        return rc;
+    DWG_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return check_device_err(h);
+}
+
 int dwg_mlp_features(dwg_handle h, float *X_out)
 {
     if (!h || !X_out) return DWG_ERR_INVALID;
@@ -1661,8 +1717,8 @@ int dwg_create_batch(const float *points, const int64_t *offsets, int n_clouds, 
         return DWG_ERR_INVALID;
     }
     std::vector<int64_t> off(n_clouds + 1);
-    if (is_device_ptr(offsets)) {
-        if (cudaMemcpy(off.data(), offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
+    if (!is_host_ptr(offsets)) {
+        if (cudaMemcpy(off.data(), offsets, off.size() * sizeof(int64_t), cudaMemcpyDefault) !=
             cudaSuccess) {
             set_global_error("dwg_create_batch: cannot read offsets");
             return DWG_ERR_CUDA;
@@ -1698,7 +1754,7 @@ int dwg_create_batch(const float *points, const int64_t *offsets, int n_clouds, 
             DWG_CUDA_TRY(h, cudaMalloc(&dpts, total * 3 * sizeof(float)));
             own = true;
             DWG_CUDA_TRY(h, cudaMemcpy(dpts, points, total * 3 * sizeof(float),
-                                       cudaMemcpyHostToDevice));
+                                       cudaMemcpyDefault));
         }
         h->n = total;
         for (int c = 0; c < n_clouds; ++c) {

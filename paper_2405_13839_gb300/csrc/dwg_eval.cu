@@ -210,7 +210,7 @@ constexpr int kStages = 4;
 // CLAMP the records carry delta_j^2 and the kernel is the modified one of
 // Sec. 5.2: rho^2 = max(|p_j - q|^2, delta_j^2) (no softening), and inside the
 // radius the term's gradient keeps only its -F m / rho^3 part.
-template <int P, int NT, bool GRAD, bool SCREENED, bool CLAMP = false>
+template <int P, int NT, bool GRAD, bool SCREENED, bool CLAMP = false, bool COMP = true>
 __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t ntiles_total,
                                           const float4 *__restrict__ q, int64_t m,
                                           int tiles_per_chunk, float *__restrict__ part,
@@ -350,10 +350,12 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                 }
             }
         }
-        // fold the tile sums into the compensated totals
+        // fold the tile sums into the compensated totals (COMP false: plain
+        // FP32 addition, the uncompensated form kept for precision studies)
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            two_sum_acc(hw[p], lw[p], tw[p]);
+            if (COMP) two_sum_acc(hw[p], lw[p], tw[p]);
+            else hw[p] = add2(hw[p], tw[p]);
             if (GRAD) {
                 f2 gx, gy, gz;
                 if (!SCREENED) {
@@ -365,9 +367,15 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                     gy = sub2(t1y[p], t2y[p]);
                     gz = sub2(t1z[p], t2z[p]);
                 }
-                two_sum_acc(hgx[p], lgx[p], gx);
-                two_sum_acc(hgy[p], lgy[p], gy);
-                two_sum_acc(hgz[p], lgz[p], gz);
+                if (COMP) {
+                    two_sum_acc(hgx[p], lgx[p], gx);
+                    two_sum_acc(hgy[p], lgy[p], gy);
+                    two_sum_acc(hgz[p], lgz[p], gz);
+                } else {
+                    hgx[p] = add2(hgx[p], gx);
+                    hgy[p] = add2(hgy[p], gy);
+                    hgz[p] = add2(hgz[p], gz);
+                }
             }
         }
         __syncthreads();  // every thread is done with buffer s
@@ -378,9 +386,10 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
         }
     }
     if (s_abort) {
-        // drain the copies still in flight before the CTA's shared memory goes away
+        // drain the copies still in flight before the CTA's shared memory goes
+        // away, the one whose wait gave up (tile t) included
         if (tid == 0)
-            for (int u = t + 1; u < ntiles && u < t + kStages; ++u)
+            for (int u = t; u < ntiles && u < t + kStages; ++u)
                 mbar_wait_bounded(&bar[u % kStages], (uint32_t)((u / kStages) & 1));
         __syncthreads();
     }
@@ -415,15 +424,15 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
     }
 }
 
-template <int P, int NT, bool GRAD, bool SCREENED, bool CLAMP = false>
+template <int P, int NT, bool GRAD, bool SCREENED, bool CLAMP = false, bool COMP = true>
 __global__ void __launch_bounds__(NT)
     k_gwn(const float *__restrict__ src, int64_t ntiles_total, const float4 *__restrict__ q,
           int64_t m, int tiles_per_chunk, float *__restrict__ part, int64_t stride,
           EvalParams ep, int *__restrict__ err)
 {
-    gwn_block<P, NT, GRAD, SCREENED, CLAMP>(src, ntiles_total, q, m, tiles_per_chunk, part,
-                                            stride, ep, err, (int64_t)blockIdx.x,
-                                            (int)blockIdx.y);
+    gwn_block<P, NT, GRAD, SCREENED, CLAMP, COMP>(src, ntiles_total, q, m, tiles_per_chunk,
+                                                  part, stride, ep, err, (int64_t)blockIdx.x,
+                                                  (int)blockIdx.y);
 }
 
 // Many clouds in one launch: CTA b runs work item items[b] of its cloud;
@@ -582,6 +591,11 @@ static const GwnVariant kVarClampGrad = {2, 128, {k_gwn<2, 128, true, false, tru
                                                   k_gwn<2, 128, true, true, true>}};
 static const GwnVariant kVarClampW = {4, 128, {k_gwn<4, 128, false, false, true>,
                                                k_gwn<4, 128, false, true, true>}};
+// the uncompensated fold (precision studies), default shapes only
+static const GwnVariant kVarPlainFoldGrad = {2, 128, {k_gwn<2, 128, true, false, false, false>,
+                                                      k_gwn<2, 128, true, true, false, false>}};
+static const GwnVariant kVarPlainFoldW = {4, 128, {k_gwn<4, 128, false, false, false, false>,
+                                                   k_gwn<4, 128, false, true, false, false>}};
 constexpr int kNumVarGrad = (int)(sizeof(kVarGrad) / sizeof(kVarGrad[0]));
 constexpr int kNumVarW = (int)(sizeof(kVarW) / sizeof(kVarW[0]));
 
@@ -600,11 +614,21 @@ static const GwnVariant &variant(bool grad, int v)
     return kVarW[(v >= 0 && v < kNumVarW) ? v : 0];
 }
 
-// variant v of the context's kernel (the modified kernel has one shape)
+// variant v of the context's kernel (the modified kernel and the
+// uncompensated fold have one shape each)
 static const GwnVariant &variant_of(const Ctx *c, bool grad, int v)
 {
     if (c->reg_mode == DWG_REG_CLAMP) return grad ? kVarClampGrad : kVarClampW;
+    if (!c->compensated) return grad ? kVarPlainFoldGrad : kVarPlainFoldW;
     return variant(grad, v);
+}
+
+// occupancy-cache slot of a context's variant
+static int slot_of(const Ctx *c, int v)
+{
+    if (c->reg_mode == DWG_REG_CLAMP) return 15;
+    if (!c->compensated) return 14;
+    return v;
 }
 
 // resident CTAs of a variant on the whole device (cached per device; the
@@ -633,7 +657,7 @@ static bool screened_of(const Ctx *c) { return c->kernel == DWG_KERNEL_SCREENED 
 int eval_chunks_variant(const Ctx *c, int64_t m, bool grad, int v)
 {
     const GwnVariant &V = variant_of(c, grad, v);
-    const int slot_id = c->reg_mode == DWG_REG_CLAMP ? 15 : v;
+    const int slot_id = slot_of(c, v);
     int64_t QB = (int64_t)V.nt * 2 * V.p;
     return pick_chunks(ceil_div(m, QB), c->npad / kSrcTile,
                        variant_slots(V, grad, slot_id, screened_of(c), c->device));

@@ -136,6 +136,7 @@ struct Ctx {
     float *d_src = nullptr;        // npad x kSrcFloats source records
     // modified Poisson kernel (Sec. 5.2): rho = max(|p_j - q|, delta_j)
     int reg_mode = 0;              // DWG_REG_SOFTEN or DWG_REG_CLAMP
+    bool compensated = true;       // two-sum fold of the all-pairs tile sums
     float *d_delta2 = nullptr;     // n: delta_j^2, sorted order
     float *d_src16 = nullptr;      // npad x kSrcFloatsClamp records (DWG_REG_CLAMP)
     float4 *d_nrm = nullptr;       // current normals, sorted

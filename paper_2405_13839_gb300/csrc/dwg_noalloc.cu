@@ -97,14 +97,18 @@ __global__ void k_noalloc_queries(const float *__restrict__ v, int64_t m, float4
     out[i] = make_float4(x, y, z, 0.f);
 }
 
-static bool on_device(const void *p)
+// true for managed memory and for device memory of device `dev`; a pointer
+// into another GPU's memory is refused (without peer access the kernels below
+// could not read it)
+static bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace dwg
@@ -127,13 +131,14 @@ extern "C" int dwg_eval_w_noalloc(const float *points, const float *normals, con
         return noalloc_fail(DWG_ERR_INVALID, "dwg_eval_w_noalloc: unknown kernel");
     if (!(eps > 0.f) || !isfinite(eps) || !(screening >= 0.f) || !isfinite(screening))
         return noalloc_fail(DWG_ERR_INVALID, "dwg_eval_w_noalloc: need eps > 0, screening >= 0");
-    if (!on_device(points) || !on_device(normals) || !on_device(queries) || !on_device(w_out) ||
-        (weights && !on_device(weights)))
-        return noalloc_fail(DWG_ERR_INVALID,
-                            "dwg_eval_w_noalloc: every array must be device memory");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(DWG_ERR_CUDA, cudaGetErrorString(e));
+    if (!on_device(points, dev) || !on_device(normals, dev) || !on_device(queries, dev) ||
+        !on_device(w_out, dev) || (weights && !on_device(weights, dev)))
+        return noalloc_fail(DWG_ERR_INVALID,
+                            "dwg_eval_w_noalloc: every array must be device memory of the "
+                            "current device");
     unsigned char *base = nullptr;
     int rc = noalloc_scratch(dev, &base);
     if (rc) return rc;

@@ -102,6 +102,7 @@ def _load() -> ctypes.CDLL:
         "dwg_set_params": ([H, I, F, F, I, F], I),
         "dwg_set_update": ([H, I, I, I], I),
         "dwg_set_convergence": ([H, I], I),
+        "dwg_set_compensation": ([H, I], I),
         "dwg_set_weights": ([H, P], I),
         "dwg_voronoi_weights": ([H, I, P], I),
         "dwg_selfcheck_wait": ([H, I], I),
@@ -124,6 +125,7 @@ def _load() -> ctypes.CDLL:
         "dwg_get_trace": ([H, P, P, P, P, I, ctypes.POINTER(I)], I),
         "dwg_get_leaves": ([H, P, I64, ctypes.POINTER(I64)], I),
         "dwg_get_corners": ([H, P, I64, ctypes.POINTER(I64)], I),
+        "dwg_get_tree": ([H, I64, ctypes.POINTER(I64), ctypes.POINTER(I), P, P, P, P, P], I),
         "dwg_knn": ([H, P, I64, I, P], I),
         "dwg_profile_step": ([H, P, I, ctypes.POINTER(I)], I),
         "dwg_eval_w_noalloc": ([P, P, P, I64, P, I64, I, F, F, P, P], I),
@@ -239,6 +241,11 @@ def dwg_set_params(h, kernel, eps, screening, max_iters, tol):
 
 def dwg_set_convergence(h, rule):
     return _raise(h, _lib.dwg_set_convergence(h, int(rule)))
+
+
+def dwg_set_compensation(h, on):
+    """1: two-sum fold of the all-pairs tile sums (default); 0: plain FP32."""
+    return _raise(h, _lib.dwg_set_compensation(h, int(on)))
 
 
 def dwg_set_update(h, depth, knn=10, mode=DWG_UPDATE_LEVELSET):
@@ -378,6 +385,26 @@ def dwg_get_corners(h):
     return out
 
 
+def dwg_get_tree(h, n):
+    """The Barnes-Hut hierarchy as built (dict of numpy arrays: perm, area,
+    centre, radius, record; leaf size and node count); n = number of points."""
+    nodes = ctypes.c_int64()
+    leaf = ctypes.c_int()
+    _raise(h, _lib.dwg_get_tree(h, 0, ctypes.byref(nodes), ctypes.byref(leaf), None, None, None,
+                                None, None))
+    nn = nodes.value
+    perm = np.zeros(n, np.int64)
+    area = np.zeros(nn)
+    centre = np.zeros((nn, 3))
+    radius = np.zeros(nn)
+    record = np.zeros((nn, 4), np.float32)
+    _raise(h, _lib.dwg_get_tree(h, nn, ctypes.byref(nodes), ctypes.byref(leaf), perm.ctypes.data,
+                                area.ctypes.data, centre.ctypes.data, radius.ctypes.data,
+                                record.ctypes.data))
+    return dict(nodes=nn, leaf=leaf.value, perm=perm, area=area, centre=centre, radius=radius,
+                record=record)
+
+
 def dwg_knn(h, queries, k, idx_out):
     _check_f32(queries, 3, "queries")
     return _raise(h, _lib.dwg_knn(h, _ptr(queries), int(queries.shape[0]), int(k),
@@ -398,12 +425,26 @@ def dwg_profile_step(h):
 
 def dwg_eval_w_noalloc(points, normals, weights, queries, w_out, kernel=DWG_KERNEL_PLAIN,
                        eps=1e-3, screening=0.0, stream=None):
-    """w at queries without any device allocation (all arrays CUDA tensors)."""
+    """w at queries without any device allocation (all arrays CUDA tensors of
+    one device; the library refuses host memory and other devices' memory)."""
     _check_f32(points, 3, "points")
     _check_f32(normals, 3, "normals")
     _check_f32(queries, 3, "queries")
+    _check_f32(w_out, None, "w_out")
+    n, m = int(points.shape[0]), int(queries.shape[0])
+    if int(normals.shape[0]) != n:
+        raise ValueError(f"normals has {int(normals.shape[0])} rows, points has {n}")
+    if w_out.ndim != 1 or int(w_out.shape[0]) != m:
+        raise ValueError(f"w_out must have shape ({m},), got {tuple(w_out.shape)}")
+    arrays = [points, normals, queries, w_out]
     if weights is not None:
         _check_f32(weights, None, "weights")
+        if weights.ndim != 1 or int(weights.shape[0]) != n:
+            raise ValueError(f"weights must have shape ({n},), got {tuple(weights.shape)}")
+        arrays.append(weights)
+    devices = {str(getattr(a, "device", "cpu")) for a in arrays}
+    if len(devices) != 1:
+        raise ValueError(f"all arrays must be on one device, got {sorted(devices)}")
     rc = _lib.dwg_eval_w_noalloc(_ptr(points), _ptr(normals), _ptr(weights),
                                  int(points.shape[0]), _ptr(queries), int(queries.shape[0]),
                                  int(kernel), float(eps), float(screening), _ptr(w_out), stream)

@@ -50,3 +50,40 @@ def test_binding_constants_match_the_header(dwglib):
     for name, value in consts.items():
         if hasattr(dwglib, name):
             assert getattr(dwglib, name) == int(value), name
+
+
+def test_noalloc_binding_checks_shapes_before_the_call(dwglib):
+    """Mismatched lengths and dtypes are refused by the binding before the
+    library is called (the library cannot check device array lengths)."""
+    import numpy as np
+    p = np.zeros((8, 3), np.float32)
+    q = np.zeros((5, 3), np.float32)
+    w = np.zeros(5, np.float32)
+    cases = [
+        (p, np.zeros((7, 3), np.float32), None, q, w),          # normals short
+        (p, p, np.ones(7, np.float32), q, w),                   # weights short
+        (p, p, None, q, np.zeros(4, np.float32)),               # w_out short
+        (p, p, None, q, np.zeros((5, 1), np.float32)),          # w_out not 1-D
+    ]
+    for args in cases:
+        with pytest.raises(ValueError):
+            dwglib.dwg_eval_w_noalloc(*args, eps=0.01)
+    with pytest.raises(TypeError):                              # w_out not float32
+        dwglib.dwg_eval_w_noalloc(p, p, None, q, np.zeros(5, np.float64), eps=0.01)
+
+
+def test_noalloc_binding_refuses_mixed_devices(dwglib):
+    torch = pytest.importorskip("torch")
+    import numpy as np
+
+    class FakeDev:
+        """A float32 array that reports another device (no GPU needed)."""
+        def __init__(self, a, device):
+            self._a, self.device = a, device
+            self.dtype, self.shape, self.ndim = a.dtype, a.shape, a.ndim
+
+    p = torch.zeros((8, 3), dtype=torch.float32)
+    q = torch.zeros((5, 3), dtype=torch.float32)
+    w = FakeDev(np.zeros(5, np.float32), "cuda:1")
+    with pytest.raises(ValueError, match="one device"):
+        dwglib.dwg_eval_w_noalloc(p, p, None, q, w, eps=0.01)
