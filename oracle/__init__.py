@@ -330,6 +330,70 @@ def tree_gwn_group(points, normals, weights, queries, kernel=KERNEL_PLAIN, eps=0
     return tuple(out) if len(out) > 1 else w
 
 
+def kernel_derivative_norms(rho, lam=0.0):
+    """Operator norms of the second and third derivative tensors of the
+    potential whose negative directional derivative is the term of Eq. 2/3
+    (lam = 0) or Eq. 5 (lam > 0), at distance rho.
+
+    With G(rho) = exp(-s rho) / rho, s = sqrt(lam), a source's term is
+    t(q) = -<m, grad G(p - q)>: grad G(x) = -F(rho) x / rho^3 with
+    F = exp(-s rho)(1 + s rho), the factor of Eq. 5 (F = 1 for lam = 0), and
+    grad_q t = Hess G(p - q) m.  For a radial function with derivatives
+    G1, G2, G3 (first to third) the Hessian has eigenvalues G2 (radial) and
+    G1 / rho (tangential, twice); the third-derivative tensor is
+    a xh xh xh + b (delta_ij xh_k + delta_ik xh_j + delta_jk xh_i), xh the unit
+    direction, with b = (G2 - G1 / rho) / rho and a = G3 - 3 G2 / rho +
+    3 G1 / rho^2.  As a symmetric trilinear form its norm is the largest
+    |T(u, u, u)| over unit u, i.e. the maximum over c = xh.u in [0, 1] of
+    |a c^3 + 3 b c|: at c = 1 (|G3|) or at c^2 = -b / a.  Here, with
+    u = s rho and e = exp(-u):
+      G2 = e (2 + 2u + u^2) / rho^3,  G1 / rho = -e (1 + u) / rho^3,
+      G3 = -e (6 + 6u + 3u^2 + u^3) / rho^4,
+      b = e (3 + 3u + u^2) / rho^4,   a = -e (15 + 15u + 6u^2 + u^3) / rho^4.
+    Both norms decrease with rho.  Softening (the regulariser of Sec. 3, read
+    as rho^2 = |x|^2 + eps^2) makes the potential the restriction of the 4D
+    radial function G(|(x, eps)|) to a hyperplane, so the same norms at
+    rho = sqrt(|x|^2 + eps^2) bound it.
+    Returns (hessian_norm, third_norm) as arrays."""
+    rho = np.asarray(rho, np.float64)
+    s = math.sqrt(max(lam, 0.0))
+    u = s * rho
+    e = np.exp(-u)
+    g2 = e * (2 + 2 * u + u * u) / rho ** 3
+    g1r = e * (1 + u) / rho ** 3                  # |G1| / rho
+    g3 = e * (6 + 6 * u + 3 * u * u + u ** 3) / rho ** 4
+    b = e * (3 + 3 * u + u * u) / rho ** 4
+    a = -e * (15 + 15 * u + 6 * u * u + u ** 3) / rho ** 4
+    c2 = np.clip(-b / a, 0.0, 1.0)
+    inner = np.abs(np.sqrt(c2) * (a * c2 + 3 * b))
+    return np.maximum(g2, g1r), np.maximum(g3, inner)
+
+
+def far_field_bound(mass, r, d, lam=0.0, eps=0.0):
+    """First-order remainder bound of the Barnes-Hut far field (Sec. 5.2,
+    "Octree Traversal"): a node whose sources p_j lie within r of the point c
+    where its dipole sum M = sum m_j is placed, at distance d > r from the
+    query, is replaced by one term at c.  By the mean-value theorem on each
+    source's term the error is at most
+      |dw|      <= (mass / 4 pi) r H(rho0),
+      |d grad|  <= (mass / 4 pi) r T(rho0),
+    with mass = sum_j a_j |n_j| (so sum |m_j| = mass / 4 pi), H and T the
+    norms of kernel_derivative_norms at the nearest distance any segment
+    [c, p_j] comes to the query, rho0 = sqrt((d - r)^2 + eps^2).  For
+    lam = 0 and eps = 0 these are A r / (2 pi (d - r)^3) and
+    3 A r / (2 pi (d - r)^4).  The bound needs no property of c beyond
+    |p_j - c| <= r.  Returns (w_bound, grad_bound); infinite where d <= r."""
+    mass = np.asarray(mass, np.float64)
+    r = np.asarray(r, np.float64)
+    d = np.asarray(d, np.float64)
+    gap = d - r
+    ok = gap > 0
+    rho0 = np.sqrt(np.where(ok, gap, 1.0) ** 2 + eps * eps)
+    H, T = kernel_derivative_norms(rho0, lam)
+    k = mass * r / (4 * np.pi)
+    return (np.where(ok, k * H, np.inf), np.where(ok, k * T, np.inf))
+
+
 # ----------------------------------------------------------------------------
 # Initial normals (Sec. 5.1, "Normal Initialization")
 # ----------------------------------------------------------------------------
