@@ -83,3 +83,31 @@ def test_mean_change_rule_stops_at_the_first_small_mean_change(oracle_mod):
     assert stop is not None and r["iters"] == stop and r["converged"]
     np.testing.assert_array_equal(r["normals"], cur)
     assert agreement(r["normals"], nt) >= 0.99
+
+
+@pytest.mark.parametrize("noise", [0.0, 0.005])
+def test_top1_statistic_plateaus_above_the_tolerance(oracle_mod, noise):
+    """On a 5,000-point torus, clean or with 0.5 % noise, the level-set update
+    of Eq. 7 settles -- every normal agrees with the analytic one and the mean
+    change over all points (the measure of Fig. 6) falls far below the chord
+    of 0.1 deg -- while the mean change of the 1 % most-changed points (the
+    rule of Sec. 5.1) stays at a few tenths of a degree: a handful of points
+    keep switching between nearby marching-cubes faces' k-nearest sets.  The
+    top-1 % rule at 0.1 deg is then never met, which is why the benchmarks on
+    noisy and large clouds stop on the Fig. 6 measure."""
+    n, depth = 5000, 6
+    p, nt = synth.torus(n, seed=0, noise=noise)
+    area = 4 * np.pi ** 2 * 0.3
+    a = np.full(n, area / n)
+    prm = oracle_mod.params(eps=synth.default_eps(area, n), depth=depth, max_iters=1, tol=0.1)
+    cur = synth.random_unit_normals(n, seed=1)
+    top, mean = [], []
+    for _ in range(25):
+        r = oracle_mod.iterate(p, a, cur, prm)
+        top.append(oracle_mod.top1_mean(r["dtheta"]))
+        mean.append(np.mean(np.linalg.norm(r["normals"] - cur, axis=1)))
+        cur = r["normals"]
+    chord = 2 * np.sin(np.radians(0.1) / 2)
+    assert agreement(cur, nt) == 1.0
+    assert max(mean[18:]) <= 0.2 * chord
+    assert 0.2 <= min(top[18:]) and max(top[18:]) <= 2.0, top[18:]
