@@ -26,6 +26,9 @@ struct dwg_ctx : public Ctx {
     int64_t nit_p = 0, nit_c = 0;
     IterState **d_states = nullptr;
     bool eps_given = false;
+    // fork / join of the clouds' chains in a batch iteration (each cloud runs
+    // on its own stream, so the graph holds one branch per cloud)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static std::mutex g_err_mu;
@@ -525,6 +528,8 @@ void dwg_destroy(dwg_handle h)
     for (void *p : bufs) cudaFree(p);
     free_lists(h->lists_p);
     free_lists(h->lists_c);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -1113,6 +1118,7 @@ int dwg_step(dwg_handle h, float *w_out, float *grad_out, float *dtheta_out, dou
     if ((rc = check_device_err(h))) return rc;
     if (iso_out) *iso_out = st.iso;
     if (stat_out) *stat_out = st.stat;
+    if (!w_out && !grad_out && !dtheta_out) return DWG_OK;
     float *d = nullptr;
     DWG_CUDA_TRY(h, cudaMalloc(&d, h->n * 4 * sizeof(float)));
     if (w_out || grad_out) {
@@ -1613,7 +1619,11 @@ static int batch_tables(dwg_ctx *h)
     return DWG_OK;
 }
 
-// one iteration of every cloud
+// one iteration of every cloud: the all-pairs sums of every cloud in one
+// launch, then each cloud's chain (tree sums, reduce, iso-value, level set,
+// kNN scatter, update, convergence) on the cloud's own stream, forked from
+// and joined back into the batch stream, so that the chains of different
+// clouds run concurrently (one graph branch per cloud)
 static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
 {
     bool scr = h->kernel == DWG_KERNEL_SCREENED && h->lambda > 0.f;
@@ -1622,8 +1632,14 @@ static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
         launch_gwn_batch(h->d_bcl_c, h->d_bit_c, h->nit_c, false, scr, h->d_err, h->stream) !=
             cudaSuccess)
         return fail(h, DWG_ERR_CUDA, "batched gwn launch failed");
+    if (!h->ev_fork)
+        DWG_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    DWG_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
     for (dwg_ctx *c : h->clouds) {
-        c->stream = h->stream;
+        if (!c->ev_join)
+            DWG_CUDA_TRY(h, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        DWG_CUDA_TRY(h, cudaStreamWaitEvent(c->own_stream, h->ev_fork, 0));
+        c->stream = c->own_stream;
         if (use_tree(c)) {
             if (launch_tree_moments(c) != cudaSuccess ||
                 launch_tree_iter(c, c->lists_p, c->d_p4, c->n, true, c->d_part_p, c->n,
@@ -1643,6 +1659,8 @@ static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
             return fail(h, DWG_ERR_CUDA, "level-set launch failed");
         if (launch_normal_update(c) != cudaSuccess || launch_select(c, cond, 0) != cudaSuccess)
             return fail(h, DWG_ERR_CUDA, "update launch failed");
+        DWG_CUDA_TRY(h, cudaEventRecord(c->ev_join, c->stream));
+        DWG_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, c->ev_join, 0));
     }
     k_batch_cond<<<1, 256, 0, h->stream>>>(h->d_states, (int)h->clouds.size(), h->max_iters, cond);
     LAUNCH_CHECK(h);

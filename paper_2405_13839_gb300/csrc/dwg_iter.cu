@@ -1058,14 +1058,16 @@ __global__ void __launch_bounds__(256)
         dn = (double)sqrtf(ex * ex + ey * ey + ez * ez);
         nrm[i] = make_float4(nx, ny, nz, 0.f);
         float c = p4[i].w * (float)(1.0 / (4.0 * kPi));
-        float4 *r = reinterpret_cast<float4 *>(src + i * kSrcFloats);
         float mx = c * nx, my = c * ny, mz = c * nz;
-        r[1] = make_float4(r[1].x, r[1].y, mx, mx);
-        r[2] = make_float4(my, my, mz, mz);
+        // only the moment words of the record change: (mx, mx) as one 8-byte
+        // store (no read of the position words), then (my, my, mz, mz)
+        float *r = src + i * kSrcFloats;
+        *reinterpret_cast<float2 *>(r + 6) = make_float2(mx, mx);
+        *reinterpret_cast<float4 *>(r + 8) = make_float4(my, my, mz, mz);
         if (src16) {  // the modified kernel's records (same first 12 floats)
-            float4 *r16 = reinterpret_cast<float4 *>(src16 + i * kSrcFloatsClamp);
-            r16[1] = make_float4(r16[1].x, r16[1].y, mx, mx);
-            r16[2] = make_float4(my, my, mz, mz);
+            float *r16 = src16 + i * kSrcFloatsClamp;
+            *reinterpret_cast<float2 *>(r16 + 6) = make_float2(mx, mx);
+            *reinterpret_cast<float4 *>(r16 + 8) = make_float4(my, my, mz, mz);
         }
     }
     __shared__ double sh[256];

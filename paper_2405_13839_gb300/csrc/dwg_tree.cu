@@ -435,6 +435,95 @@ struct GrpAcc {
     f2 hw, lw, hgx, lgx, hgy, lgy, hgz, lgz;
 };
 
+// One query pair's plain FP32 sums over the records of a flush.
+struct PairSums {
+    f2 tw, t1x, t1y, t1z, t2x, t2y, t2z;
+};
+
+__device__ __forceinline__ void pair_zero(PairSums &T)
+{
+    T.tw = T.t1x = T.t1y = T.t1z = T.t2x = T.t2y = T.t2z = 0ull;  // +0.0f in both lanes
+}
+
+// One record (r0 = (x,x)(y,y), r1 = (z,z)(mx,mx), r2v = (my,my)(mz,mz), d2c the
+// modified kernel's (d2,d2)) against one query pair.
+template <bool GRAD, bool SCREENED, bool CLAMP>
+__device__ __forceinline__ void pair_term(PairSums &T, const ulonglong2 &r0, const ulonglong2 &r1,
+                                          const ulonglong2 &r2v, f2 d2c, f2 qx, f2 qy, f2 qz,
+                                          f2 eps2, f2 three, f2 sv, f2 s2v, f2 nl2e)
+{
+    f2 dx = sub2(r0.x, qx);
+    f2 dy = sub2(r0.y, qy);
+    f2 dz = sub2(r1.x, qz);
+    f2 rr = fma2(dx, dx, eps2);
+    rr = fma2(dy, dy, rr);
+    rr = fma2(dz, dz, rr);
+    const f2 r2raw = rr;
+    if (CLAMP) rr = max2(rr, d2c);
+    f2 inv = rsqrt2(rr);
+    f2 md = mul2(r1.y, dx);
+    md = fma2(r2v.x, dy, md);
+    md = fma2(r2v.y, dz, md);
+    f2 i2 = mul2(inv, inv);
+    f2 i3 = mul2(i2, inv);
+    if (!SCREENED) {
+        if (GRAD) {
+            f2 phi = mul2(md, i3);
+            T.tw = add2(T.tw, phi);
+            f2 c = mul2(phi, i2);
+            if (CLAMP) c = keep_ge(c, r2raw, d2c);
+            T.t1x = fma2(c, dx, T.t1x);
+            T.t1y = fma2(c, dy, T.t1y);
+            T.t1z = fma2(c, dz, T.t1z);
+            T.t2x = fma2(r1.y, i3, T.t2x);
+            T.t2y = fma2(r2v.x, i3, T.t2y);
+            T.t2z = fma2(r2v.y, i3, T.t2z);
+        } else {
+            T.tw = fma2(md, i3, T.tw);
+        }
+    } else {
+        f2 rho = mul2(rr, inv);
+        f2 e = ex22(mul2(rho, nl2e));
+        f2 F = fma2(e, mul2(rho, sv), e);
+        f2 phi = mul2(md, i3);
+        T.tw = fma2(F, phi, T.tw);
+        if (GRAD) {
+            f2 fi3 = mul2(F, i3);
+            f2 cc = fma2(three, mul2(F, i2), mul2(s2v, e));
+            f2 c = mul2(phi, cc);
+            if (CLAMP) c = keep_ge(c, r2raw, d2c);
+            T.t1x = fma2(c, dx, T.t1x);
+            T.t1y = fma2(c, dy, T.t1y);
+            T.t1z = fma2(c, dz, T.t1z);
+            T.t2x = fma2(r1.y, fi3, T.t2x);
+            T.t2y = fma2(r2v.x, fi3, T.t2y);
+            T.t2z = fma2(r2v.y, fi3, T.t2z);
+        }
+    }
+}
+
+// a flush's plain sums folded into the compensated totals
+template <bool GRAD, bool SCREENED>
+__device__ __forceinline__ void pair_fold(GrpAcc &A, const PairSums &T, f2 three)
+{
+    two_sum_acc(A.hw, A.lw, T.tw);
+    if (GRAD) {
+        f2 gx, gy, gz;
+        if (!SCREENED) {
+            gx = sub2(mul2(three, T.t1x), T.t2x);
+            gy = sub2(mul2(three, T.t1y), T.t2y);
+            gz = sub2(mul2(three, T.t1z), T.t2z);
+        } else {
+            gx = sub2(T.t1x, T.t2x);
+            gy = sub2(T.t1y, T.t2y);
+            gz = sub2(T.t1z, T.t2z);
+        }
+        two_sum_acc(A.hgx, A.lgx, gx);
+        two_sum_acc(A.hgy, A.lgy, gy);
+        two_sum_acc(A.hgz, A.lgz, gz);
+    }
+}
+
 // every lane: its two queries against `cnt` records of `buf`, the flush's
 // plain FP32 sums folded into the compensated totals
 // With CLAMP the records are four 16-byte words, the fourth (d2, d2, 0, 0)
@@ -446,84 +535,22 @@ __device__ __forceinline__ void grp_flush(GrpAcc &A, const float4 *buf, int cnt,
     constexpr int RW = CLAMP ? 4 : 3;
     const f2 eps2 = pk(ep.eps2, ep.eps2);
     const f2 three = pk(3.f, 3.f);
-    const f2 zero = pk(0.f, 0.f);
     const f2 sv = pk(ep.s, ep.s);
     const f2 s2v = pk(ep.s2, ep.s2);
     const f2 nl2e = pk(ep.nl2e_s, ep.nl2e_s);
-    f2 tw = zero, t1x = zero, t1y = zero, t1z = zero, t2x = zero, t2y = zero, t2z = zero;
+    PairSums T;
+    pair_zero(T);
     const ulonglong2 *rec = reinterpret_cast<const ulonglong2 *>(buf);
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
-        const ulonglong2 r0 = rec[RW * j + 0];  // (x,x) (y,y)
-        const ulonglong2 r1 = rec[RW * j + 1];  // (z,z) (mx,mx)
-        const ulonglong2 r2v = rec[RW * j + 2]; // (my,my) (mz,mz)
-        f2 d2c = zero;
-        if (CLAMP) d2c = rec[RW * j + 3].x;     // (d2,d2)
-        f2 dx = sub2(r0.x, qx);
-        f2 dy = sub2(r0.y, qy);
-        f2 dz = sub2(r1.x, qz);
-        f2 rr = fma2(dx, dx, eps2);
-        rr = fma2(dy, dy, rr);
-        rr = fma2(dz, dz, rr);
-        const f2 r2raw = rr;
-        if (CLAMP) rr = max2(rr, d2c);
-        f2 inv = rsqrt2(rr);
-        f2 md = mul2(r1.y, dx);
-        md = fma2(r2v.x, dy, md);
-        md = fma2(r2v.y, dz, md);
-        f2 i2 = mul2(inv, inv);
-        f2 i3 = mul2(i2, inv);
-        if (!SCREENED) {
-            if (GRAD) {
-                f2 phi = mul2(md, i3);
-                tw = add2(tw, phi);
-                f2 c = mul2(phi, i2);
-                if (CLAMP) c = keep_ge(c, r2raw, d2c);
-                t1x = fma2(c, dx, t1x);
-                t1y = fma2(c, dy, t1y);
-                t1z = fma2(c, dz, t1z);
-                t2x = fma2(r1.y, i3, t2x);
-                t2y = fma2(r2v.x, i3, t2y);
-                t2z = fma2(r2v.y, i3, t2z);
-            } else {
-                tw = fma2(md, i3, tw);
-            }
-        } else {
-            f2 rho = mul2(rr, inv);
-            f2 e = ex22(mul2(rho, nl2e));
-            f2 F = fma2(e, mul2(rho, sv), e);
-            f2 phi = mul2(md, i3);
-            tw = fma2(F, phi, tw);
-            if (GRAD) {
-                f2 fi3 = mul2(F, i3);
-                f2 cc = fma2(three, mul2(F, i2), mul2(s2v, e));
-                f2 c = mul2(phi, cc);
-                if (CLAMP) c = keep_ge(c, r2raw, d2c);
-                t1x = fma2(c, dx, t1x);
-                t1y = fma2(c, dy, t1y);
-                t1z = fma2(c, dz, t1z);
-                t2x = fma2(r1.y, fi3, t2x);
-                t2y = fma2(r2v.x, fi3, t2y);
-                t2z = fma2(r2v.y, fi3, t2z);
-            }
-        }
+        const ulonglong2 r0 = rec[RW * j + 0];
+        const ulonglong2 r1 = rec[RW * j + 1];
+        const ulonglong2 r2v = rec[RW * j + 2];
+        const f2 d2c = CLAMP ? rec[RW * j + 3].x : 0ull;
+        pair_term<GRAD, SCREENED, CLAMP>(T, r0, r1, r2v, d2c, qx, qy, qz, eps2, three, sv, s2v,
+                                         nl2e);
     }
-    two_sum_acc(A.hw, A.lw, tw);
-    if (GRAD) {
-        f2 gx, gy, gz;
-        if (!SCREENED) {
-            gx = sub2(mul2(three, t1x), t2x);
-            gy = sub2(mul2(three, t1y), t2y);
-            gz = sub2(mul2(three, t1z), t2z);
-        } else {
-            gx = sub2(t1x, t2x);
-            gy = sub2(t1y, t2y);
-            gz = sub2(t1z, t2z);
-        }
-        two_sum_acc(A.hgx, A.lgx, gx);
-        two_sum_acc(A.hgy, A.lgy, gy);
-        two_sum_acc(A.hgz, A.lgz, gz);
-    }
+    pair_fold<GRAD, SCREENED>(A, T, three);
 }
 
 // The warp's 64 queries (two per lane, tail queries repeat the last one) and

@@ -111,3 +111,53 @@ def test_top1_statistic_plateaus_above_the_tolerance(oracle_mod, noise):
     assert agreement(cur, nt) == 1.0
     assert max(mean[18:]) <= 0.2 * chord
     assert 0.2 <= min(top[18:]) and max(top[18:]) <= 2.0, top[18:]
+
+
+def _two_spheres():
+    pa, na = synth.sphere(3000, seed=1)
+    pb, nb = synth.sphere(1500, seed=2)
+    pa = pa.astype(np.float64) + [-1.6, 0.0, 0.0]
+    pb = 0.6 * pb.astype(np.float64) + [1.6, 0.0, 0.0]
+    aa = np.full(3000, 4 * np.pi / 3000)
+    ab = np.full(1500, 4 * np.pi * 0.36 / 1500)
+    nb0 = nb.copy()
+    nb0[pb[:, 2] < 0.0] *= -1.0                      # lower half of B turned inward
+    return pa, na, aa, pb, nb, ab, nb0
+
+
+def mixed_component_runs(oracle_mod, iters=15, depth=6):
+    """Sphere B (1,500 points) with its lower half turned inward, alone and
+    beside a consistently oriented sphere A (3,000 points, outward or
+    inward).  Returns, per run, the share of B's points with outward
+    normals after `iters` iterations, and the last iso-value."""
+    pa, na, aa, pb, nb, ab, nb0 = _two_spheres()
+    runs = {"B alone": (pb, ab, nb0),
+            "A outward": (np.vstack([pa, pb]), np.concatenate([aa, ab]), np.vstack([na, nb0])),
+            "A inward": (np.vstack([pa, pb]), np.concatenate([aa, ab]), np.vstack([-na, nb0]))}
+    out = {}
+    for name, (P, A, N0) in runs.items():
+        P = P.astype(np.float32)
+        prm = oracle_mod.params(eps=0.5 * np.sqrt(A.sum() / len(P)), depth=depth, max_iters=1)
+        cur = N0
+        for _ in range(iters):
+            r = oracle_mod.iterate(P, A, cur, prm)
+            cur = r["normals"]
+        b = np.sum(cur[-1500:] * nb, axis=1)
+        out[name] = (float(np.mean(b > 0)), r["iso"], cur)
+    return out
+
+
+def test_a_mixed_component_heals_alone_but_not_beside_another(oracle_mod):
+    """Why a union of separate shapes does not reach one orientation per
+    shape: the level set of Eq. 6's single iso-value w_bar only passes near
+    the parts whose w crosses w_bar.  Alone, B's iso-value is its own mean and
+    B heals to one orientation.  Beside a consistently oriented A, w_bar takes
+    A's sign; the half of B oriented the other way has w of the other sign
+    next to it, gets no faces, and keeps its normals -- B stays mixed."""
+    res = mixed_component_runs(oracle_mod)
+    frac, _, _ = res["B alone"]
+    assert frac in (0.0, 1.0)
+    for name in ("A outward", "A inward"):
+        frac, iso, _ = res[name]
+        assert 0.3 < frac < 0.7, (name, frac)
+        assert np.sign(iso) == (1.0 if name == "A outward" else -1.0)
