@@ -126,6 +126,19 @@ def profiled_traffic(kernel_file, shape):
     return traffic if got == shape else None
 
 
+def profiled_bytes_per_interaction(which):
+    """DRAM bytes per interaction of the list evaluator from the committed
+    ncu summary (None when absent)."""
+    key = f"dram_bytes_per_interaction_{which}:"
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "tree_lists_metaballs1m.md")):
+            if line.startswith(key):
+                return float(line.split(":")[1])
+    except OSError:
+        return None
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -513,6 +526,7 @@ def run_ours(args, rank, world, local):
             ops = FP32_OPS[("wg", kind)]
         achieved = work / (kms[dom] / 1e3)
         shape = f"corners_pairs={tuning['corners_pairs']},corners_threads={tuning['corners_threads']}"
+        traffic_basis = "ncu dram bytes per launch (profiles/eval_corners_torus100k.md)"
         traffic = profiled_traffic("eval_corners_torus100k.md", shape) if (
             dom == "eval_corners" and kind == 0 and W["name"] == "torus-100k" and
             W["depth"] == 8) else None
@@ -526,10 +540,18 @@ def run_ours(args, rank, world, local):
             dom, work, ops = "eval_points", st["interactions_points_step"], FP32_OPS[("wg", kind)]
         dom += " (Barnes-Hut lists)"
         achieved = work / (kms[dom.split()[0]] / 1e3)
-        traffic = None
+        # DRAM bytes of the same list kernel captured by ncu on metaballs-1m,
+        # per interaction, times this launch's interactions (the lists, item
+        # partials and record misses grow with the records per group)
+        bpi = profiled_bytes_per_interaction(
+            "corners" if dom.startswith("eval_corners") else "points")
+        traffic = bpi * work if (bpi is not None and tuning.get("tree_group")) else None
+        traffic_basis = ("ncu dram bytes of k_tree_eval_lists on metaballs-1m per interaction "
+                         "(profiles/tree_lists_metaballs1m.md) x this launch's interactions")
     peak = lanes / ops
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "Ginteractions/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_basis": traffic_basis,
             "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {fmax/1e6:.0f} MHz"
                           f" / {ops} FP32 ops per interaction",
             "kernel_ms": {k: round(v, 4) for k, v in kms.items()},
