@@ -952,6 +952,8 @@ def main():
         "roofline": r["roof"], "cpu_baseline": cpu, "clocks": r["clocks"], "e2e": r["e2e"],
         "gpu_launches": r["launches"],
     }
+    if isinstance(cpu, dict) and "precision" in cpu:
+        line["precision"] = cpu.pop("precision")   # measured in the oracle leg
     print(json.dumps(line))
 
 
