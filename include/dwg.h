@@ -149,6 +149,20 @@ int dwg_set_convergence(dwg_handle h, int rule);
 int dwg_set_compensation(dwg_handle h, int on);
 
 /*
+ * How a batch handle (dwg_create_batch) runs an iteration of all its clouds
+ * (the paper orients one cloud; batching is this library's): phases = 1 (the
+ * default): every phase of the iteration -- Barnes-Hut moments per tree
+ * level, list evaluations, reduce, iso-value, level set, kNN scatter, update,
+ * the convergence select -- is one launch over every cloud's blocks, so the
+ * launches per iteration do not grow with the number of clouds; phases = 0:
+ * each cloud's chain of launches is a branch of the iteration graph on its
+ * own stream.  Both give every cloud the same bits as orienting it alone.
+ * The phases need k = 10 and the softened kernel in every cloud; otherwise
+ * the branches run.  Not a batch handle: DWG_ERR_STATE.
+ */
+int dwg_set_batch_mode(dwg_handle h, int phases);
+
+/*
  * Discretisation and update rule.
  *   depth: octree depth d in [1, 14] (Sec. 5.1 recommends 8-10 up to 1M
  *          points, 11-13 beyond).

@@ -29,6 +29,14 @@ struct dwg_ctx : public Ctx {
     // fork / join of the clouds' chains in a batch iteration (each cloud runs
     // on its own stream, so the graph holds one branch per cloud)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // batched phases: the clouds' argument table and, per phase and per tree
+    // level, the offsets of each cloud's blocks in the phase's grid
+    CloudIter *d_citer = nullptr;
+    int *d_boff = nullptr;             // (kPhCount + tree levels) x (clouds + 1)
+    int ph_blocks[kPhCount] = {};
+    std::vector<int> lv_blocks;        // per tree level
+    bool batched = false;              // the batched phases apply (uniform settings)
+    std::vector<dwg_ctx *> walk_p, walk_c;  // tree clouds without current lists
 };
 
 static std::mutex g_err_mu;
@@ -513,6 +521,8 @@ void dwg_destroy(dwg_handle h)
     cudaFree(h->d_bit_p);
     cudaFree(h->d_bit_c);
     cudaFree(h->d_states);
+    cudaFree(h->d_citer);
+    cudaFree(h->d_boff);
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     invalidate_graph(h);
@@ -699,6 +709,18 @@ int dwg_set_convergence(dwg_handle h, int rule)
     h->conv_rule = rule;
     invalidate_graph(h);
     for (dwg_ctx *c : h->clouds) dwg_set_convergence(c, rule);
+    return DWG_OK;
+}
+
+int dwg_set_batch_mode(dwg_handle h, int phases)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (!h->is_batch) return fail(h, DWG_ERR_STATE, "dwg_set_batch_mode needs a batch handle");
+    if (phases != 0 && phases != 1) return fail(h, DWG_ERR_INVALID, "phases must be 0 or 1");
+    if (h->batch_phases != phases) {
+        h->batch_phases = phases;
+        invalidate_graph(h);
+    }
     return DWG_OK;
 }
 
@@ -1562,6 +1584,79 @@ static int batch_prepare(dwg_ctx *h)
     return DWG_OK;
 }
 
+// Blocks of a cloud's part of a batched phase: the grid its own launch uses
+// (launch_reduce_points, launch_reduce_w, launch_mc_faces,
+// launch_knn_scatter, launch_normal_update, launch_select, the tree phases).
+static int phase_blocks(const dwg_ctx *c, int ph)
+{
+    const bool ls = c->mode == DWG_UPDATE_LEVELSET;
+    switch (ph) {
+    case kPhReducePoints: return (int)ceil_div(c->n, 256);
+    case kPhReduceW: return ls ? (int)ceil_div(c->ncorners, 256) : 0;
+    case kPhMcFaces: return ls ? (int)ceil_div(c->nleaves, 256) : 0;
+    case kPhKnn: return ls ? (int)ceil_div(c->max_faces, 128) : 0;
+    case kPhUpdate: return (int)ceil_div(c->n, 256);
+    case kPhSelHist:
+    case kPhSelSum: return select_blocks(c->n);
+    case kPhIso:
+    case kPhSelFind:
+    case kPhSelFinal: return 1;
+    default: return tree_phase_blocks(c, ph, -1);
+    }
+}
+
+// The batched iteration's tables: each cloud's arguments and the block
+// offsets of every phase.  The batched phases need one kernel instance for
+// all clouds: the same k (10) and the softened kernel everywhere; otherwise
+// the clouds' chains run as separate graph branches.
+static int batch_plan(dwg_ctx *h)
+{
+    const int ncl = (int)h->clouds.size();
+    h->batched = false;
+    h->walk_p.clear();
+    h->walk_c.clear();
+    if (!h->batch_phases) return DWG_OK;
+    for (const dwg_ctx *c : h->clouds)
+        if (c->knn != 10 || c->reg_mode != DWG_REG_SOFTEN) return DWG_OK;
+    std::vector<CloudIter> tab(ncl);
+    int maxL = 0;
+    for (int i = 0; i < ncl; ++i) {
+        dwg_ctx *c = h->clouds[i];
+        fill_cloud_iter(c, &tab[i]);
+        if (use_tree(c)) {
+            maxL = std::max(maxL, c->tree_levels);
+            if (!tree_lists_current(c, false)) h->walk_p.push_back(c);
+            if (c->mode == DWG_UPDATE_LEVELSET && !tree_lists_current(c, true))
+                h->walk_c.push_back(c);
+        }
+    }
+    const int rows = kPhCount + maxL;
+    std::vector<int> off((size_t)rows * (ncl + 1), 0);
+    h->lv_blocks.assign(maxL, 0);
+    for (int r = 0; r < rows; ++r) {
+        int *o = off.data() + (size_t)r * (ncl + 1);
+        for (int i = 0; i < ncl; ++i) {
+            const dwg_ctx *c = h->clouds[i];
+            const int b = r < kPhCount ? phase_blocks(c, r) : tree_phase_blocks(c, 0, r - kPhCount);
+            o[i + 1] = o[i] + b;
+        }
+        if (r < kPhCount) h->ph_blocks[r] = o[ncl];
+        else h->lv_blocks[r - kPhCount] = o[ncl];
+    }
+    cudaFree(h->d_citer);
+    cudaFree(h->d_boff);
+    h->d_citer = nullptr;
+    h->d_boff = nullptr;
+    DWG_CUDA_TRY(h, cudaMalloc(&h->d_citer, ncl * sizeof(CloudIter)));
+    DWG_CUDA_TRY(h, cudaMemcpy(h->d_citer, tab.data(), ncl * sizeof(CloudIter),
+                               cudaMemcpyHostToDevice));
+    DWG_CUDA_TRY(h, cudaMalloc(&h->d_boff, off.size() * sizeof(int)));
+    DWG_CUDA_TRY(h, cudaMemcpy(h->d_boff, off.data(), off.size() * sizeof(int),
+                               cudaMemcpyHostToDevice));
+    h->batched = true;
+    return DWG_OK;
+}
+
 static int batch_tables(dwg_ctx *h)
 {
     std::vector<GwnCloud> cp, cc;
@@ -1616,15 +1711,79 @@ static int batch_tables(dwg_ctx *h)
     DWG_CUDA_TRY(h, cudaMalloc(&h->d_states, st.size() * sizeof(IterState *)));
     DWG_CUDA_TRY(h, cudaMemcpy(h->d_states, st.data(), st.size() * sizeof(IterState *),
                                cudaMemcpyHostToDevice));
+    return batch_plan(h);
+}
+
+// one iteration of every cloud, phase by phase: each phase is one launch
+// over every cloud's blocks (the all-pairs sums, the Barnes-Hut moments per
+// tree level, the list evaluations and their combination, the reduce, the
+// iso-value, the level set, the kNN scatter, the update and the convergence
+// select), so the number of launches per iteration does not grow with the
+// number of clouds.  Each cloud's blocks are those of its own launch: the
+// results are the same bits as orienting the cloud alone.  Tree clouds whose
+// interaction lists are not resident (they would not fit) walk the tree in
+// launches of their own.
+static int batch_body_phases(dwg_ctx *h)
+{
+    const bool scr = h->kernel == DWG_KERNEL_SCREENED && h->lambda > 0.f;
+    const int ncl = (int)h->clouds.size();
+    cudaStream_t s = h->stream;
+    const CloudIter *cl = h->d_citer;
+    auto off = [&](int row) { return h->d_boff + (size_t)row * (ncl + 1); };
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    ok(launch_gwn_batch(h->d_bcl_p, h->d_bit_p, h->nit_p, true, scr, h->d_err, s));
+    ok(launch_gwn_batch(h->d_bcl_c, h->d_bit_c, h->nit_c, false, scr, h->d_err, s));
+    // Barnes-Hut moments: leaves, then each tree level from the bottom up
+    ok(launch_tree_batch(kPhLeafMom, cl, off(kPhLeafMom), ncl, h->ph_blocks[kPhLeafMom], -1, scr, s));
+    for (int lv = (int)h->lv_blocks.size() - 1; lv >= 0; --lv)
+        ok(launch_tree_batch(kPhLeafMom, cl, off(kPhCount + lv), ncl, h->lv_blocks[lv], lv, scr, s));
+    ok(launch_tree_batch(kPhMomRec, cl, off(kPhMomRec), ncl, h->ph_blocks[kPhMomRec], -1, scr, s));
+    // w and grad w at the points
+    ok(launch_tree_batch(kPhListsP, cl, off(kPhListsP), ncl, h->ph_blocks[kPhListsP], -1, scr, s));
+    ok(launch_tree_batch(kPhCombineP, cl, off(kPhCombineP), ncl, h->ph_blocks[kPhCombineP], -1,
+                         scr, s));
+    for (dwg_ctx *c : h->walk_p) {
+        c->stream = s;
+        ok(launch_tree_iter(c, c->lists_p, c->d_p4, c->n, true, c->d_part_p, c->n, c->d_state));
+    }
+    ok(launch_eval_batch(kPhReducePoints, cl, off(kPhReducePoints), ncl,
+                         h->ph_blocks[kPhReducePoints], s));
+    ok(launch_iter_batch(kPhIso, cl, off(kPhIso), ncl, h->ph_blocks[kPhIso], 0, s));
+    // w at the corners, level set, face gradients to the k nearest points
+    ok(launch_tree_batch(kPhListsC, cl, off(kPhListsC), ncl, h->ph_blocks[kPhListsC], -1, scr, s));
+    ok(launch_tree_batch(kPhCombineC, cl, off(kPhCombineC), ncl, h->ph_blocks[kPhCombineC], -1,
+                         scr, s));
+    for (dwg_ctx *c : h->walk_c) {
+        c->stream = s;
+        ok(launch_tree_iter(c, c->lists_c, c->d_corner_pos, c->ncorners, false, c->d_part_c,
+                            c->ncorners, c->d_state));
+    }
+    ok(launch_eval_batch(kPhReduceW, cl, off(kPhReduceW), ncl, h->ph_blocks[kPhReduceW], s));
+    ok(launch_iter_batch(kPhMcFaces, cl, off(kPhMcFaces), ncl, h->ph_blocks[kPhMcFaces], 0, s));
+    ok(launch_iter_batch(kPhKnn, cl, off(kPhKnn), ncl, h->ph_blocks[kPhKnn], 0, s));
+    // normal update and convergence
+    ok(launch_iter_batch(kPhUpdate, cl, off(kPhUpdate), ncl, h->ph_blocks[kPhUpdate], 0, s));
+    for (int level = 0; level < 3; ++level) {
+        ok(launch_iter_batch(kPhSelHist, cl, off(kPhSelHist), ncl, h->ph_blocks[kPhSelHist],
+                             level, s));
+        ok(launch_iter_batch(kPhSelFind, cl, off(kPhSelFind), ncl, h->ph_blocks[kPhSelFind],
+                             level, s));
+    }
+    ok(launch_iter_batch(kPhSelSum, cl, off(kPhSelSum), ncl, h->ph_blocks[kPhSelSum], 0, s));
+    ok(launch_iter_batch(kPhSelFinal, cl, off(kPhSelFinal), ncl, h->ph_blocks[kPhSelFinal], 0, s));
+    if (e != cudaSuccess)
+        return fail(h, DWG_ERR_CUDA, std::string("batched phase launch: ") + cudaGetErrorString(e));
     return DWG_OK;
 }
 
-// one iteration of every cloud: the all-pairs sums of every cloud in one
-// launch, then each cloud's chain (tree sums, reduce, iso-value, level set,
+// one iteration of every cloud when the phases cannot be batched (mixed k
+// or kernels): the all-pairs sums of every cloud in one launch, then each
+// cloud's chain (tree sums, reduce, iso-value, level set,
 // kNN scatter, update, convergence) on the cloud's own stream, forked from
 // and joined back into the batch stream, so that the chains of different
 // clouds run concurrently (one graph branch per cloud)
-static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
+static int batch_body_branches(dwg_ctx *h, cudaGraphConditionalHandle cond)
 {
     bool scr = h->kernel == DWG_KERNEL_SCREENED && h->lambda > 0.f;
     if (launch_gwn_batch(h->d_bcl_p, h->d_bit_p, h->nit_p, true, scr, h->d_err, h->stream) !=
@@ -1662,6 +1821,13 @@ static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
         DWG_CUDA_TRY(h, cudaEventRecord(c->ev_join, c->stream));
         DWG_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, c->ev_join, 0));
     }
+    return DWG_OK;
+}
+
+static int batch_body(dwg_ctx *h, cudaGraphConditionalHandle cond)
+{
+    int rc = h->batched ? batch_body_phases(h) : batch_body_branches(h, cond);
+    if (rc) return rc;
     k_batch_cond<<<1, 256, 0, h->stream>>>(h->d_states, (int)h->clouds.size(), h->max_iters, cond);
     LAUNCH_CHECK(h);
     return DWG_OK;

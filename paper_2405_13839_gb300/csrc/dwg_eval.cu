@@ -703,21 +703,18 @@ constexpr int kPW = 4;      // query pairs per thread, w-only kernel (batched an
 // reduce: combine chunk partials in chunk order; for gradients add back the
 // coincident-source terms; optionally per-block FP64 sums of w.
 // ---------------------------------------------------------------------------
-struct CubeQ {
-    double lo[3];
-    double inv_h21;
-};
-
 template <bool GRAD>
-__global__ void k_reduce_points(const float *__restrict__ part, int nchunks, int64_t m,
-                                int64_t stride, const float4 *__restrict__ q,
-                                const float *__restrict__ src, int rec_floats,
-                                const uint64_t *__restrict__ codes, int64_t nsrc, int self_mode,
-                                CubeQ cq, EvalParams ep, float4 *__restrict__ out,
-                                double *__restrict__ wsum_blocks)
+__device__ __forceinline__ void reduce_points_body(const float *__restrict__ part, int nchunks,
+                                                   int64_t m, int64_t stride,
+                                                   const float4 *__restrict__ q,
+                                                   const float *__restrict__ src, int rec_floats,
+                                                   const uint64_t *__restrict__ codes,
+                                                   int64_t nsrc, int self_mode, const CubeQ &cq,
+                                                   const EvalParams &ep, float4 *__restrict__ out,
+                                                   double *__restrict__ wsum_blocks, int64_t bid)
 {
     constexpr int NA = GRAD ? 4 : 1;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = bid * blockDim.x + threadIdx.x;
     double wloc = 0.0;
     if (i < m) {
         float h[NA], l[NA];
@@ -802,16 +799,29 @@ __global__ void k_reduce_points(const float *__restrict__ part, int nchunks, int
             if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
             __syncthreads();
         }
-        if (threadIdx.x == 0) wsum_blocks[blockIdx.x] = sh[0];
+        if (threadIdx.x == 0) wsum_blocks[bid] = sh[0];
     }
+}
+
+template <bool GRAD>
+__global__ void k_reduce_points(const float *__restrict__ part, int nchunks, int64_t m,
+                                int64_t stride, const float4 *__restrict__ q,
+                                const float *__restrict__ src, int rec_floats,
+                                const uint64_t *__restrict__ codes, int64_t nsrc, int self_mode,
+                                CubeQ cq, EvalParams ep, float4 *__restrict__ out,
+                                double *__restrict__ wsum_blocks)
+{
+    reduce_points_body<GRAD>(part, nchunks, m, stride, q, src, rec_floats, codes, nsrc,
+                             self_mode, cq, ep, out, wsum_blocks, blockIdx.x);
 }
 
 int wsum_block_count(int64_t n) { return (int)ceil_div(n, 256); }
 
-__global__ void k_reduce_w(const float *__restrict__ part, int nchunks, int64_t m, int64_t stride,
-                           float *__restrict__ out)
+__device__ __forceinline__ void reduce_w_body(const float *__restrict__ part, int nchunks,
+                                              int64_t m, int64_t stride, float *__restrict__ out,
+                                              int64_t bid)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = bid * blockDim.x + threadIdx.x;
     if (i >= m) return;
     float h = 0.f, l = 0.f;
     for (int ch = 0; ch < nchunks; ++ch) {
@@ -819,6 +829,45 @@ __global__ void k_reduce_w(const float *__restrict__ part, int nchunks, int64_t 
         l = __fadd_rn(l, part[((int64_t)ch * 2 + 1) * stride + i]);
     }
     out[i] = __fadd_rn(h, l);
+}
+
+__global__ void k_reduce_w(const float *__restrict__ part, int nchunks, int64_t m, int64_t stride,
+                           float *__restrict__ out)
+{
+    reduce_w_body(part, nchunks, m, stride, out, blockIdx.x);
+}
+
+// batched: every cloud of a batch in one launch (the point reduce of a
+// batch runs with self_mode 1 and the gradient, as each cloud's own launch)
+__global__ void k_reduce_points_b(const CloudIter *__restrict__ cl, const int *__restrict__ off,
+                                  int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    reduce_points_body<true>(c.part_p, c.nchunks_p, c.n, c.n, c.p4, c.src, kSrcFloats, c.codes,
+                             c.n, 1, c.cq, c.ep, c.wg, c.wsum_blocks,
+                             (int64_t)blockIdx.x - off[ci]);
+}
+
+__global__ void k_reduce_w_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    reduce_w_body(c.part_c, c.nchunks_c, c.ncorners, c.ncorners, c.wc,
+                  (int64_t)blockIdx.x - off[ci]);
+}
+
+cudaError_t launch_eval_batch(int phase, const CloudIter *cl, const int *off, int ncl,
+                              int blocks, cudaStream_t s)
+{
+    if (blocks <= 0) return cudaSuccess;
+    if (phase == kPhReducePoints)
+        k_reduce_points_b<<<(unsigned)blocks, 256, 0, s>>>(cl, off, ncl);
+    else if (phase == kPhReduceW)
+        k_reduce_w_b<<<(unsigned)blocks, 256, 0, s>>>(cl, off, ncl);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_w(Ctx *c, const float *part, int nchunks, int64_t m, float *out)

@@ -51,6 +51,19 @@ __device__ __forceinline__ bool cloud_idle(const IterState *st)
 {
     return st->done || st->iter >= st->max_iters;
 }
+
+// Many clouds in one launch: blocks [off[c], off[c + 1]) of the grid run
+// cloud c's blocks (clouds may have none).  Returns the cloud of this block.
+__device__ __forceinline__ int seg_cloud(const int *__restrict__ off, int ncl)
+{
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = ncl - 1;
+    while (lo < hi) {  // the last cloud whose first block is <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 #endif
 
 // radix-select state of the convergence statistic (device)
@@ -83,6 +96,100 @@ struct GwnCloud {
 };
 struct GwnItem {
     int cloud, qtile, chunk, pad;
+};
+
+// the kNN bucket tree of a cloud as the device searches see it
+struct KnnTree {
+    const float4 *p4;
+    const int64_t *perm;
+    const uint64_t *codes;  // sorted 63-bit Morton codes of the points
+    int64_t n;
+    const float4 *lo, *hi;
+    int levels;
+    double cube_lo[3];
+    double inv_h21;
+};
+
+// the root cube's quantisation (Morton codes of arbitrary queries)
+struct CubeQ {
+    double lo[3];
+    double inv_h21;
+};
+
+// Everything one cloud's per-iteration kernels read, gathered for the
+// batched launches of a batch handle: one entry per cloud in a device table,
+// and per phase the offsets of each cloud's blocks in the launch's grid.
+struct CloudIter {
+    IterState *st;
+    int *err;
+    unsigned long long *counter;
+    int64_t n;
+    EvalParams ep;
+    // reduce at the points (w and grad w, the iso-value's block sums)
+    const float *part_p;
+    int nchunks_p;
+    const float4 *p4;
+    const float *src;
+    const uint64_t *codes;
+    CubeQ cq;
+    float4 *wg;
+    double *wsum_blocks;
+    int wsum_nb;
+    // w at the corners
+    const float *part_c;
+    int nchunks_c;
+    int64_t ncorners;
+    float *wc;
+    // level set
+    const int *leaf_corners;
+    const int4 *leaves;
+    int64_t nleaves;
+    const float4 *corner_pos;
+    float4 *faces;
+    int64_t max_faces;
+    // kNN scatter
+    KnnTree T;
+    int k;
+    const int64_t *cell_off;
+    const int *cell_idx;
+    double acc_scale;
+    unsigned long long *acc;
+    // normal update and convergence
+    int mode;
+    float4 *nrm;
+    float *src_rw;
+    float *dtheta;
+    double *dn_blocks;
+    struct SelState *sel;
+    unsigned *sel_hist;
+    double *sel_part;
+    int sel_nb;
+    float tol;
+    int conv_rule;
+    double *tr_iso, *tr_stat, *tr_dn;
+    long long *tr_faces;
+    // Barnes-Hut (tree clouds): moments and the two query sets' lists
+    int tree;
+    int levels, bucket;
+    const float4 *nrm_c;
+    double *tree_M;
+    const float4 *tree_rec;
+    float4 *tree_mrec, *tree_frec;
+    const float4 *lq[2];          // [0] points, [1] corners
+    int64_t lm[2];
+    const int64_t *far_off[2], *near_off[2], *item_off[2];
+    const int *far_ids[2], *near_ids[2];
+    const int2 *items[2];
+    int64_t nitems[2];
+    float *ipart[2];
+    float *lpart[2];              // the reduce's chunk-0 partials
+};
+
+// phases of a batched iteration (one launch each, every cloud's blocks)
+enum BatchPhase {
+    kPhReducePoints, kPhReduceW, kPhIso, kPhMcFaces, kPhKnn, kPhUpdate, kPhSelHist, kPhSelFind,
+    kPhSelSum, kPhSelFinal, kPhLeafMom, kPhMomRec, kPhListsP, kPhListsC, kPhCombineP,
+    kPhCombineC, kPhCount
 };
 
 // interaction lists of one query set for the group form of the Barnes-Hut
@@ -197,6 +304,7 @@ struct Ctx {
     float tree_beta = 2.0f;            // 1 / opening angle
     int tree_leaf = 16;                // points per tree leaf (16, 32, 64 or 128)
     int tree_group = 1;                // 1: opening test per 64-query group, 0: per query
+    int batch_phases = 1;              // batch handles: 1 one launch per phase, 0 branches
     uint64_t tree_gen = 0;             // counts tree builds
     TreeLists lists_p, lists_c;        // group-test lists at the points and corners
     int tree_levels = 0;               // 2^tree_levels leaves
@@ -350,6 +458,24 @@ void free_lists(TreeLists &L);
 // are valid for it, else the walk
 cudaError_t launch_tree_iter(Ctx *c, TreeLists &L, const float4 *q, int64_t m, bool grad,
                              float *part, int64_t stride, const IterState *st);
+
+// batched iteration phases over a device table of CloudIter (one per cloud)
+// and the block offsets `off` (ncl + 1) of the phase; `blocks` = off[ncl];
+// `arg`: the select level (kPhSelHist, kPhSelFind) or the tree level
+// (kPhLevelMom, see launch_tree_batch)
+cudaError_t launch_iter_batch(int phase, const CloudIter *cl, const int *off, int ncl,
+                              int blocks, int arg, cudaStream_t s);
+cudaError_t launch_eval_batch(int phase, const CloudIter *cl, const int *off, int ncl,
+                              int blocks, cudaStream_t s);
+// kPhLeafMom, kPhMomRec, kPhListsP/C, kPhCombineP/C; level >= 0: the moments
+// of tree level `level` (nodes [2^level, 2^(level + 1)) of every cloud)
+cudaError_t launch_tree_batch(int phase, const CloudIter *cl, const int *off, int ncl,
+                              int blocks, int level, bool screened, cudaStream_t s);
+// blocks a cloud's part of a batched tree phase takes (0: none); level >= 0:
+// the moments of that tree level
+int tree_phase_blocks(const Ctx *c, int phase, int level);
+bool tree_lists_current(const Ctx *c, bool corners);
+void fill_cloud_iter(const Ctx *c, CloudIter *out);
 
 // dwg_iter.cu
 cudaError_t launch_iso(Ctx *c);

@@ -24,6 +24,8 @@
 //   k_features                  patch features of the learned warm start.
 #include <algorithm>
 
+#include <string.h>
+
 #include "dwg_internal.cuh"
 
 namespace dwg {
@@ -31,7 +33,8 @@ namespace dwg {
 // ---------------------------------------------------------------------------
 // iso-value
 // ---------------------------------------------------------------------------
-__global__ void k_iso(const double *__restrict__ wsum_blocks, int nb, int64_t n, IterState *st)
+__device__ __forceinline__ void iso_body(const double *__restrict__ wsum_blocks, int nb,
+                                         int64_t n, IterState *st)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
     __shared__ double sh[256];
@@ -47,6 +50,11 @@ __global__ void k_iso(const double *__restrict__ wsum_blocks, int nb, int64_t n,
         st->iso = sh[0] / (double)n;
         st->nfaces = 0;
     }
+}
+
+__global__ void k_iso(const double *__restrict__ wsum_blocks, int nb, int64_t n, IterState *st)
+{
+    iso_body(wsum_blocks, nb, n, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,14 +253,16 @@ cudaError_t launch_mc_tris(Ctx *c, float *out, int64_t cap, unsigned long long *
 // (in the area's w) and, in the centroid's w, the position in the
 // Morton-sorted points of the face's leaf cell (found once per cut leaf):
 // the k-nearest search of its faces starts there.
-__global__ void __launch_bounds__(256)
-    k_mc_faces(const int *__restrict__ leaf_corners, const int4 *__restrict__ leaves, int64_t nl,
-               const float4 *__restrict__ cpos, const float *__restrict__ wc,
-               const uint64_t *__restrict__ codes, int64_t n, IterState *st,
-               float4 *__restrict__ faces, int64_t max_faces, int *err)
+__device__ __forceinline__ void mc_faces_body(const int *__restrict__ leaf_corners,
+                                              const int4 *__restrict__ leaves, int64_t nl,
+                                              const float4 *__restrict__ cpos,
+                                              const float *__restrict__ wc,
+                                              const uint64_t *__restrict__ codes, int64_t n,
+                                              IterState *st, float4 *__restrict__ faces,
+                                              int64_t max_faces, int *err, int64_t bid)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t l = bid * blockDim.x + threadIdx.x;
     const double iso = st->iso;
     F3 area[6], cen[6];
     int cnt = 0;
@@ -315,6 +325,16 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+__global__ void __launch_bounds__(256)
+    k_mc_faces(const int *__restrict__ leaf_corners, const int4 *__restrict__ leaves, int64_t nl,
+               const float4 *__restrict__ cpos, const float *__restrict__ wc,
+               const uint64_t *__restrict__ codes, int64_t n, IterState *st,
+               float4 *__restrict__ faces, int64_t max_faces, int *err)
+{
+    mc_faces_body(leaf_corners, leaves, nl, cpos, wc, codes, n, st, faces, max_faces, err,
+                  blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // exact k nearest points over the bucket tree
 // ---------------------------------------------------------------------------
@@ -330,17 +350,6 @@ __device__ __forceinline__ float pt_d2(float4 p, F3 q)
     float dx = __fsub_rn(p.x, q.x), dy = __fsub_rn(p.y, q.y), dz = __fsub_rn(p.z, q.z);
     return fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
 }
-
-struct KnnTree {
-    const float4 *p4;
-    const int64_t *perm;
-    const uint64_t *codes;  // sorted 63-bit Morton codes of the points
-    int64_t n;
-    const float4 *lo, *hi;
-    int levels;
-    double cube_lo[3];
-    double inv_h21;
-};
 
 // Candidate order: squared float32 distance, ties to the smaller input index,
 // as one 64-bit key (the bits of a non-negative float order like the float).
@@ -470,14 +479,15 @@ __device__ __forceinline__ void knn_scan(const KnnTree &T, F3 q, int k, const in
 static KnnTree knn_tree(const Ctx *c);
 
 template <int KMAX, bool FIXED>
-__global__ void __launch_bounds__(128)
-    k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
-                  KnnTree T, int k, const int64_t *__restrict__ cell_off,
-                  const int *__restrict__ cell_idx, double scale, unsigned long long *acc,
-                  int *err)
+__device__ __forceinline__ void knn_scatter_body(const float4 *__restrict__ faces,
+                                                 const IterState *st, int64_t max_faces,
+                                                 const KnnTree &T, int k,
+                                                 const int64_t *__restrict__ cell_off,
+                                                 const int *__restrict__ cell_idx, double scale,
+                                                 unsigned long long *acc, int *err, int64_t bid)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
-    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t f = bid * blockDim.x + threadIdx.x;
     int64_t nf = min((int64_t)st->nfaces, max_faces);
     if (f >= nf) return;
     float4 A = faces[2 * f], C = faces[2 * f + 1];
@@ -503,6 +513,17 @@ __global__ void __launch_bounds__(128)
         atomicAdd(a + 1, (unsigned long long)vy);
         atomicAdd(a + 2, (unsigned long long)vz);
     }
+}
+
+template <int KMAX, bool FIXED>
+__global__ void __launch_bounds__(128)
+    k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
+                  KnnTree T, int k, const int64_t *__restrict__ cell_off,
+                  const int *__restrict__ cell_idx, double scale, unsigned long long *acc,
+                  int *err)
+{
+    knn_scatter_body<KMAX, FIXED>(faces, st, max_faces, T, k, cell_off, cell_idx, scale, acc,
+                                  err, blockIdx.x);
 }
 
 template <int KMAX, bool FIXED>
@@ -1013,15 +1034,19 @@ cudaError_t launch_clamp_delta(Ctx *c, int k, double vmin, double vmax, float *d
 // ---------------------------------------------------------------------------
 // normal update (Eq. 7) and per-point change
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    k_normal_update(int mode, int64_t n, unsigned long long *__restrict__ acc,
-                    const float4 *__restrict__ wg, const float4 *__restrict__ p4,
-                    float4 *__restrict__ nrm, float *__restrict__ src,
-                    float *__restrict__ src16, float *__restrict__ dtheta,
-                    double *__restrict__ dn_blocks, const IterState *st)
+__device__ __forceinline__ void normal_update_body(int mode, int64_t n,
+                                                   unsigned long long *__restrict__ acc,
+                                                   const float4 *__restrict__ wg,
+                                                   const float4 *__restrict__ p4,
+                                                   float4 *__restrict__ nrm,
+                                                   float *__restrict__ src,
+                                                   float *__restrict__ src16,
+                                                   float *__restrict__ dtheta,
+                                                   double *__restrict__ dn_blocks,
+                                                   const IterState *st, int64_t bid)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch: normals stay
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = bid * blockDim.x + threadIdx.x;
     double dn = 0.0;
     if (i < n) {
         float4 o = nrm[i];
@@ -1077,7 +1102,17 @@ __global__ void __launch_bounds__(256)
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) dn_blocks[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) dn_blocks[bid] = sh[0];
+}
+
+__global__ void __launch_bounds__(256)
+    k_normal_update(int mode, int64_t n, unsigned long long *__restrict__ acc,
+                    const float4 *__restrict__ wg, const float4 *__restrict__ p4,
+                    float4 *__restrict__ nrm, float *__restrict__ src,
+                    float *__restrict__ src16, float *__restrict__ dtheta,
+                    double *__restrict__ dn_blocks, const IterState *st)
+{
+    normal_update_body(mode, n, acc, wg, p4, nrm, src, src16, dtheta, dn_blocks, st, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1148,9 +1183,10 @@ __device__ void find_bin(const unsigned *hist, int nb, unsigned k, unsigned *war
 // and one CTA adds the partials in a fixed order and takes the decision.
 constexpr int kSelGridThreads = 256;
 
-__global__ void __launch_bounds__(kSelGridThreads)
-    k_sel_hist(const float *__restrict__ dtheta, int64_t n, int level,
-               const SelState *__restrict__ ss, unsigned *__restrict__ hist, const IterState *st)
+__device__ __forceinline__ void sel_hist_body(const float *__restrict__ dtheta, int64_t n,
+                                              int level, const SelState *__restrict__ ss,
+                                              unsigned *__restrict__ hist, const IterState *st,
+                                              int64_t bid, int64_t nblk)
 {
     if (cloud_idle(st)) return;
     __shared__ unsigned h[kSelBins];
@@ -1161,8 +1197,7 @@ __global__ void __launch_bounds__(kSelGridThreads)
     const unsigned mask = level == 2 ? 255u : 4095u;
     const int sh_hi = level == 1 ? 20 : 8;  // bits above this level's field (levels 1, 2)
     const unsigned prefix = ss->prefix;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
         const unsigned v = bits[i];
         if (level > 0 && (v >> sh_hi) != prefix) continue;
         atomicAdd(&h[(v >> shift) & mask], 1u);
@@ -1172,9 +1207,15 @@ __global__ void __launch_bounds__(kSelGridThreads)
         if (h[b]) atomicAdd(&hist[b], h[b]);
 }
 
-__global__ void __launch_bounds__(kSelThreads)
-    k_sel_find(int64_t n, int level, SelState *__restrict__ ss, unsigned *__restrict__ hist,
-               const IterState *st)
+__global__ void __launch_bounds__(kSelGridThreads)
+    k_sel_hist(const float *__restrict__ dtheta, int64_t n, int level,
+               const SelState *__restrict__ ss, unsigned *__restrict__ hist, const IterState *st)
+{
+    sel_hist_body(dtheta, n, level, ss, hist, st, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void sel_find_body(int64_t n, int level, SelState *__restrict__ ss,
+                                              unsigned *__restrict__ hist, const IterState *st)
 {
     if (cloud_idle(st)) return;
     __shared__ unsigned warp_sums[33];
@@ -1196,17 +1237,24 @@ __global__ void __launch_bounds__(kSelThreads)
     for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0;  // for the next level
 }
 
-__global__ void __launch_bounds__(kSelGridThreads)
-    k_sel_sum(const float *__restrict__ dtheta, int64_t n, const SelState *__restrict__ ss,
-              double *__restrict__ part, const IterState *st)
+__global__ void __launch_bounds__(kSelThreads)
+    k_sel_find(int64_t n, int level, SelState *__restrict__ ss, unsigned *__restrict__ hist,
+               const IterState *st)
+{
+    sel_find_body(n, level, ss, hist, st);
+}
+
+__device__ __forceinline__ void sel_sum_body(const float *__restrict__ dtheta, int64_t n,
+                                             const SelState *__restrict__ ss,
+                                             double *__restrict__ part, const IterState *st,
+                                             int64_t bid, int64_t nblk)
 {
     if (cloud_idle(st)) return;
     __shared__ double sh[kSelGridThreads];
     const unsigned *bits = reinterpret_cast<const unsigned *>(dtheta);
     const unsigned tbits = ss->prefix;
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x)
         if (bits[i] > tbits) s += (double)dtheta[i];
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -1214,14 +1262,24 @@ __global__ void __launch_bounds__(kSelGridThreads)
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) part[bid] = sh[0];
 }
 
-__global__ void __launch_bounds__(kSelThreads)
-    k_sel_final(int64_t n, float tol, int rule, const SelState *__restrict__ ss,
-                const double *__restrict__ part, int npart, IterState *st,
-                const double *__restrict__ dn_blocks, int ndn, double *tr_iso, double *tr_stat,
-                double *tr_dn, long long *tr_faces, cudaGraphConditionalHandle cond, int use_cond)
+__global__ void __launch_bounds__(kSelGridThreads)
+    k_sel_sum(const float *__restrict__ dtheta, int64_t n, const SelState *__restrict__ ss,
+              double *__restrict__ part, const IterState *st)
+{
+    sel_sum_body(dtheta, n, ss, part, st, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void sel_final_body(int64_t n, float tol, int rule,
+                                               const SelState *__restrict__ ss,
+                                               const double *__restrict__ part, int npart,
+                                               IterState *st,
+                                               const double *__restrict__ dn_blocks, int ndn,
+                                               double *tr_iso, double *tr_stat, double *tr_dn,
+                                               long long *tr_faces,
+                                               cudaGraphConditionalHandle cond, int use_cond)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
     __shared__ double sh[kSelThreads];
@@ -1265,6 +1323,16 @@ __global__ void __launch_bounds__(kSelThreads)
         st->done = done;
         if (use_cond) cudaGraphSetConditional(cond, (!done && it < st->max_iters) ? 1u : 0u);
     }
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+    k_sel_final(int64_t n, float tol, int rule, const SelState *__restrict__ ss,
+                const double *__restrict__ part, int npart, IterState *st,
+                const double *__restrict__ dn_blocks, int ndn, double *tr_iso, double *tr_stat,
+                double *tr_dn, long long *tr_faces, cudaGraphConditionalHandle cond, int use_cond)
+{
+    sel_final_body(n, tol, rule, ss, part, npart, st, dn_blocks, ndn, tr_iso, tr_stat, tr_dn,
+                   tr_faces, cond, use_cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -1321,6 +1389,87 @@ cudaError_t launch_iso(Ctx *c)
 {
     k_iso<<<1, 256, 0, c->stream>>>(c->d_wsum_blocks, c->wsum_blocks, c->n, c->d_state);
     return cudaGetLastError();
+}
+
+// A cloud's entry of the batched iteration's table: the same arguments its
+// own launches pass (launch_reduce_points with the points as queries,
+// launch_iso, launch_reduce_w, launch_mc_faces, launch_knn_scatter,
+// launch_normal_update, launch_select, launch_tree_moments, the list
+// evaluation); valid while the cloud's buffers stay (the batch graph's
+// generation covers them).
+void fill_cloud_iter(const Ctx *c, CloudIter *o)
+{
+    memset(o, 0, sizeof *o);
+    o->st = c->d_state;
+    o->err = c->d_err;
+    o->counter = c->d_counter;
+    o->n = c->n;
+    o->ep = make_eval_params(c);
+    o->part_p = c->d_part_p;
+    o->nchunks_p = c->nchunks_p;
+    o->p4 = c->d_p4;
+    o->src = c->d_src;
+    o->codes = c->d_codes;
+    for (int k = 0; k < 3; ++k) o->cq.lo[k] = c->cube_lo[k];
+    o->cq.inv_h21 = (double)(1 << kMortonBits) / c->cube_L;
+    o->wg = c->d_wg;
+    o->wsum_blocks = c->d_wsum_blocks;
+    o->wsum_nb = c->wsum_blocks;
+    o->part_c = c->d_part_c;
+    o->nchunks_c = c->nchunks_c;
+    o->ncorners = c->ncorners;
+    o->wc = c->d_wc;
+    o->leaf_corners = c->d_leaf_corners;
+    o->leaves = c->d_leaves;
+    o->nleaves = c->nleaves;
+    o->corner_pos = c->d_corner_pos;
+    o->faces = c->d_faces;
+    o->max_faces = c->max_faces;
+    o->T = knn_tree(c);
+    o->k = c->knn;
+    const bool lists = c->knn_lists && c->cells_k == c->knn && c->d_cell_off;
+    o->cell_off = lists ? c->d_cell_off : nullptr;
+    o->cell_idx = lists ? c->d_cell_idx : nullptr;
+    o->acc_scale = c->acc_scale;
+    o->acc = c->d_acc;
+    o->mode = c->mode;
+    o->nrm = c->d_nrm;
+    o->nrm_c = c->d_nrm;
+    o->src_rw = c->d_src;
+    o->dtheta = c->d_dtheta;
+    o->dn_blocks = c->d_dn_blocks;
+    o->sel = c->d_sel;
+    o->sel_hist = c->d_sel_hist;
+    o->sel_part = c->d_sel_part;
+    o->sel_nb = select_blocks(c->n);
+    o->tol = c->tol;
+    o->conv_rule = c->conv_rule;
+    o->tr_iso = c->d_tr_iso;
+    o->tr_stat = c->d_tr_stat;
+    o->tr_dn = c->d_tr_dn;
+    o->tr_faces = c->d_tr_faces;
+    o->tree = use_tree(c) ? 1 : 0;
+    o->levels = c->tree_levels;
+    o->bucket = c->tree_leaf;
+    o->tree_M = c->d_tree_M;
+    o->tree_rec = c->d_tree_rec;
+    o->tree_mrec = c->d_tree_mrec;
+    o->tree_frec = c->d_tree_frec;
+    const TreeLists *L[2] = {&c->lists_p, &c->lists_c};
+    float *lp[2] = {c->d_part_p, c->d_part_c};
+    for (int w = 0; w < 2; ++w) {
+        o->lq[w] = L[w]->q;
+        o->lm[w] = L[w]->m;
+        o->far_off[w] = L[w]->d_far_off;
+        o->near_off[w] = L[w]->d_near_off;
+        o->item_off[w] = L[w]->d_item_off;
+        o->far_ids[w] = L[w]->d_far;
+        o->near_ids[w] = L[w]->d_near;
+        o->items[w] = L[w]->d_items;
+        o->nitems[w] = L[w]->nitems;
+        o->ipart[w] = L[w]->d_ipart;
+        o->lpart[w] = lp[w];
+    }
 }
 
 cudaError_t launch_mc_faces(Ctx *c)
@@ -1559,6 +1708,94 @@ cudaError_t launch_select(Ctx *c, cudaGraphConditionalHandle cond, int use_cond)
         c->n, c->tol, c->conv_rule, c->d_sel, c->d_sel_part, nb, c->d_state, c->d_dn_blocks,
         (int)ceil_div(c->n, 256), c->d_tr_iso, c->d_tr_stat, c->d_tr_dn, c->d_tr_faces, cond,
         use_cond);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batched iteration phases: every cloud of a batch in one launch (each
+// cloud's blocks as in its own launch, so its results are the same bits)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_iso_b(const CloudIter *__restrict__ cl)
+{
+    const CloudIter &c = cl[blockIdx.x];
+    iso_body(c.wsum_blocks, c.wsum_nb, c.n, c.st);
+}
+
+__global__ void __launch_bounds__(256)
+    k_mc_faces_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    mc_faces_body(c.leaf_corners, c.leaves, c.nleaves, c.corner_pos, c.wc, c.codes, c.n, c.st,
+                  c.faces, c.max_faces, c.err, (int64_t)blockIdx.x - off[ci]);
+}
+
+template <int KMAX, bool FIXED>
+__global__ void __launch_bounds__(128)
+    k_knn_scatter_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    knn_scatter_body<KMAX, FIXED>(c.faces, c.st, c.max_faces, c.T, c.k, c.cell_off, c.cell_idx,
+                                  c.acc_scale, c.acc, c.err, (int64_t)blockIdx.x - off[ci]);
+}
+
+__global__ void __launch_bounds__(256)
+    k_normal_update_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    normal_update_body(c.mode, c.n, c.acc, c.wg, c.p4, c.nrm, c.src_rw, nullptr, c.dtheta,
+                       c.dn_blocks, c.st, (int64_t)blockIdx.x - off[ci]);
+}
+
+__global__ void __launch_bounds__(kSelGridThreads)
+    k_sel_hist_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl, int level)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    sel_hist_body(c.dtheta, c.n, level, c.sel, c.sel_hist, c.st, (int64_t)blockIdx.x - off[ci],
+                  (int64_t)off[ci + 1] - off[ci]);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_find_b(const CloudIter *__restrict__ cl, int level)
+{
+    const CloudIter &c = cl[blockIdx.x];
+    sel_find_body(c.n, level, c.sel, c.sel_hist, c.st);
+}
+
+__global__ void __launch_bounds__(kSelGridThreads)
+    k_sel_sum_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    sel_sum_body(c.dtheta, c.n, c.sel, c.sel_part, c.st, (int64_t)blockIdx.x - off[ci],
+                 (int64_t)off[ci + 1] - off[ci]);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_final_b(const CloudIter *__restrict__ cl)
+{
+    const CloudIter &c = cl[blockIdx.x];
+    sel_final_body(c.n, c.tol, c.conv_rule, c.sel, c.sel_part, c.sel_nb, c.st, c.dn_blocks,
+                   (int)((c.n + 255) / 256), c.tr_iso, c.tr_stat, c.tr_dn, c.tr_faces, 0, 0);
+}
+
+cudaError_t launch_iter_batch(int phase, const CloudIter *cl, const int *off, int ncl,
+                              int blocks, int arg, cudaStream_t s)
+{
+    if (blocks <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)blocks;
+    switch (phase) {
+    case kPhIso: k_iso_b<<<(unsigned)ncl, 256, 0, s>>>(cl); break;
+    case kPhMcFaces: k_mc_faces_b<<<g, 256, 0, s>>>(cl, off, ncl); break;
+    case kPhKnn: k_knn_scatter_b<10, true><<<g, 128, 0, s>>>(cl, off, ncl); break;
+    case kPhUpdate: k_normal_update_b<<<g, 256, 0, s>>>(cl, off, ncl); break;
+    case kPhSelHist: k_sel_hist_b<<<g, kSelGridThreads, 0, s>>>(cl, off, ncl, arg); break;
+    case kPhSelFind: k_sel_find_b<<<(unsigned)ncl, kSelThreads, 0, s>>>(cl, arg); break;
+    case kPhSelSum: k_sel_sum_b<<<g, kSelGridThreads, 0, s>>>(cl, off, ncl); break;
+    case kPhSelFinal: k_sel_final_b<<<(unsigned)ncl, kSelThreads, 0, s>>>(cl); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

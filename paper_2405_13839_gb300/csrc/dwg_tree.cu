@@ -171,12 +171,13 @@ __global__ void k_tree_records(int64_t nn, const double *A, const double *C, con
 constexpr int kMomThreads = 128;
 constexpr int kMomTile = 2048;  // points per CTA (a multiple of every leaf size)
 
-__global__ void __launch_bounds__(kMomThreads)
-    k_tree_leaf_moments(const float4 *__restrict__ p4, const float4 *__restrict__ nrm, int64_t n,
-                        int64_t nleaf, int bucket, double *M)
+__device__ __forceinline__ void leaf_moments_body(const float4 *__restrict__ p4,
+                                                  const float4 *__restrict__ nrm, int64_t n,
+                                                  int64_t nleaf, int bucket, double *M,
+                                                  int64_t bid)
 {
     __shared__ float4 an[kMomTile];  // (nx, ny, nz, a)
-    const int64_t p0 = (int64_t)blockIdx.x * kMomTile;
+    const int64_t p0 = bid * kMomTile;
     for (int t = threadIdx.x; t < kMomTile; t += kMomThreads) {
         const int64_t j = p0 + t;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kMomThreads)
     __syncthreads();
     const int per = kMomTile / bucket;  // leaves of this tile
     if (threadIdx.x >= per) return;
-    const int64_t b = (int64_t)blockIdx.x * per + threadIdx.x;
+    const int64_t b = bid * per + threadIdx.x;
     if (b >= nleaf) return;
     const int64_t j0 = b * bucket, j1 = min(j0 + bucket, n);
     double mx = 0.0, my = 0.0, mz = 0.0;
@@ -206,21 +207,33 @@ __global__ void __launch_bounds__(kMomThreads)
     M[3 * node + 2] = mz;
 }
 
-__global__ void k_tree_level_moments(int64_t first, double *M)
+__global__ void __launch_bounds__(kMomThreads)
+    k_tree_leaf_moments(const float4 *__restrict__ p4, const float4 *__restrict__ nrm, int64_t n,
+                        int64_t nleaf, int bucket, double *M)
 {
-    int64_t node = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    leaf_moments_body(p4, nrm, n, nleaf, bucket, M, blockIdx.x);
+}
+
+__device__ __forceinline__ void level_moments_body(int64_t first, double *M, int64_t bid)
+{
+    int64_t node = first + bid * blockDim.x + threadIdx.x;
     if (node >= 2 * first) return;
     int64_t l = 2 * node, r = l + 1;
     for (int k = 0; k < 3; ++k) M[3 * node + k] = __dadd_rn(M[3 * l + k], M[3 * r + k]);
 }
 
+__global__ void k_tree_level_moments(int64_t first, double *M)
+{
+    level_moments_body(first, M, blockIdx.x);
+}
+
 // m = M / (4 pi) as float; frec (may be NULL): the node as a 48-byte source
 // record (c and m, each value twice) like the point records, for the list
 // evaluation's bulk copies
-__global__ void k_tree_moment_records(int64_t nn, const double *M, const float4 *rec, float4 *mrec,
-                                      float4 *frec)
+__device__ __forceinline__ void moment_records_body(int64_t nn, const double *M, const float4 *rec,
+                                                    float4 *mrec, float4 *frec, int64_t bid)
 {
-    int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t node = bid * blockDim.x + threadIdx.x;
     if (node >= nn) return;
     const double fpi = 4.0 * kPi;
     const float mx = (float)__ddiv_rn(M[3 * node], fpi), my = (float)__ddiv_rn(M[3 * node + 1], fpi),
@@ -232,6 +245,12 @@ __global__ void k_tree_moment_records(int64_t nn, const double *M, const float4 
         frec[3 * node + 1] = make_float4(c.z, c.z, mx, mx);
         frec[3 * node + 2] = make_float4(my, my, mz, mz);
     }
+}
+
+__global__ void k_tree_moment_records(int64_t nn, const double *M, const float4 *rec, float4 *mrec,
+                                      float4 *frec)
+{
+    moment_records_body(nn, M, rec, mrec, frec, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -858,21 +877,21 @@ __global__ void k_tree_item_table(const int64_t *__restrict__ item_off, int64_t 
 }
 
 template <bool GRAD, bool SCREENED, bool CLAMP = false>
-__global__ void __launch_bounds__(32 * kGrpWarps)
-    k_tree_eval_lists(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ frec,
-                      const float *__restrict__ src, int64_t n, int levels, int bucket,
-                      const int64_t *__restrict__ far_off, const int *__restrict__ far_ids,
-                      const int64_t *__restrict__ near_off, const int *__restrict__ near_ids,
-                      const int2 *__restrict__ items, int64_t nitems, EvalParams ep,
-                      float *__restrict__ ipart, unsigned long long *__restrict__ counter,
-                      const IterState *st)
+__device__ __forceinline__ void eval_lists_body(
+    const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ frec,
+    const float *__restrict__ src, int64_t n, int levels, int bucket,
+    const int64_t *__restrict__ far_off, const int *__restrict__ far_ids,
+    const int64_t *__restrict__ near_off, const int *__restrict__ near_ids,
+    const int2 *__restrict__ items, int64_t nitems, const EvalParams &ep,
+    float *__restrict__ ipart, unsigned long long *__restrict__ counter, const IterState *st,
+    int64_t bid)
 {
     if (st && cloud_idle(st)) return;  // finished cloud of a batch
     constexpr int NA = GRAD ? 4 : 1;
     constexpr int RW = CLAMP ? 4 : 3;  // 16-byte words per staged record
     __shared__ float4 buf_all[kGrpWarps][2][kLstChunk * RW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t it = (int64_t)blockIdx.x * kGrpWarps + wid;
+    const int64_t it = bid * kGrpWarps + wid;
     if (it >= nitems) return;
     const int2 item = items[it];
     const int64_t g = item.x;
@@ -950,16 +969,32 @@ __global__ void __launch_bounds__(32 * kGrpWarps)
     }
 }
 
+template <bool GRAD, bool SCREENED, bool CLAMP = false>
+__global__ void __launch_bounds__(32 * kGrpWarps)
+    k_tree_eval_lists(const float4 *__restrict__ q, int64_t m, const float4 *__restrict__ frec,
+                      const float *__restrict__ src, int64_t n, int levels, int bucket,
+                      const int64_t *__restrict__ far_off, const int *__restrict__ far_ids,
+                      const int64_t *__restrict__ near_off, const int *__restrict__ near_ids,
+                      const int2 *__restrict__ items, int64_t nitems, EvalParams ep,
+                      float *__restrict__ ipart, unsigned long long *__restrict__ counter,
+                      const IterState *st)
+{
+    eval_lists_body<GRAD, SCREENED, CLAMP>(q, m, frec, src, n, levels, bucket, far_off, far_ids,
+                                           near_off, near_ids, items, nitems, ep, ipart, counter,
+                                           st, blockIdx.x);
+}
+
 // per query: the items of its group added in order (two-sum on the hi
 // parts, lo parts summed), written as the chunk-0 partials of the reduce
 template <bool GRAD>
-__global__ void k_tree_combine(const float *__restrict__ ipart, const int64_t *__restrict__ item_off,
-                               int64_t m, float *__restrict__ part, int64_t stride,
-                               const IterState *st)
+__device__ __forceinline__ void combine_body(const float *__restrict__ ipart,
+                                             const int64_t *__restrict__ item_off, int64_t m,
+                                             float *__restrict__ part, int64_t stride,
+                                             const IterState *st, int64_t bid)
 {
     if (st && cloud_idle(st)) return;
     constexpr int NA = GRAD ? 4 : 1;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = bid * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int64_t g = i / kGrpQ, slot = i % kGrpQ;
     float h[NA], l[NA];
@@ -975,6 +1010,14 @@ __global__ void k_tree_combine(const float *__restrict__ ipart, const int64_t *_
         part[(2 * a) * stride + i] = h[a];
         part[(2 * a + 1) * stride + i] = l[a];
     }
+}
+
+template <bool GRAD>
+__global__ void k_tree_combine(const float *__restrict__ ipart, const int64_t *__restrict__ item_off,
+                               int64_t m, float *__restrict__ part, int64_t stride,
+                               const IterState *st)
+{
+    combine_body<GRAD>(ipart, item_off, m, part, stride, st, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1310,6 +1353,118 @@ cudaError_t launch_tree_gwn(Ctx *c, const float4 *q, int64_t m, bool grad, float
                 c->d_counter, c->d_err, st);
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batched phases: every tree cloud of a batch in one launch (each cloud's
+// blocks as in its own launch)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMomThreads)
+    k_tree_leaf_moments_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    leaf_moments_body(c.p4, c.nrm_c, c.n, (int64_t)1 << c.levels, c.bucket, c.tree_M,
+                      (int64_t)blockIdx.x - off[ci]);
+}
+
+__global__ void k_tree_level_moments_b(const CloudIter *__restrict__ cl, const int *__restrict__ off,
+                                       int ncl, int level)
+{
+    const int ci = seg_cloud(off, ncl);
+    level_moments_body((int64_t)1 << level, cl[ci].tree_M, (int64_t)blockIdx.x - off[ci]);
+}
+
+__global__ void k_tree_moment_records_b(const CloudIter *__restrict__ cl, const int *__restrict__ off,
+                                        int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    moment_records_body((int64_t)2 << c.levels, c.tree_M, c.tree_rec, c.tree_mrec, c.tree_frec,
+                        (int64_t)blockIdx.x - off[ci]);
+}
+
+// GRAD: the points (w and grad w), else the corners (w)
+template <bool GRAD, bool SCREENED>
+__global__ void __launch_bounds__(32 * kGrpWarps)
+    k_tree_eval_lists_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    constexpr int w = GRAD ? 0 : 1;
+    eval_lists_body<GRAD, SCREENED>(c.lq[w], c.lm[w], c.tree_frec, c.src, c.n, c.levels, c.bucket,
+                                    c.far_off[w], c.far_ids[w], c.near_off[w], c.near_ids[w],
+                                    c.items[w], c.nitems[w], c.ep, c.ipart[w], c.counter, c.st,
+                                    (int64_t)blockIdx.x - off[ci]);
+}
+
+template <bool GRAD>
+__global__ void k_tree_combine_b(const CloudIter *__restrict__ cl, const int *__restrict__ off,
+                                 int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    constexpr int w = GRAD ? 0 : 1;
+    combine_body<GRAD>(c.ipart[w], c.item_off[w], c.lm[w], c.lpart[w], c.lm[w], c.st,
+                       (int64_t)blockIdx.x - off[ci]);
+}
+
+cudaError_t launch_tree_batch(int phase, const CloudIter *cl, const int *off, int ncl,
+                              int blocks, int level, bool screened, cudaStream_t s)
+{
+    if (blocks <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)blocks;
+    const unsigned T = 32 * kGrpWarps;
+    if (level >= 0) {
+        k_tree_level_moments_b<<<g, 256, 0, s>>>(cl, off, ncl, level);
+        return cudaGetLastError();
+    }
+    switch (phase) {
+    case kPhLeafMom: k_tree_leaf_moments_b<<<g, kMomThreads, 0, s>>>(cl, off, ncl); break;
+    case kPhMomRec: k_tree_moment_records_b<<<g, 256, 0, s>>>(cl, off, ncl); break;
+    case kPhListsP:
+        if (screened) k_tree_eval_lists_b<true, true><<<g, T, 0, s>>>(cl, off, ncl);
+        else k_tree_eval_lists_b<true, false><<<g, T, 0, s>>>(cl, off, ncl);
+        break;
+    case kPhListsC:
+        if (screened) k_tree_eval_lists_b<false, true><<<g, T, 0, s>>>(cl, off, ncl);
+        else k_tree_eval_lists_b<false, false><<<g, T, 0, s>>>(cl, off, ncl);
+        break;
+    case kPhCombineP: k_tree_combine_b<true><<<g, 256, 0, s>>>(cl, off, ncl); break;
+    case kPhCombineC: k_tree_combine_b<false><<<g, 256, 0, s>>>(cl, off, ncl); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// the group lists of the points (corners = false) or the corners hold for
+// the current tree, opening angle and depth (launch_tree_iter's test)
+bool tree_lists_current(const Ctx *c, bool corners)
+{
+    const TreeLists &L = corners ? c->lists_c : c->lists_p;
+    const float4 *q = corners ? c->d_corner_pos : c->d_p4;
+    const int64_t m = corners ? c->ncorners : c->n;
+    return c->tree_group && L.valid && L.q == q && L.m == m && L.key == lists_key(c);
+}
+
+// blocks of a cloud's part in a batched tree phase (0: no part); level >= 0:
+// the moments of that tree level
+int tree_phase_blocks(const Ctx *c, int phase, int level)
+{
+    if (!use_tree(c) || !c->tree_built) return 0;
+    const int64_t nleaf = (int64_t)1 << c->tree_levels, nn = 2 * nleaf;
+    if (level >= 0) return level < c->tree_levels ? (int)ceil_div((int64_t)1 << level, 256) : 0;
+    const bool lists_p = tree_lists_current(c, false);
+    const bool lists_c = c->mode == DWG_UPDATE_LEVELSET && tree_lists_current(c, true);
+    switch (phase) {
+    case kPhLeafMom: return (int)ceil_div(nleaf * c->tree_leaf, kMomTile);
+    case kPhMomRec: return (int)ceil_div(nn, 256);
+    case kPhListsP: return lists_p ? (int)ceil_div(c->lists_p.nitems, kGrpWarps) : 0;
+    case kPhListsC: return lists_c ? (int)ceil_div(c->lists_c.nitems, kGrpWarps) : 0;
+    case kPhCombineP: return lists_p ? (int)ceil_div(c->lists_p.m, 256) : 0;
+    case kPhCombineC: return lists_c ? (int)ceil_div(c->lists_c.m, 256) : 0;
+    default: return 0;
+    }
 }
 
 }  // namespace dwg

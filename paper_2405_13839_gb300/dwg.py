@@ -103,6 +103,7 @@ def _load() -> ctypes.CDLL:
         "dwg_set_update": ([H, I, I, I], I),
         "dwg_set_convergence": ([H, I], I),
         "dwg_set_compensation": ([H, I], I),
+        "dwg_set_batch_mode": ([H, I], I),
         "dwg_set_weights": ([H, P], I),
         "dwg_voronoi_weights": ([H, I, P], I),
         "dwg_selfcheck_wait": ([H, I], I),
@@ -241,6 +242,12 @@ def dwg_set_params(h, kernel, eps, screening, max_iters, tol):
 
 def dwg_set_convergence(h, rule):
     return _raise(h, _lib.dwg_set_convergence(h, int(rule)))
+
+
+def dwg_set_batch_mode(h, phases):
+    """Batch handles: 1 one launch per iteration phase over all clouds
+    (default), 0 one graph branch per cloud."""
+    return _raise(h, _lib.dwg_set_batch_mode(h, int(phases)))
 
 
 def dwg_set_compensation(h, on):

@@ -19,13 +19,19 @@ def _clouds():
     return np.ascontiguousarray(np.vstack(pts)), np.array(offs, np.int64)
 
 
-@pytest.mark.parametrize("path,init", [(1, 0), (2, 0), (1, 3), (2, 4)])
-def test_batch_equals_singles(dwglib, path, init):
-    """init: DWG_INIT_RANDOM (0), DWG_INIT_PCA (3), DWG_INIT_GAUSS (4)."""
+@pytest.mark.parametrize("path,init,knn,phases", [(1, 0, 10, 1), (2, 0, 10, 1), (1, 3, 10, 1),
+                                                  (2, 4, 10, 1), (2, 0, 10, 0), (2, 0, 12, 1)])
+def test_batch_equals_singles(dwglib, path, init, knn, phases):
+    """init: DWG_INIT_RANDOM (0), DWG_INIT_PCA (3), DWG_INIT_GAUSS (4).  With
+    k = 10 every phase of an iteration is one launch over all clouds; with
+    another k, or phases = 0, the clouds' chains run as graph branches."""
     P, off = _clouds()
     nc = len(off) - 1
     hb = dwglib.dwg_create_batch(P, off)
     try:
+        dwglib.dwg_set_batch_mode(hb, phases)
+        if knn != 10:   # one depth for every cloud then (the singles take it too)
+            dwglib.dwg_set_update(hb, 6, knn, dwglib.DWG_UPDATE_LEVELSET)
         dwglib.dwg_set_tree(hb, path, 0.5)
         dwglib.dwg_set_init(hb, init, 11)
         out = np.zeros_like(P)
@@ -39,8 +45,8 @@ def test_batch_equals_singles(dwglib, path, init):
         n = len(p)
         h = dwglib.dwg_create(p)
         try:
-            depth = min(10, max(5, int(round(0.5 * np.log2(max(n, 2))))))
-            dwglib.dwg_set_update(h, depth, 10, dwglib.DWG_UPDATE_LEVELSET)
+            depth = min(10, max(5, int(round(0.5 * np.log2(max(n, 2)))))) if knn == 10 else 6
+            dwglib.dwg_set_update(h, depth, knn, dwglib.DWG_UPDATE_LEVELSET)
             dwglib.dwg_set_tree(h, path, 0.5)
             dwglib.dwg_set_init(h, init, 11 + c)
             o = np.zeros_like(p)
@@ -108,3 +114,29 @@ def test_batch_autotune_per_cloud_then_orient(dwglib):
         d = np.sum(o * nts[c], axis=1)
         s = 1.0 if d.sum() >= 0 else -1.0
         assert np.mean(s * d > 0) >= 0.99, (c, np.mean(s * d > 0))
+
+
+def _kernels_per_iteration(dwglib, clouds, path):
+    P = np.ascontiguousarray(np.vstack(clouds))
+    off = np.cumsum([0] + [len(c) for c in clouds]).astype(np.int64)
+    hb = dwglib.dwg_create_batch(P, off)
+    try:
+        dwglib.dwg_set_params(hb, 1, 0.0, 10.0, 2, 0.1)
+        dwglib.dwg_set_tree(hb, path, 0.5)
+        dwglib.dwg_orient_batch(hb, np.zeros_like(P), len(clouds))
+        return dwglib.dwg_get_stats(hb)["kernels_per_iteration"]
+    finally:
+        dwglib.dwg_destroy(hb)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_launches_per_iteration_do_not_grow_with_the_clouds(dwglib, path):
+    """Every phase of a batched iteration is one launch over all clouds: the
+    iteration graph has as many kernel launches for 16 clouds as for 4 (the
+    tree levels of the moments follow the largest cloud, the same here)."""
+    big = synth.torus(20000, seed=7)[0]
+    small = [synth.sphere(2000, seed=20 + i)[0] for i in range(15)]
+    k4 = _kernels_per_iteration(dwglib, [big] + small[:3], path)
+    k16 = _kernels_per_iteration(dwglib, [big] + small, path)
+    assert k4 == k16, (k4, k16)
+    assert k16 < 4 * 15    # a dozen phases, not a chain per cloud
