@@ -50,9 +50,13 @@ import synth  # noqa: E402
 
 # FP32 operations per interaction in the minimal formulation of each kernel
 # (sub x3, fma x3 for rho^2, mul+fma x2 for <m,d>, then the kernel's own):
-#   w only, plain 12 | w and grad, plain 20 | w only, screened 17 | w and grad, screened 29
-FP32_OPS = {("w", 0): 12, ("wg", 0): 20, ("w", 1): 17, ("wg", 1): 29}
+#   w only, plain 12 | w and grad, plain 20 | w only, screened 16 | w and grad, screened 27
+# (screened: F / rho^3 = e inv^2 (inv + s)), and MUFU operations per
+# interaction (rsqrt; ex2 for the screened kernel)
+FP32_OPS = {("w", 0): 12, ("wg", 0): 20, ("w", 1): 16, ("wg", 1): 27}
+MUFU_OPS = {0: 1, 1: 2}
 FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16
 
 
 def parse():
@@ -548,12 +552,15 @@ def run_ours(args, rank, world, local):
         traffic = bpi * work if (bpi is not None and tuning.get("tree_group")) else None
         traffic_basis = ("ncu dram bytes of k_tree_eval_lists on metaballs-1m per interaction "
                          "(profiles/tree_lists_metaballs1m.md) x this launch's interactions")
-    peak = lanes / ops
+    # the FMA pipe and the MUFU each bound the rate; the lower bound is the peak
+    mufu = MUFU_OPS[kind]
+    peak = min(lanes / ops, sm_count * MUFU_PER_SM * fmax / mufu)
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "Ginteractions/s", "frac": achieved / peak, "traffic": traffic,
             "traffic_basis": traffic_basis,
-            "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {fmax/1e6:.0f} MHz"
-                          f" / {ops} FP32 ops per interaction",
+            "peak_basis": f"min of {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                          f"{fmax/1e6:.0f} MHz / {ops} FP32 ops and {sm_count} SMs x "
+                          f"{MUFU_PER_SM} MUFU x {fmax/1e6:.0f} MHz / {mufu} MUFU ops per interaction",
             "kernel_ms": {k: round(v, 4) for k, v in kms.items()},
             "share": {k: round(v / iter_ms, 4) for k, v in kms.items()}}
     # the same denominator measured: packed-FMA and MUFU rsqrt microbenchmarks
@@ -562,7 +569,8 @@ def run_ours(args, rank, world, local):
         roof["fp32_measured"] = {
             "ffma_lane_ops_per_s": ffma, "rsqrt_per_s": rsq,
             "derived_lane_ops_per_s": lanes, "ffma_over_derived": ffma / lanes,
-            "peak_from_measured": ffma / ops / 1e9, "frac_of_measured": achieved / (ffma / ops)}
+            "peak_from_measured": min(ffma / ops, rsq / mufu) / 1e9,
+            "frac_of_measured": achieved / min(ffma / ops, rsq / mufu)}
     except Exception as e:  # reported beside the derived peak, never instead of it
         roof["fp32_measured"] = {"error": str(e)}
 
@@ -794,19 +802,19 @@ def run_batch(args, rank=0, world=1, local=0):
     ck = clocks.stop()
     o = out.cpu().numpy()
     ags = [agreement(o[off[c]:off[c + 1]], nt[off[c]:off[c + 1]]) for c in range(nc)]
-    # the same orientation with each cloud's chain as a graph branch instead
-    # of one launch per phase (untimed by the line; same results)
-    dwg.dwg_set_batch_mode(hb, 0)
-    dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
-    dwg.dwg_orient_batch(hb, out, nc)   # captures the branch graph
-    dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
-    dwg.dwg_orient_batch(hb, out, nc)
-    branches_s = dwg.dwg_get_stats(hb)["ms_orient"] / 1e3
-    kpi_branches = dwg.dwg_get_stats(hb)["kernels_per_iteration"]
-    dwg.dwg_set_batch_mode(hb, 1)
-    dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
-    dwg.dwg_orient_batch(hb, out, nc)
-    kpi_phases = dwg.dwg_get_stats(hb)["kernels_per_iteration"]
+    # the same orientation in the other batch modes (untimed by the line; the
+    # same results): batched phases on 1 and 8 lanes, and each cloud's chain
+    # as a graph branch
+    modes = {"phases_4_lanes": (dwg.dwg_get_stats(hb)["kernels_per_iteration"], sum(ms) / 1e3 / args.steps)}
+    for name, lanes in (("phases_1_lane", 1), ("phases_8_lanes", 8), ("branches", 0)):
+        dwg.dwg_set_batch_mode(hb, lanes)
+        dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
+        dwg.dwg_orient_batch(hb, out, nc)   # captures the mode's graph
+        dwg.dwg_set_init(hb, dwg.DWG_INIT_RANDOM, 1)
+        dwg.dwg_orient_batch(hb, out, nc)
+        st = dwg.dwg_get_stats(hb)
+        modes[name] = (st["kernels_per_iteration"], st["ms_orient"] / 1e3)
+    dwg.dwg_set_batch_mode(hb, 4)
     # the other initialisations on every cloud (one run each): the learned
     # warm start and the paper's PCA and Gauss-map options
     from paper_2405_13839_gb300 import train_init
@@ -868,8 +876,8 @@ def run_batch(args, rank=0, world=1, local=0):
             "agreement": {"min": min(ags), "mean": float(np.mean(ags)),
                           "clouds_at_least_99pct": int(sum(a >= 0.99 for a in ags))},
             "warm_start": warm,
-            "batch_modes": {"phases": {"s": dev_s / args.steps, "kernels_per_iteration": kpi_phases},
-                            "branches": {"s": branches_s, "kernels_per_iteration": kpi_branches}},
+            "batch_modes": {k: {"s": s_m, "kernels_per_iteration": k_m}
+                            for k, (k_m, s_m) in modes.items()},
             "clocks": ck}
     print(json.dumps(line))
 

@@ -150,17 +150,24 @@ int dwg_set_compensation(dwg_handle h, int on);
 
 /*
  * How a batch handle (dwg_create_batch) runs an iteration of all its clouds
- * (the paper orients one cloud; batching is this library's): phases = 1 (the
- * default): every phase of the iteration -- Barnes-Hut moments per tree
- * level, list evaluations, reduce, iso-value, level set, kNN scatter, update,
- * the convergence select -- is one launch over every cloud's blocks, so the
- * launches per iteration do not grow with the number of clouds; phases = 0:
- * each cloud's chain of launches is a branch of the iteration graph on its
- * own stream.  Both give every cloud the same bits as orienting it alone.
- * The phases need k = 10 and the softened kernel in every cloud; otherwise
- * the branches run.  Not a batch handle: DWG_ERR_STATE.
+ * (the paper orients one cloud; batching is this library's).
+ *   lanes in [1, DWG_MAX_BATCH_LANES] (default 4): batched phases.  The
+ *     clouds are split into min(lanes, clouds) groups of about equal work;
+ *     within a group every phase of the iteration -- Barnes-Hut moments per
+ *     tree level, list evaluations, reduce, iso-value, level set, kNN
+ *     scatter, update, the convergence select -- is one launch over all the
+ *     group's clouds, and the groups run concurrently as branches of the
+ *     iteration graph.  The launches per iteration grow with the lanes and
+ *     the deepest tree, not with the number of clouds.
+ *   lanes = 0: each cloud's chain of launches is a branch of the iteration
+ *     graph on its own stream.
+ * Every mode gives every cloud the same bits as orienting it alone.  The
+ * batched phases need k = 10 and the softened kernel in every cloud;
+ * otherwise the per-cloud branches run.  Not a batch handle: DWG_ERR_STATE;
+ * lanes out of range: DWG_ERR_INVALID.
  */
-int dwg_set_batch_mode(dwg_handle h, int phases);
+#define DWG_MAX_BATCH_LANES 16
+int dwg_set_batch_mode(dwg_handle h, int lanes);
 
 /*
  * Discretisation and update rule.

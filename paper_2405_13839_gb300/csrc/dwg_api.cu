@@ -29,14 +29,22 @@ struct dwg_ctx : public Ctx {
     // fork / join of the clouds' chains in a batch iteration (each cloud runs
     // on its own stream, so the graph holds one branch per cloud)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // batched phases: the clouds' argument table and, per phase and per tree
-    // level, the offsets of each cloud's blocks in the phase's grid
+    // batched phases: the clouds are split over a few lanes (streams); in
+    // each lane every phase is one launch over the lane's clouds.  The
+    // clouds' argument table (lane by lane) and, per lane, phase and tree
+    // level, the offsets of each cloud's blocks in the phase's grid.
+    struct Lane {
+        std::vector<dwg_ctx *> clouds;
+        int base = 0;                  // first entry of the lane in d_citer
+        size_t off_base = 0;           // first offset of the lane in d_boff
+        int ph_blocks[kPhCount] = {};
+        std::vector<int> lv_blocks;    // per tree level
+        std::vector<dwg_ctx *> walk_p, walk_c;  // tree clouds without current lists
+    };
+    std::vector<Lane> lanes;
     CloudIter *d_citer = nullptr;
-    int *d_boff = nullptr;             // (kPhCount + tree levels) x (clouds + 1)
-    int ph_blocks[kPhCount] = {};
-    std::vector<int> lv_blocks;        // per tree level
+    int *d_boff = nullptr;
     bool batched = false;              // the batched phases apply (uniform settings)
-    std::vector<dwg_ctx *> walk_p, walk_c;  // tree clouds without current lists
 };
 
 static std::mutex g_err_mu;
@@ -712,13 +720,14 @@ int dwg_set_convergence(dwg_handle h, int rule)
     return DWG_OK;
 }
 
-int dwg_set_batch_mode(dwg_handle h, int phases)
+int dwg_set_batch_mode(dwg_handle h, int lanes)
 {
     if (!h) return DWG_ERR_INVALID;
     if (!h->is_batch) return fail(h, DWG_ERR_STATE, "dwg_set_batch_mode needs a batch handle");
-    if (phases != 0 && phases != 1) return fail(h, DWG_ERR_INVALID, "phases must be 0 or 1");
-    if (h->batch_phases != phases) {
-        h->batch_phases = phases;
+    if (lanes < 0 || lanes > DWG_MAX_BATCH_LANES)
+        return fail(h, DWG_ERR_INVALID, "lanes must be in [0, DWG_MAX_BATCH_LANES]");
+    if (h->batch_phases != lanes) {
+        h->batch_phases = lanes;
         invalidate_graph(h);
     }
     return DWG_OK;
@@ -1613,42 +1622,67 @@ static int batch_plan(dwg_ctx *h)
 {
     const int ncl = (int)h->clouds.size();
     h->batched = false;
-    h->walk_p.clear();
-    h->walk_c.clear();
+    h->lanes.clear();
     if (!h->batch_phases) return DWG_OK;
     for (const dwg_ctx *c : h->clouds)
         if (c->knn != 10 || c->reg_mode != DWG_REG_SOFTEN) return DWG_OK;
-    std::vector<CloudIter> tab(ncl);
-    int maxL = 0;
-    for (int i = 0; i < ncl; ++i) {
-        dwg_ctx *c = h->clouds[i];
-        fill_cloud_iter(c, &tab[i]);
-        if (use_tree(c)) {
-            maxL = std::max(maxL, c->tree_levels);
-            if (!tree_lists_current(c, false)) h->walk_p.push_back(c);
-            if (c->mode == DWG_UPDATE_LEVELSET && !tree_lists_current(c, true))
-                h->walk_c.push_back(c);
-        }
+    // lanes balanced by an estimate of each cloud's per-iteration work
+    // (largest first onto the least loaded lane); a tree cloud's list
+    // evaluations dominate its share, an all-pairs cloud's sums run in the
+    // shared launch before the lanes
+    const int nl = std::min(h->batch_phases, ncl);
+    h->lanes.assign(nl, dwg_ctx::Lane());
+    std::vector<int> order(ncl);
+    for (int i = 0; i < ncl; ++i) order[i] = i;
+    auto work = [&](int i) {
+        const dwg_ctx *c = h->clouds[i];
+        return (double)c->n * (use_tree(c) ? 32.0 : 1.0);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<double> load(nl, 0.0);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[l] += work(i);
+        h->lanes[l].clouds.push_back(h->clouds[i]);
     }
-    const int rows = kPhCount + maxL;
-    std::vector<int> off((size_t)rows * (ncl + 1), 0);
-    h->lv_blocks.assign(maxL, 0);
-    for (int r = 0; r < rows; ++r) {
-        int *o = off.data() + (size_t)r * (ncl + 1);
-        for (int i = 0; i < ncl; ++i) {
-            const dwg_ctx *c = h->clouds[i];
-            const int b = r < kPhCount ? phase_blocks(c, r) : tree_phase_blocks(c, 0, r - kPhCount);
-            o[i + 1] = o[i] + b;
+    std::vector<CloudIter> tab;
+    std::vector<int> off;
+    for (auto &L : h->lanes) {
+        const int m = (int)L.clouds.size();
+        L.base = (int)tab.size();
+        L.off_base = off.size();
+        int maxL = 0;
+        for (dwg_ctx *c : L.clouds) {
+            tab.emplace_back();
+            fill_cloud_iter(c, &tab.back());
+            if (use_tree(c)) {
+                maxL = std::max(maxL, c->tree_levels);
+                if (!tree_lists_current(c, false)) L.walk_p.push_back(c);
+                if (c->mode == DWG_UPDATE_LEVELSET && !tree_lists_current(c, true))
+                    L.walk_c.push_back(c);
+            }
         }
-        if (r < kPhCount) h->ph_blocks[r] = o[ncl];
-        else h->lv_blocks[r - kPhCount] = o[ncl];
+        const int rows = kPhCount + maxL;
+        L.lv_blocks.assign(maxL, 0);
+        for (int r = 0; r < rows; ++r) {
+            const size_t row0 = off.size();
+            off.push_back(0);
+            for (int i = 0; i < m; ++i) {
+                const dwg_ctx *c = L.clouds[i];
+                const int b =
+                    r < kPhCount ? phase_blocks(c, r) : tree_phase_blocks(c, 0, r - kPhCount);
+                off.push_back(off[row0 + i] + b);
+            }
+            if (r < kPhCount) L.ph_blocks[r] = off.back();
+            else L.lv_blocks[r - kPhCount] = off.back();
+        }
     }
     cudaFree(h->d_citer);
     cudaFree(h->d_boff);
     h->d_citer = nullptr;
     h->d_boff = nullptr;
-    DWG_CUDA_TRY(h, cudaMalloc(&h->d_citer, ncl * sizeof(CloudIter)));
-    DWG_CUDA_TRY(h, cudaMemcpy(h->d_citer, tab.data(), ncl * sizeof(CloudIter),
+    DWG_CUDA_TRY(h, cudaMalloc(&h->d_citer, tab.size() * sizeof(CloudIter)));
+    DWG_CUDA_TRY(h, cudaMemcpy(h->d_citer, tab.data(), tab.size() * sizeof(CloudIter),
                                cudaMemcpyHostToDevice));
     DWG_CUDA_TRY(h, cudaMalloc(&h->d_boff, off.size() * sizeof(int)));
     DWG_CUDA_TRY(h, cudaMemcpy(h->d_boff, off.data(), off.size() * sizeof(int),
@@ -1723,57 +1757,82 @@ static int batch_tables(dwg_ctx *h)
 // results are the same bits as orienting the cloud alone.  Tree clouds whose
 // interaction lists are not resident (they would not fit) walk the tree in
 // launches of their own.
-static int batch_body_phases(dwg_ctx *h)
+static cudaError_t batch_lane_phases(dwg_ctx *h, const dwg_ctx::Lane &L, bool scr,
+                                     cudaStream_t s)
 {
-    const bool scr = h->kernel == DWG_KERNEL_SCREENED && h->lambda > 0.f;
-    const int ncl = (int)h->clouds.size();
-    cudaStream_t s = h->stream;
-    const CloudIter *cl = h->d_citer;
-    auto off = [&](int row) { return h->d_boff + (size_t)row * (ncl + 1); };
+    const int ncl = (int)L.clouds.size();
+    const CloudIter *cl = h->d_citer + L.base;
+    const int *ph = L.ph_blocks;
+    auto off = [&](int row) { return h->d_boff + L.off_base + (size_t)row * (ncl + 1); };
     cudaError_t e = cudaSuccess;
     auto ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-    ok(launch_gwn_batch(h->d_bcl_p, h->d_bit_p, h->nit_p, true, scr, h->d_err, s));
-    ok(launch_gwn_batch(h->d_bcl_c, h->d_bit_c, h->nit_c, false, scr, h->d_err, s));
     // Barnes-Hut moments: leaves, then each tree level from the bottom up
-    ok(launch_tree_batch(kPhLeafMom, cl, off(kPhLeafMom), ncl, h->ph_blocks[kPhLeafMom], -1, scr, s));
-    for (int lv = (int)h->lv_blocks.size() - 1; lv >= 0; --lv)
-        ok(launch_tree_batch(kPhLeafMom, cl, off(kPhCount + lv), ncl, h->lv_blocks[lv], lv, scr, s));
-    ok(launch_tree_batch(kPhMomRec, cl, off(kPhMomRec), ncl, h->ph_blocks[kPhMomRec], -1, scr, s));
+    ok(launch_tree_batch(kPhLeafMom, cl, off(kPhLeafMom), ncl, ph[kPhLeafMom], -1, scr, s));
+    for (int lv = (int)L.lv_blocks.size() - 1; lv >= 0; --lv)
+        ok(launch_tree_batch(kPhLeafMom, cl, off(kPhCount + lv), ncl, L.lv_blocks[lv], lv, scr, s));
+    ok(launch_tree_batch(kPhMomRec, cl, off(kPhMomRec), ncl, ph[kPhMomRec], -1, scr, s));
     // w and grad w at the points
-    ok(launch_tree_batch(kPhListsP, cl, off(kPhListsP), ncl, h->ph_blocks[kPhListsP], -1, scr, s));
-    ok(launch_tree_batch(kPhCombineP, cl, off(kPhCombineP), ncl, h->ph_blocks[kPhCombineP], -1,
-                         scr, s));
-    for (dwg_ctx *c : h->walk_p) {
+    ok(launch_tree_batch(kPhListsP, cl, off(kPhListsP), ncl, ph[kPhListsP], -1, scr, s));
+    ok(launch_tree_batch(kPhCombineP, cl, off(kPhCombineP), ncl, ph[kPhCombineP], -1, scr, s));
+    for (dwg_ctx *c : L.walk_p) {
         c->stream = s;
         ok(launch_tree_iter(c, c->lists_p, c->d_p4, c->n, true, c->d_part_p, c->n, c->d_state));
     }
-    ok(launch_eval_batch(kPhReducePoints, cl, off(kPhReducePoints), ncl,
-                         h->ph_blocks[kPhReducePoints], s));
-    ok(launch_iter_batch(kPhIso, cl, off(kPhIso), ncl, h->ph_blocks[kPhIso], 0, s));
+    ok(launch_eval_batch(kPhReducePoints, cl, off(kPhReducePoints), ncl, ph[kPhReducePoints], s));
+    ok(launch_iter_batch(kPhIso, cl, off(kPhIso), ncl, ph[kPhIso], 0, s));
     // w at the corners, level set, face gradients to the k nearest points
-    ok(launch_tree_batch(kPhListsC, cl, off(kPhListsC), ncl, h->ph_blocks[kPhListsC], -1, scr, s));
-    ok(launch_tree_batch(kPhCombineC, cl, off(kPhCombineC), ncl, h->ph_blocks[kPhCombineC], -1,
-                         scr, s));
-    for (dwg_ctx *c : h->walk_c) {
+    ok(launch_tree_batch(kPhListsC, cl, off(kPhListsC), ncl, ph[kPhListsC], -1, scr, s));
+    ok(launch_tree_batch(kPhCombineC, cl, off(kPhCombineC), ncl, ph[kPhCombineC], -1, scr, s));
+    for (dwg_ctx *c : L.walk_c) {
         c->stream = s;
         ok(launch_tree_iter(c, c->lists_c, c->d_corner_pos, c->ncorners, false, c->d_part_c,
                             c->ncorners, c->d_state));
     }
-    ok(launch_eval_batch(kPhReduceW, cl, off(kPhReduceW), ncl, h->ph_blocks[kPhReduceW], s));
-    ok(launch_iter_batch(kPhMcFaces, cl, off(kPhMcFaces), ncl, h->ph_blocks[kPhMcFaces], 0, s));
-    ok(launch_iter_batch(kPhKnn, cl, off(kPhKnn), ncl, h->ph_blocks[kPhKnn], 0, s));
+    ok(launch_eval_batch(kPhReduceW, cl, off(kPhReduceW), ncl, ph[kPhReduceW], s));
+    ok(launch_iter_batch(kPhMcFaces, cl, off(kPhMcFaces), ncl, ph[kPhMcFaces], 0, s));
+    ok(launch_iter_batch(kPhKnn, cl, off(kPhKnn), ncl, ph[kPhKnn], 0, s));
     // normal update and convergence
-    ok(launch_iter_batch(kPhUpdate, cl, off(kPhUpdate), ncl, h->ph_blocks[kPhUpdate], 0, s));
+    ok(launch_iter_batch(kPhUpdate, cl, off(kPhUpdate), ncl, ph[kPhUpdate], 0, s));
     for (int level = 0; level < 3; ++level) {
-        ok(launch_iter_batch(kPhSelHist, cl, off(kPhSelHist), ncl, h->ph_blocks[kPhSelHist],
-                             level, s));
-        ok(launch_iter_batch(kPhSelFind, cl, off(kPhSelFind), ncl, h->ph_blocks[kPhSelFind],
-                             level, s));
+        ok(launch_iter_batch(kPhSelHist, cl, off(kPhSelHist), ncl, ph[kPhSelHist], level, s));
+        ok(launch_iter_batch(kPhSelFind, cl, off(kPhSelFind), ncl, ph[kPhSelFind], level, s));
     }
-    ok(launch_iter_batch(kPhSelSum, cl, off(kPhSelSum), ncl, h->ph_blocks[kPhSelSum], 0, s));
-    ok(launch_iter_batch(kPhSelFinal, cl, off(kPhSelFinal), ncl, h->ph_blocks[kPhSelFinal], 0, s));
-    if (e != cudaSuccess)
-        return fail(h, DWG_ERR_CUDA, std::string("batched phase launch: ") + cudaGetErrorString(e));
+    ok(launch_iter_batch(kPhSelSum, cl, off(kPhSelSum), ncl, ph[kPhSelSum], 0, s));
+    ok(launch_iter_batch(kPhSelFinal, cl, off(kPhSelFinal), ncl, ph[kPhSelFinal], 0, s));
+    return e;
+}
+
+static int batch_body_phases(dwg_ctx *h)
+{
+    const bool scr = h->kernel == DWG_KERNEL_SCREENED && h->lambda > 0.f;
+    cudaStream_t s = h->stream;
+    if (launch_gwn_batch(h->d_bcl_p, h->d_bit_p, h->nit_p, true, scr, h->d_err, s) !=
+            cudaSuccess ||
+        launch_gwn_batch(h->d_bcl_c, h->d_bit_c, h->nit_c, false, scr, h->d_err, s) !=
+            cudaSuccess)
+        return fail(h, DWG_ERR_CUDA, "batched gwn launch failed");
+    if (h->lanes.size() == 1) {
+        cudaError_t e = batch_lane_phases(h, h->lanes[0], scr, s);
+        if (e != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, std::string("batched phase launch: ") + cudaGetErrorString(e));
+        return DWG_OK;
+    }
+    // each lane on the stream of its first cloud, forked from and joined
+    // back into the batch stream
+    if (!h->ev_fork)
+        DWG_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    DWG_CUDA_TRY(h, cudaEventRecord(h->ev_fork, s));
+    for (const auto &L : h->lanes) {
+        dwg_ctx *c0 = L.clouds[0];
+        if (!c0->ev_join)
+            DWG_CUDA_TRY(h, cudaEventCreateWithFlags(&c0->ev_join, cudaEventDisableTiming));
+        DWG_CUDA_TRY(h, cudaStreamWaitEvent(c0->own_stream, h->ev_fork, 0));
+        cudaError_t e = batch_lane_phases(h, L, scr, c0->own_stream);
+        if (e != cudaSuccess)
+            return fail(h, DWG_ERR_CUDA, std::string("batched phase launch: ") + cudaGetErrorString(e));
+        DWG_CUDA_TRY(h, cudaEventRecord(c0->ev_join, c0->own_stream));
+        DWG_CUDA_TRY(h, cudaStreamWaitEvent(s, c0->ev_join, 0));
+    }
     return DWG_OK;
 }
 

@@ -312,8 +312,8 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                     md = fma2(r2v.x, dy, md);
                     md = fma2(r2v.y, dz, md);
                     f2 i2 = mul2(inv, inv);
-                    f2 i3 = mul2(i2, inv);
                     if (!SCREENED) {
+                        f2 i3 = mul2(i2, inv);
                         if (GRAD) {
                             f2 phi = mul2(md, i3);
                             tw[p] = add2(tw[p], phi);
@@ -329,22 +329,24 @@ __device__ __forceinline__ void gwn_block(const float *__restrict__ src, int64_t
                             tw[p] = fma2(md, i3, tw[p]);
                         }
                     } else {
+                        // g = F / rho^3 = e^(-s rho) (1 + s rho) / rho^3
+                        //   = e inv^2 (inv + s)
                         f2 rho = mul2(rr, inv);
                         f2 e = ex22(mul2(rho, nl2e));
-                        f2 F = fma2(e, mul2(rho, sv), e);
-                        f2 phi = mul2(md, i3);
-                        tw[p] = fma2(F, phi, tw[p]);
+                        f2 g = mul2(mul2(i2, add2(inv, sv)), e);
+                        tw[p] = fma2(g, md, tw[p]);
                         if (GRAD) {
-                            f2 fi3 = mul2(F, i3);
-                            f2 cc = fma2(three, mul2(F, i2), mul2(s2v, e));
-                            f2 c = mul2(phi, cc);
+                            // md (3 F / rho^5 + s^2 e / rho^3)
+                            //   = md inv^2 (3 g + s^2 e inv)
+                            f2 cc = fma2(three, g, mul2(e, mul2(s2v, inv)));
+                            f2 c = mul2(md, mul2(i2, cc));
                             if (CLAMP) c = keep_ge(c, r2raw, d2c);
                             t1x[p] = fma2(c, dx, t1x[p]);
                             t1y[p] = fma2(c, dy, t1y[p]);
                             t1z[p] = fma2(c, dz, t1z[p]);
-                            t2x[p] = fma2(r1.y, fi3, t2x[p]);
-                            t2y[p] = fma2(r2v.x, fi3, t2y[p]);
-                            t2z[p] = fma2(r2v.y, fi3, t2z[p]);
+                            t2x[p] = fma2(r1.y, g, t2x[p]);
+                            t2y[p] = fma2(r2v.x, g, t2y[p]);
+                            t2z[p] = fma2(r2v.y, g, t2z[p]);
                         }
                     }
                 }
@@ -728,18 +730,17 @@ __device__ __forceinline__ void reduce_points_body(const float *__restrict__ par
             }
         if (GRAD && self_mode != 0) {
             // The coincident sources' gradient term is -(F inv^3) m with
-            // rho = eps; add it back so that those sources are skipped.
+            // rho = eps; add it back so that those sources are skipped
+            // (the factor rounded as the evaluators round it).
             float4 qi = q[i];
-            float inv = rsqrt_mufu(ep.eps2);
-            float i2 = inv * inv;
-            float i3 = i2 * inv;
-            float fi3 = i3;
-            if (ep.screened) {
-                float rho = ep.eps2 * inv;
-                float e = ex2_mufu(rho * ep.nl2e_s);
-                float F = fmaf(e, rho * ep.s, e);
-                fi3 = F * i3;
-            }
+            auto factor = [&](float rr) {
+                const float inv = rsqrt_mufu(rr);
+                const float i2 = inv * inv;
+                if (!ep.screened) return i2 * inv;
+                const float e = ex2_mufu((rr * inv) * ep.nl2e_s);
+                return (i2 * (inv + ep.s)) * e;
+            };
+            float fi3 = factor(ep.eps2);
             int64_t lo_j, hi_j;
             if (self_mode == 1) {  // queries are the sources, same order
                 lo_j = i;
@@ -765,14 +766,7 @@ __device__ __forceinline__ void reduce_points_body(const float *__restrict__ par
                 if (r[0] == qi.x && r[2] == qi.y && r[4] == qi.z) {
                     if (rec_floats == kSrcFloatsClamp) {
                         // modified kernel: this source's rho is its own delta_j
-                        const float d2 = r[12];
-                        const float dinv = rsqrt_mufu(d2);
-                        fi3 = dinv * dinv * dinv;
-                        if (ep.screened) {
-                            float rho = d2 * dinv;
-                            float e = ex2_mufu(rho * ep.nl2e_s);
-                            fi3 *= fmaf(e, rho * ep.s, e);
-                        }
+                        fi3 = factor(r[12]);
                     }
                     two_sum1(h[1], l[1], r[6] * fi3);
                     two_sum1(h[2], l[2], r[8] * fi3);

@@ -304,7 +304,7 @@ struct Ctx {
     float tree_beta = 2.0f;            // 1 / opening angle
     int tree_leaf = 16;                // points per tree leaf (16, 32, 64 or 128)
     int tree_group = 1;                // 1: opening test per 64-query group, 0: per query
-    int batch_phases = 1;              // batch handles: 1 one launch per phase, 0 branches
+    int batch_phases = 4;              // batch handles: lanes of batched phases, 0 branches
     uint64_t tree_gen = 0;             // counts tree builds
     TreeLists lists_p, lists_c;        // group-test lists at the points and corners
     int tree_levels = 0;               // 2^tree_levels leaves

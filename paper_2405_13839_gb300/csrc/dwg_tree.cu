@@ -297,8 +297,9 @@ __device__ __forceinline__ void tree_term(TreeAcc &A, float qx, float qy, float 
     if (CLAMP) rr = fmaxf(rr, d2);
     float inv = rsqrt_approx(rr);
     float md = fmaf(mz, dz, fmaf(my, dy, mx * dx));
-    float i2 = inv * inv, i3 = i2 * inv;
+    float i2 = inv * inv;
     if (!SCREENED) {
+        float i3 = i2 * inv;
         float phi = md * i3;
         A.tw += phi;
         if (GRAD) {
@@ -307,17 +308,16 @@ __device__ __forceinline__ void tree_term(TreeAcc &A, float qx, float qy, float 
             A.t2x = fmaf(mx, i3, A.t2x); A.t2y = fmaf(my, i3, A.t2y); A.t2z = fmaf(mz, i3, A.t2z);
         }
     } else {
+        // g = F / rho^3 = e inv^2 (inv + s), as the packed evaluators
         float rho = rr * inv;
         float e = ex2_approx(rho * ep.nl2e_s);
-        float F = fmaf(e, rho * ep.s, e);
-        float phi = md * i3;
-        A.tw = fmaf(F, phi, A.tw);
+        float g = (i2 * (inv + ep.s)) * e;
+        A.tw = fmaf(g, md, A.tw);
         if (GRAD) {
-            float fi3 = F * i3;
-            float cc = fmaf(3.f, F * i2, ep.s2 * e);
-            float c = outside ? phi * cc : 0.f;
+            float cc = fmaf(3.f, g, e * (ep.s2 * inv));
+            float c = outside ? md * (i2 * cc) : 0.f;
             A.t1x = fmaf(c, dx, A.t1x); A.t1y = fmaf(c, dy, A.t1y); A.t1z = fmaf(c, dz, A.t1z);
-            A.t2x = fmaf(mx, fi3, A.t2x); A.t2y = fmaf(my, fi3, A.t2y); A.t2z = fmaf(mz, fi3, A.t2z);
+            A.t2x = fmaf(mx, g, A.t2x); A.t2y = fmaf(my, g, A.t2y); A.t2z = fmaf(mz, g, A.t2z);
         }
     }
     A.pending++;
@@ -484,8 +484,8 @@ __device__ __forceinline__ void pair_term(PairSums &T, const ulonglong2 &r0, con
     md = fma2(r2v.x, dy, md);
     md = fma2(r2v.y, dz, md);
     f2 i2 = mul2(inv, inv);
-    f2 i3 = mul2(i2, inv);
     if (!SCREENED) {
+        f2 i3 = mul2(i2, inv);
         if (GRAD) {
             f2 phi = mul2(md, i3);
             T.tw = add2(T.tw, phi);
@@ -501,22 +501,22 @@ __device__ __forceinline__ void pair_term(PairSums &T, const ulonglong2 &r0, con
             T.tw = fma2(md, i3, T.tw);
         }
     } else {
+        // g = F / rho^3 = e inv^2 (inv + s); the gradient's coefficient
+        // md (3 F / rho^5 + s^2 e / rho^3) = md inv^2 (3 g + s^2 e inv)
         f2 rho = mul2(rr, inv);
         f2 e = ex22(mul2(rho, nl2e));
-        f2 F = fma2(e, mul2(rho, sv), e);
-        f2 phi = mul2(md, i3);
-        T.tw = fma2(F, phi, T.tw);
+        f2 g = mul2(mul2(i2, add2(inv, sv)), e);
+        T.tw = fma2(g, md, T.tw);
         if (GRAD) {
-            f2 fi3 = mul2(F, i3);
-            f2 cc = fma2(three, mul2(F, i2), mul2(s2v, e));
-            f2 c = mul2(phi, cc);
+            f2 cc = fma2(three, g, mul2(e, mul2(s2v, inv)));
+            f2 c = mul2(md, mul2(i2, cc));
             if (CLAMP) c = keep_ge(c, r2raw, d2c);
             T.t1x = fma2(c, dx, T.t1x);
             T.t1y = fma2(c, dy, T.t1y);
             T.t1z = fma2(c, dz, T.t1z);
-            T.t2x = fma2(r1.y, fi3, T.t2x);
-            T.t2y = fma2(r2v.x, fi3, T.t2y);
-            T.t2z = fma2(r2v.y, fi3, T.t2z);
+            T.t2x = fma2(r1.y, g, T.t2x);
+            T.t2y = fma2(r2v.x, g, T.t2y);
+            T.t2z = fma2(r2v.y, g, T.t2z);
         }
     }
 }

@@ -38,6 +38,7 @@ DWG_REG_CLAMP = 1
 MLP_PARAMS = 12675
 DWG_CONV_TOP1 = 0
 DWG_CONV_MEAN = 1
+DWG_MAX_BATCH_LANES = 16
 DWG_PATH_AUTO = 0
 DWG_PATH_ALLPAIRS = 1
 DWG_PATH_TREE = 2
@@ -244,10 +245,11 @@ def dwg_set_convergence(h, rule):
     return _raise(h, _lib.dwg_set_convergence(h, int(rule)))
 
 
-def dwg_set_batch_mode(h, phases):
-    """Batch handles: 1 one launch per iteration phase over all clouds
-    (default), 0 one graph branch per cloud."""
-    return _raise(h, _lib.dwg_set_batch_mode(h, int(phases)))
+def dwg_set_batch_mode(h, lanes):
+    """Batch handles: lanes >= 1 batched phases (one launch per phase over a
+    lane's clouds, lanes concurrent; default 4), 0 one graph branch per
+    cloud."""
+    return _raise(h, _lib.dwg_set_batch_mode(h, int(lanes)))
 
 
 def dwg_set_compensation(h, on):

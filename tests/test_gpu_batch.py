@@ -19,12 +19,14 @@ def _clouds():
     return np.ascontiguousarray(np.vstack(pts)), np.array(offs, np.int64)
 
 
-@pytest.mark.parametrize("path,init,knn,phases", [(1, 0, 10, 1), (2, 0, 10, 1), (1, 3, 10, 1),
-                                                  (2, 4, 10, 1), (2, 0, 10, 0), (2, 0, 12, 1)])
+@pytest.mark.parametrize("path,init,knn,phases", [(1, 0, 10, 4), (2, 0, 10, 4), (1, 3, 10, 4),
+                                                  (2, 4, 10, 4), (2, 0, 10, 1), (1, 0, 10, 3),
+                                                  (2, 0, 10, 0), (2, 0, 12, 4)])
 def test_batch_equals_singles(dwglib, path, init, knn, phases):
     """init: DWG_INIT_RANDOM (0), DWG_INIT_PCA (3), DWG_INIT_GAUSS (4).  With
-    k = 10 every phase of an iteration is one launch over all clouds; with
-    another k, or phases = 0, the clouds' chains run as graph branches."""
+    k = 10 every phase of an iteration is one launch over the clouds of a
+    lane (phases = lanes); with another k, or phases = 0, the clouds' chains
+    run as graph branches."""
     P, off = _clouds()
     nc = len(off) - 1
     hb = dwglib.dwg_create_batch(P, off)
@@ -116,11 +118,12 @@ def test_batch_autotune_per_cloud_then_orient(dwglib):
         assert np.mean(s * d > 0) >= 0.99, (c, np.mean(s * d > 0))
 
 
-def _kernels_per_iteration(dwglib, clouds, path):
+def _kernels_per_iteration(dwglib, clouds, path, lanes):
     P = np.ascontiguousarray(np.vstack(clouds))
     off = np.cumsum([0] + [len(c) for c in clouds]).astype(np.int64)
     hb = dwglib.dwg_create_batch(P, off)
     try:
+        dwglib.dwg_set_batch_mode(hb, lanes)
         dwglib.dwg_set_params(hb, 1, 0.0, 10.0, 2, 0.1)
         dwglib.dwg_set_tree(hb, path, 0.5)
         dwglib.dwg_orient_batch(hb, np.zeros_like(P), len(clouds))
@@ -131,12 +134,15 @@ def _kernels_per_iteration(dwglib, clouds, path):
 
 @pytest.mark.parametrize("path", [1, 2])
 def test_launches_per_iteration_do_not_grow_with_the_clouds(dwglib, path):
-    """Every phase of a batched iteration is one launch over all clouds: the
-    iteration graph has as many kernel launches for 16 clouds as for 4 (the
-    tree levels of the moments follow the largest cloud, the same here)."""
+    """Every phase of a batched iteration is one launch over a lane's clouds:
+    the iteration graph has as many kernel launches for 16 clouds as for 4
+    (the tree levels of the moments follow each lane's largest cloud; the
+    large cloud has a lane of its own in both batches)."""
     big = synth.torus(20000, seed=7)[0]
     small = [synth.sphere(2000, seed=20 + i)[0] for i in range(15)]
-    k4 = _kernels_per_iteration(dwglib, [big] + small[:3], path)
-    k16 = _kernels_per_iteration(dwglib, [big] + small, path)
+    k1 = _kernels_per_iteration(dwglib, [big] + small, path, 1)
+    assert k1 < 4 * 15     # a few dozen phases, not a chain per cloud
+    k4 = _kernels_per_iteration(dwglib, [big] + small[:3], path, 4)
+    k16 = _kernels_per_iteration(dwglib, [big] + small, path, 4)
     assert k4 == k16, (k4, k16)
-    assert k16 < 4 * 15    # a dozen phases, not a chain per cloud
+    assert k16 <= 4 * k1, (k1, k16)
