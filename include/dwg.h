@@ -151,7 +151,7 @@ int dwg_set_compensation(dwg_handle h, int on);
 /*
  * How a batch handle (dwg_create_batch) runs an iteration of all its clouds
  * (the paper orients one cloud; batching is this library's).
- *   lanes in [1, DWG_MAX_BATCH_LANES] (default 4): batched phases.  The
+ *   lanes in [1, DWG_MAX_BATCH_LANES] (default 1): batched phases.  The
  *     clouds are split into min(lanes, clouds) groups of about equal work;
  *     within a group every phase of the iteration -- Barnes-Hut moments per
  *     tree level, list evaluations, reduce, iso-value, level set, kNN
@@ -253,12 +253,14 @@ int dwg_extract_level_set(dwg_handle h, float *tri_out, int64_t cap, int64_t *co
  * denominators of the evaluators' roofline.  ffma_lane_ops_per_s: FP32 lane
  * operations per second of packed fused multiply-adds (fma.rn.f32x2; one
  * packed instruction = 2 lane operations), 8 independent chains per thread,
- * 8 CTAs of 256 threads per SM; rsqrt_per_s: MUFU reciprocal square roots per
+ * 8 CTAs of 256 threads per SM; rsqrt_per_s and ex2_per_s: MUFU reciprocal
+ * square roots and base-2 exponentials (the screened kernel's factor) per
  * second, the same way.  Each is the faster of two timed launches of a few
  * milliseconds after a warm-up.  Returns DWG_ERR_INVALID for a bad device or
  * NULL outputs, DWG_ERR_CUDA on a CUDA error.
  */
-int dwg_measure_fp32_peaks(int device, double *ffma_lane_ops_per_s, double *rsqrt_per_s);
+int dwg_measure_fp32_peaks(int device, double *ffma_lane_ops_per_s, double *rsqrt_per_s,
+                           double *ex2_per_s);
 
 /*
  * Failure-detection self-check (not in the paper).  Every device-side wait of

@@ -917,13 +917,14 @@ int dwg_extract_level_set(dwg_handle h, float *tri_out, int64_t cap, int64_t *co
     return rc;
 }
 
-int dwg_measure_fp32_peaks(int device, double *ffma_lane_ops_per_s, double *rsqrt_per_s)
+int dwg_measure_fp32_peaks(int device, double *ffma_lane_ops_per_s, double *rsqrt_per_s,
+                           double *ex2_per_s)
 {
-    if (!ffma_lane_ops_per_s || !rsqrt_per_s) return DWG_ERR_INVALID;
+    if (!ffma_lane_ops_per_s || !rsqrt_per_s || !ex2_per_s) return DWG_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return DWG_ERR_INVALID;
-    return measure_fp32_peaks(device, ffma_lane_ops_per_s, rsqrt_per_s);
+    return measure_fp32_peaks(device, ffma_lane_ops_per_s, rsqrt_per_s, ex2_per_s);
 }
 
 int dwg_selfcheck_wait(dwg_handle h, int polls)

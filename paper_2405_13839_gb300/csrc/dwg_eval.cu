@@ -150,7 +150,24 @@ __global__ void __launch_bounds__(256) k_peak_rsqrt(int iters, float seed, float
     if (s == -1.f) sink[blockIdx.x] = s;
 }
 
-int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops)
+// MUFU base-2 exponential: 8 independent chains y <- 2^(-y) (a fixed point
+// near 0.641), `iters` times.
+__global__ void __launch_bounds__(256) k_peak_ex2(int iters, float seed, float *sink)
+{
+    float y[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) y[k] = seed + 0.01f * k + threadIdx.x * 1e-5f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) y[k] = ex2_mufu(-y[k]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += y[k];
+    if (s == -1.f) sink[blockIdx.x] = s;
+}
+
+int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops, double *ex2_ops)
 {
     cudaSetDevice(device);
     int sms = 0;
@@ -160,10 +177,11 @@ int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops)
     float *sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = DWG_OK;
-    auto timed = [&](bool ffma, int iters, double *ms) -> bool {
+    auto timed = [&](int which, int iters, double *ms) -> bool {
         cudaEventRecord(e0);
-        if (ffma) k_peak_ffma<<<blocks, threads>>>(iters, 1.0f, sink);
-        else k_peak_rsqrt<<<blocks, threads>>>(iters, 1.5f, sink);
+        if (which == 0) k_peak_ffma<<<blocks, threads>>>(iters, 1.0f, sink);
+        else if (which == 1) k_peak_rsqrt<<<blocks, threads>>>(iters, 1.5f, sink);
+        else k_peak_ex2<<<blocks, threads>>>(iters, 0.6f, sink);
         cudaEventRecord(e1);
         if (cudaEventSynchronize(e1) != cudaSuccess) return false;
         float f = 0.f;
@@ -176,15 +194,16 @@ int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops)
         rc = DWG_ERR_CUDA;
     } else {
         const int it_f = 1 << 16, it_r = 1 << 13;
-        double ms_f = 0.0, ms_r = 0.0, w = 0.0;
+        double ms_f = 0.0, ms_r = 0.0, ms_e = 0.0, w = 0.0;
         // a short warm-up launch each, then two timed launches each; the
         // shorter time is taken
-        bool ok = timed(true, it_f / 8, &w) && timed(false, it_r / 8, &w);
-        double best_f = 1e30, best_r = 1e30;
+        bool ok = timed(0, it_f / 8, &w) && timed(1, it_r / 8, &w) && timed(2, it_r / 8, &w);
+        double best_f = 1e30, best_r = 1e30, best_e = 1e30;
         for (int r = 0; ok && r < 2; ++r) {
-            ok = timed(true, it_f, &ms_f) && timed(false, it_r, &ms_r);
+            ok = timed(0, it_f, &ms_f) && timed(1, it_r, &ms_r) && timed(2, it_r, &ms_e);
             best_f = std::min(best_f, ms_f);
             best_r = std::min(best_r, ms_r);
+            best_e = std::min(best_e, ms_e);
         }
         if (!ok || cudaGetLastError() != cudaSuccess) {
             rc = DWG_ERR_CUDA;
@@ -192,6 +211,7 @@ int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops)
             const double thr = (double)blocks * threads;
             *ffma_lane_ops = thr * it_f * 8.0 * 2.0 / (best_f * 1e-3);
             *rsqrt_ops = thr * it_r * 8.0 / (best_r * 1e-3);
+            *ex2_ops = thr * it_r * 8.0 / (best_e * 1e-3);
         }
     }
     if (e0) cudaEventDestroy(e0);

@@ -304,7 +304,7 @@ struct Ctx {
     float tree_beta = 2.0f;            // 1 / opening angle
     int tree_leaf = 16;                // points per tree leaf (16, 32, 64 or 128)
     int tree_group = 1;                // 1: opening test per 64-query group, 0: per query
-    int batch_phases = 4;              // batch handles: lanes of batched phases, 0 branches
+    int batch_phases = 1;              // batch handles: lanes of batched phases, 0 branches
     uint64_t tree_gen = 0;             // counts tree builds
     TreeLists lists_p, lists_c;        // group-test lists at the points and corners
     int tree_levels = 0;               // 2^tree_levels leaves
@@ -503,7 +503,7 @@ cudaError_t launch_pack_sources16(const Ctx *c);
 cudaError_t launch_wait_selfcheck(Ctx *c, int polls);
 // measured FP32 issue rates of this device: packed-FMA lane operations and
 // MUFU rsqrt per second
-int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops);
+int measure_fp32_peaks(int device, double *ffma_lane_ops, double *rsqrt_ops, double *ex2_ops);
 // the level set's triangles (count only with out null; counter: device)
 cudaError_t launch_mc_tris(Ctx *c, float *out, int64_t cap, unsigned long long *counter);
 // per-leaf candidate lists for the faces' k nearest points (once per

@@ -1384,9 +1384,12 @@ __global__ void k_tree_moment_records_b(const CloudIter *__restrict__ cl, const 
                         (int64_t)blockIdx.x - off[ci]);
 }
 
-// GRAD: the points (w and grad w), else the corners (w)
+// GRAD: the points (w and grad w), else the corners (w).  Held to the
+// registers of the single-cloud kernel (8 or 5 resident CTAs per SM): the
+// per-cloud arguments come from memory here, not from the parameter bank,
+// and would otherwise take registers for the whole item.
 template <bool GRAD, bool SCREENED>
-__global__ void __launch_bounds__(32 * kGrpWarps)
+__global__ void __launch_bounds__(32 * kGrpWarps, GRAD ? 5 : 8)
     k_tree_eval_lists_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
 {
     const int ci = seg_cloud(off, ncl);

@@ -111,6 +111,7 @@ def _load() -> ctypes.CDLL:
         "dwg_extract_level_set": ([H, P, I64, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double)],
                                   I),
         "dwg_measure_fp32_peaks": ([I, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)], I),
         "dwg_set_regularization": ([H, I, I, F, F, P], I),
         "dwg_set_tree": ([H, I, F], I),
@@ -247,7 +248,7 @@ def dwg_set_convergence(h, rule):
 
 def dwg_set_batch_mode(h, lanes):
     """Batch handles: lanes >= 1 batched phases (one launch per phase over a
-    lane's clouds, lanes concurrent; default 4), 0 one graph branch per
+    lane's clouds, lanes concurrent; default 1), 0 one graph branch per
     cloud."""
     return _raise(h, _lib.dwg_set_batch_mode(h, int(lanes)))
 
@@ -282,11 +283,14 @@ def dwg_set_regularization(h, mode, k=10, vmin=0.0, vmax=0.0, delta_out=None):
 
 
 def dwg_measure_fp32_peaks(device=0):
-    """(packed-FMA FP32 lane operations per second, MUFU rsqrt per second)."""
+    """(packed-FMA FP32 lane operations per second, MUFU rsqrt per second,
+    MUFU ex2 per second)."""
     f = ctypes.c_double()
     r = ctypes.c_double()
-    _raise(None, _lib.dwg_measure_fp32_peaks(int(device), ctypes.byref(f), ctypes.byref(r)))
-    return f.value, r.value
+    e = ctypes.c_double()
+    _raise(None, _lib.dwg_measure_fp32_peaks(int(device), ctypes.byref(f), ctypes.byref(r),
+                                             ctypes.byref(e)))
+    return f.value, r.value, e.value
 
 
 def dwg_extract_level_set(h, tri_out=None):

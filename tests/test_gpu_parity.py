@@ -461,10 +461,10 @@ def test_wait_limit_reports_timeout_and_the_handle_stays_usable(dwglib, handle):
 def test_fp32_microbenchmarks_are_near_the_derived_issue_rate(dwglib):
     """The measured packed-FMA rate is within 25 % of SMs x 128 lanes x the
     SM clock (the derived peak of the evaluators' roofline) at any clock the
-    GPU runs at, and MUFU rsqrt is at most an eighth of it (16 per SM per
-    clock)."""
+    GPU runs at, MUFU rsqrt is at most an eighth of it (16 per SM per clock)
+    and MUFU ex2 at most a quarter."""
     torch = pytest.importorskip("torch")
-    ffma, rsq = dwglib.dwg_measure_fp32_peaks(0)
+    ffma, rsq, ex2 = dwglib.dwg_measure_fp32_peaks(0)
     props = torch.cuda.get_device_properties(0)
     sms = props.multi_processor_count
     assert ffma > 0 and rsq > 0
@@ -472,6 +472,7 @@ def test_fp32_microbenchmarks_are_near_the_derived_issue_rate(dwglib):
     # between 1.0 and 2.2 GHz of 128 lanes
     assert 0.75 * 128 * 1.0e9 <= per_sm_clk <= 1.05 * 128 * 2.2e9, per_sm_clk
     assert rsq <= ffma / 8 * 1.10, (rsq, ffma)
+    assert 0 < ex2 <= ffma / 4 * 1.10, (ex2, ffma)
     with pytest.raises(dwglib.DWGError) as e:
         dwglib.dwg_measure_fp32_peaks(999)
     assert e.value.code == dwglib.DWG_ERR_INVALID
