@@ -136,6 +136,20 @@ int dwg_set_params(dwg_handle h, int kernel, float eps, float screening, int max
 int dwg_set_convergence(dwg_handle h, int rule);
 
 /*
+ * The kNN scatter of Eq. 7 (not a parameter of the paper; results do not
+ * depend on it).  A face whose cell has no candidate list searches the
+ * points' bucket tree in its own thread; a face that is about as far from
+ * many points as from its nearest (a level set far from the cloud, as near
+ * the centre of a sphere) can make that search nearly exhaustive and hold
+ * the whole launch.  A search that takes more than `budget` node visits and
+ * point distances stops and hands the face to a second launch in which a
+ * block of threads finishes it; the k points found, and so the sums, are the
+ * same bits either way.  budget >= 0 (default 16384), or -1: every face
+ * searches alone.  Batch handles apply it to every cloud.
+ */
+int dwg_set_knn_budget(dwg_handle h, int budget);
+
+/*
  * Compensation of the exact all-pairs evaluator's sums of the Eq. 2/3 and
  * Eq. 5 terms, which are computed in FP32 here (the paper states no
  * precision and has no counterpart to this switch).  on = 1 (the
@@ -379,6 +393,7 @@ typedef struct {
     double interactions_points_step;  /* dwg_profile_step: evaluations at the points */
     double interactions_corners_step; /* dwg_profile_step: evaluations at the corners */
     int kernels_per_iteration;        /* kernel launches in one iteration of the graph */
+    int knn_deferred_last;   /* faces of the last iteration whose search a block finished */
 } dwg_stats;
 
 int dwg_get_stats(dwg_handle h, dwg_stats *out);

@@ -195,6 +195,7 @@ __global__ void k_iter_reset(IterState *st, int max_iters, unsigned long long *c
     st->done = 0;
     st->max_iters = max_iters;
     st->nfaces = 0;
+    st->ndefer = 0;
     st->iso = 0.0;
     st->stat = 0.0;
 }
@@ -720,6 +721,18 @@ int dwg_set_convergence(dwg_handle h, int rule)
     return DWG_OK;
 }
 
+int dwg_set_knn_budget(dwg_handle h, int budget)
+{
+    if (!h) return DWG_ERR_INVALID;
+    if (budget < -1) return fail(h, DWG_ERR_INVALID, "budget must be >= -1");
+    if (h->knn_budget != budget) {
+        h->knn_budget = budget;
+        invalidate_graph(h);
+    }
+    for (dwg_ctx *c : h->clouds) dwg_set_knn_budget(c, budget);
+    return DWG_OK;
+}
+
 int dwg_set_batch_mode(dwg_handle h, int lanes)
 {
     if (!h) return DWG_ERR_INVALID;
@@ -1089,6 +1102,7 @@ int dwg_orient(dwg_handle h, float *normals_out, int *iters_out)
     }
     IterState st;
     rc = read_state(h, &st);
+    h->stats.knn_deferred_last = st.ndefer;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -1148,6 +1162,7 @@ int dwg_step(dwg_handle h, float *w_out, float *grad_out, float *dtheta_out, dou
     IterState st;
     if ((rc = read_state(h, &st))) return rc;
     if ((rc = check_device_err(h))) return rc;
+    h->stats.knn_deferred_last = st.ndefer;
     if (iso_out) *iso_out = st.iso;
     if (stat_out) *stat_out = st.stat;
     if (!w_out && !grad_out && !dtheta_out) return DWG_OK;
@@ -1605,6 +1620,7 @@ static int phase_blocks(const dwg_ctx *c, int ph)
     case kPhReduceW: return ls ? (int)ceil_div(c->ncorners, 256) : 0;
     case kPhMcFaces: return ls ? (int)ceil_div(c->nleaves, 256) : 0;
     case kPhKnn: return ls ? (int)ceil_div(c->max_faces, 128) : 0;
+    case kPhKnnDefer: return ls ? 8 : 0;  // blocks take the cloud's deferred faces in turn
     case kPhUpdate: return (int)ceil_div(c->n, 256);
     case kPhSelHist:
     case kPhSelSum: return select_blocks(c->n);
@@ -1792,6 +1808,7 @@ static cudaError_t batch_lane_phases(dwg_ctx *h, const dwg_ctx::Lane &L, bool sc
     ok(launch_eval_batch(kPhReduceW, cl, off(kPhReduceW), ncl, ph[kPhReduceW], s));
     ok(launch_iter_batch(kPhMcFaces, cl, off(kPhMcFaces), ncl, ph[kPhMcFaces], 0, s));
     ok(launch_iter_batch(kPhKnn, cl, off(kPhKnn), ncl, ph[kPhKnn], 0, s));
+    ok(launch_iter_batch(kPhKnnDefer, cl, off(kPhKnnDefer), ncl, ph[kPhKnnDefer], 0, s));
     // normal update and convergence
     ok(launch_iter_batch(kPhUpdate, cl, off(kPhUpdate), ncl, ph[kPhUpdate], 0, s));
     for (int level = 0; level < 3; ++level) {

@@ -499,6 +499,7 @@ static void free_disc(Ctx *c)
     cudaFree(c->d_corner_pos);
     cudaFree(c->d_wc);
     cudaFree(c->d_faces);
+    cudaFree(c->d_defer);
     cudaFree(c->d_part_c);
     c->d_leaves = nullptr;
     c->d_leaf_corners = nullptr;
@@ -506,6 +507,7 @@ static void free_disc(Ctx *c)
     c->d_corner_pos = nullptr;
     c->d_wc = nullptr;
     c->d_faces = nullptr;
+    c->d_defer = nullptr;
     c->d_part_c = nullptr;
     c->part_c_cap = 0;
     c->built_depth = -1;
@@ -615,6 +617,7 @@ int build_discretization(Ctx *c, int d)
         c->max_faces = 6 * nleaves;
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_wc, c->ncorners * sizeof(float)));
         DWG_CUDA_TRY(c, cudaMalloc(&c->d_faces, 2 * c->max_faces * sizeof(float4)));
+        DWG_CUDA_TRY(c, cudaMalloc(&c->d_defer, kDeferCap * sizeof(int2)));
         // fixed-point scale of the face sums: 2^22 units per finest-cell area
         c->acc_scale = 4194304.0 / (h * h);
         c->built_depth = d;

@@ -24,6 +24,9 @@ constexpr int kSrcFloatsClamp = 16;      // the same + (d2,d2,0,0), d2 = delta^2
 constexpr int kSrcTile = 128;            // sources per shared-memory tile
 constexpr int kBucket = 16;              // points per kNN bucket
 constexpr int kSelBins = 4096;           // radix-select bins (level 1 and 2)
+constexpr int kSearchBudget = 16384;     // node visits + distances of a face's own kNN search
+constexpr int kDeferCap = 1 << 16;       // deferred faces per iteration (more: searched in place)
+constexpr int kDeferBlocks = 256;        // blocks of the deferred-search launch
 
 // device error flags (bitmask in ctx->d_err)
 constexpr int kErrTimeout = 1;
@@ -40,6 +43,7 @@ struct IterState {
     int done;            // converged flag
     int max_iters;
     int nfaces;          // faces emitted in the current iteration
+    int ndefer;          // faces whose k-nearest search was deferred (kNN scatter)
     double iso;          // w_bar of the current iteration
     double stat;         // convergence statistic of the current iteration
 };
@@ -147,6 +151,8 @@ struct CloudIter {
     const float4 *corner_pos;
     float4 *faces;
     int64_t max_faces;
+    int2 *defer;
+    int knn_budget;
     // kNN scatter
     KnnTree T;
     int k;
@@ -187,7 +193,8 @@ struct CloudIter {
 
 // phases of a batched iteration (one launch each, every cloud's blocks)
 enum BatchPhase {
-    kPhReducePoints, kPhReduceW, kPhIso, kPhMcFaces, kPhKnn, kPhUpdate, kPhSelHist, kPhSelFind,
+    kPhReducePoints, kPhReduceW, kPhIso, kPhMcFaces, kPhKnn, kPhKnnDefer, kPhUpdate, kPhSelHist,
+    kPhSelFind,
     kPhSelSum, kPhSelFinal, kPhLeafMom, kPhMomRec, kPhListsP, kPhListsC, kPhCombineP,
     kPhCombineC, kPhCount
 };
@@ -263,6 +270,7 @@ struct Ctx {
     // per-leaf candidate lists of the faces' kNN (CSR over the leaves; a leaf
     // with an empty range keeps the tree search)
     int knn_lists = 1;
+    int knn_budget = kSearchBudget;    // see dwg_set_knn_budget
     int64_t *d_cell_off = nullptr;     // nleaves + 1
     int *d_cell_idx = nullptr;         // sorted point indices
     int cells_k = 0;                   // k the lists were built for (0: none)
@@ -271,6 +279,7 @@ struct Ctx {
     float4 *d_corner_pos = nullptr;
     float *d_wc = nullptr;             // w at corners
     float4 *d_faces = nullptr;         // 2 x max_faces: area vector, centroid
+    int2 *d_defer = nullptr;           // kDeferCap deferred faces: (face, bound bits)
     unsigned long long *d_acc = nullptr; // n x 3 fixed-point face sums
     double acc_scale = 1.0;
 

@@ -49,6 +49,7 @@ __device__ __forceinline__ void iso_body(const double *__restrict__ wsum_blocks,
     if (threadIdx.x == 0) {
         st->iso = sh[0] / (double)n;
         st->nfaces = 0;
+        st->ndefer = 0;
     }
 }
 
@@ -381,9 +382,13 @@ __device__ __forceinline__ void knn_insert(uint64_t key, int j, int k, uint64_t 
 // arrays stay in registers).  The list is seeded with the points next to q's
 // Morton code in the sorted order, which bounds the search ball before the
 // depth-first descent (nearer child first) prunes the bucket tree.
+// With budget >= 0 the search gives up after that many node visits and
+// point distances, returns false and leaves in *bound the k-th smallest
+// distance (squared) found so far: an upper bound of q's k-th nearest.
 template <int KMAX, bool FIXED>
-__device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *bj, int *err,
-                                           int64_t seed = -1)
+__device__ __forceinline__ bool knn_search(const KnnTree &T, F3 q, int k, int *bj, int *err,
+                                           int64_t seed = -1, int budget = -1,
+                                           float *bound = nullptr)
 {
     uint64_t best[KMAX];
 #pragma unroll
@@ -415,14 +420,21 @@ __device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *b
     const int64_t nleaf = (int64_t)1 << T.levels;
     int stack[64];
     int sp = 0;
+    int work = 0;
     stack[sp++] = 1;
     while (sp > 0) {
         int node = stack[--sp];
         const float worst = best[kk - 1] == ~0ull ? INFINITY : __uint_as_float((uint32_t)(best[kk - 1] >> 32));
+        if (budget >= 0 && work > budget) {
+            *bound = worst;
+            return false;
+        }
+        ++work;
         if (box_d2(__ldg(&T.lo[node]), __ldg(&T.hi[node]), q) > worst) continue;
         if (node >= nleaf) {
             int64_t j0 = (int64_t)(node - nleaf) * kBucket;
             int64_t j1 = min(j0 + kBucket, T.n);
+            work += (int)(j1 - j0);
             for (int64_t j = j0; j < j1; ++j) {
                 if (j >= s0 && j < s1) continue;  // already seeded
                 float d = pt_d2(__ldg(&T.p4[j]), q);
@@ -448,6 +460,7 @@ __device__ __forceinline__ void knn_search(const KnnTree &T, F3 q, int k, int *b
             }
         }
     }
+    return true;
 }
 
 // The k nearest of q among a candidate list that is known to contain them:
@@ -478,52 +491,239 @@ __device__ __forceinline__ void knn_scan(const KnnTree &T, F3 q, int k, const in
 
 static KnnTree knn_tree(const Ctx *c);
 
+// The scatter's additions are first summed per block in a shared-memory
+// table keyed by point (open addressing, a few probes), then each distinct
+// point of the block takes one global addition per component.  Neighbouring
+// faces share most of their nearest points, and where the level set lies
+// away from the points many faces share the same few; summing them in the
+// block first keeps the global atomics few and uncontended.  The sums are
+// 64-bit fixed-point integers, so the grouping changes no bit of them.
+constexpr int kAggBits = 10;
+constexpr int kAggSlots = 1 << kAggBits;  // table entries per block of 128 faces
+constexpr int kAggProbes = 8;    // entries tried before adding to global memory directly
+
+// A face whose own search (no candidate list for its cell) runs past
+// kSearchBudget -- a face far from the points, about as far from many of
+// them, as near the centre of a sphere -- is deferred: its index and the
+// bound its partial search reached go to a list that k_knn_deferred finishes
+// with a whole block per face, so that no single thread holds the launch.
 template <int KMAX, bool FIXED>
 __device__ __forceinline__ void knn_scatter_body(const float4 *__restrict__ faces,
-                                                 const IterState *st, int64_t max_faces,
+                                                 IterState *st, int64_t max_faces,
                                                  const KnnTree &T, int k,
                                                  const int64_t *__restrict__ cell_off,
                                                  const int *__restrict__ cell_idx, double scale,
-                                                 unsigned long long *acc, int *err, int64_t bid)
+                                                 unsigned long long *acc, int2 *defer,
+                                                 int budget, int *err, int64_t bid)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
-    int64_t f = bid * blockDim.x + threadIdx.x;
-    int64_t nf = min((int64_t)st->nfaces, max_faces);
-    if (f >= nf) return;
-    float4 A = faces[2 * f], C = faces[2 * f + 1];
-    int bj[KMAX];
-    int64_t c0 = 0, c1 = 0;
-    if (cell_off) {
-        const int leaf = __float_as_int(A.w);
-        c0 = __ldg(&cell_off[leaf]);
-        c1 = __ldg(&cell_off[leaf + 1]);
+    const int64_t nf = min((int64_t)st->nfaces, max_faces);
+    if (bid * blockDim.x >= nf) return;  // the whole block is past the faces
+    __shared__ int s_key[kAggSlots];
+    __shared__ unsigned long long s_v[3][kAggSlots];
+    for (int i = threadIdx.x; i < kAggSlots; i += blockDim.x) {
+        s_key[i] = -1;
+        s_v[0][i] = s_v[1][i] = s_v[2][i] = 0ull;
     }
-    if (c1 > c0)
-        knn_scan<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, cell_idx, c0, c1, bj);
-    else
-        knn_search<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, bj, err, (int64_t)__float_as_int(C.w));
-    long long vx = llrint((double)A.x * scale);
-    long long vy = llrint((double)A.y * scale);
-    long long vz = llrint((double)A.z * scale);
+    const int64_t f = bid * blockDim.x + threadIdx.x;
+    const bool active = f < nf;
+    int bj[KMAX];
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) bj[t] = -1;
+    long long vx = 0, vy = 0, vz = 0;
+    if (active) {
+        float4 A = faces[2 * f], C = faces[2 * f + 1];
+        int64_t c0 = 0, c1 = 0;
+        if (cell_off) {
+            const int leaf = __float_as_int(A.w);
+            c0 = __ldg(&cell_off[leaf]);
+            c1 = __ldg(&cell_off[leaf + 1]);
+        }
+        if (c1 > c0) {
+            knn_scan<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, cell_idx, c0, c1, bj);
+        } else {
+            float bound = INFINITY;
+            const F3 q{C.x, C.y, C.z};
+            const int64_t seed = (int64_t)__float_as_int(C.w);
+            if (!knn_search<KMAX, FIXED>(T, q, k, bj, err, seed, budget, &bound)) {
+                const int slot = atomicAdd(&st->ndefer, 1);
+                if (slot < kDeferCap) {
+                    defer[slot] = make_int2((int)f, __float_as_int(bound));
+#pragma unroll
+                    for (int t = 0; t < KMAX; ++t) bj[t] = -1;  // added by k_knn_deferred
+                } else {
+                    knn_search<KMAX, FIXED>(T, q, k, bj, err, seed);
+                }
+            }
+        }
+        vx = llrint((double)A.x * scale);
+        vy = llrint((double)A.y * scale);
+        vz = llrint((double)A.z * scale);
+    }
+    __syncthreads();  // the table is cleared
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) {
         if (t >= k || bj[t] < 0) continue;
-        unsigned long long *a = acc + 3 * (int64_t)bj[t];
-        atomicAdd(a + 0, (unsigned long long)vx);
-        atomicAdd(a + 1, (unsigned long long)vy);
-        atomicAdd(a + 2, (unsigned long long)vz);
+        const int j = bj[t];
+        unsigned h = ((unsigned)j * 2654435761u) >> (32 - kAggBits);
+        bool added = false;
+        for (int p = 0; p < kAggProbes; ++p, h = (h + 1) & (kAggSlots - 1)) {
+            const int prev = atomicCAS(&s_key[h], -1, j);
+            if (prev == -1 || prev == j) {
+                atomicAdd(&s_v[0][h], (unsigned long long)vx);
+                atomicAdd(&s_v[1][h], (unsigned long long)vy);
+                atomicAdd(&s_v[2][h], (unsigned long long)vz);
+                added = true;
+                break;
+            }
+        }
+        if (!added) {  // the table is crowded: straight to the point's sums
+            unsigned long long *a = acc + 3 * (int64_t)j;
+            atomicAdd(a + 0, (unsigned long long)vx);
+            atomicAdd(a + 1, (unsigned long long)vy);
+            atomicAdd(a + 2, (unsigned long long)vz);
+        }
+    }
+    __syncthreads();  // every addition is in the table
+    for (int i = threadIdx.x; i < kAggSlots; i += blockDim.x) {
+        const int j = s_key[i];
+        if (j < 0) continue;
+        unsigned long long *a = acc + 3 * (int64_t)j;
+        atomicAdd(a + 0, s_v[0][i]);
+        atomicAdd(a + 1, s_v[1][i]);
+        atomicAdd(a + 2, s_v[2][i]);
     }
 }
 
 template <int KMAX, bool FIXED>
 __global__ void __launch_bounds__(128)
-    k_knn_scatter(const float4 *__restrict__ faces, const IterState *st, int64_t max_faces,
+    k_knn_scatter(const float4 *__restrict__ faces, IterState *st, int64_t max_faces,
                   KnnTree T, int k, const int64_t *__restrict__ cell_off,
                   const int *__restrict__ cell_idx, double scale, unsigned long long *acc,
-                  int *err)
+                  int2 *defer, int budget, int *err)
 {
     knn_scatter_body<KMAX, FIXED>(faces, st, max_faces, T, k, cell_off, cell_idx, scale, acc,
-                                  err, blockIdx.x);
+                                  defer, budget, err, blockIdx.x);
+}
+
+// The deferred faces, one block per face (the blocks take the list in
+// turn; 128 threads for k <= 16, 64 for up to 32 so that the lists fit the
+// static shared memory).  The threads first test the bucket tree's nodes at
+// one level of at most 2,048 nodes against the bound of the face's partial
+// search (an upper bound of its k-th nearest distance), then split the
+// buckets under the nodes that pass, skipping buckets whose box lies beyond
+// the bound; each thread keeps its own k nearest under the search's
+// (distance, input index) keys; thread 0 takes the k smallest of the
+// block's lists -- the k points the full search finds -- and adds the
+// face's vector to them.
+template <int KMAX>
+__host__ __device__ constexpr int defer_threads() { return KMAX > 16 ? 64 : 128; }
+
+template <int KMAX, bool FIXED>
+__device__ __forceinline__ void knn_deferred_body(const float4 *__restrict__ faces,
+                                                  const IterState *st,
+                                                  const int2 *__restrict__ defer,
+                                                  const KnnTree &T, int k, double scale,
+                                                  unsigned long long *acc, int64_t bid,
+                                                  int64_t nblk)
+{
+    if (cloud_idle(st)) return;  // finished cloud of a batch
+    const int nd = min(st->ndefer, kDeferCap);
+    if (bid >= nd) return;  // the same for every thread of the block
+    constexpr int NT = defer_threads<KMAX>();
+    __shared__ uint64_t s_key[NT * KMAX];
+    __shared__ int s_j[NT * KMAX];
+    __shared__ int s_head[NT];
+    constexpr int kCoarseBits = 11;
+    __shared__ int s_pass[1 << kCoarseBits];
+    __shared__ int s_npass;
+    const int kk = FIXED ? KMAX : k;
+    const int64_t nleaf = (int64_t)1 << T.levels;
+    const int64_t nb = (T.n + kBucket - 1) / kBucket;
+    const int lc = min(T.levels, kCoarseBits);      // the coarse level
+    const int64_t span = (int64_t)1 << (T.levels - lc);  // buckets under a coarse node
+    for (int64_t d = bid; d < nd; d += nblk) {
+        const int2 e = defer[d];
+        const int64_t f = e.x;
+        const float4 C = faces[2 * f + 1];
+        const F3 q{C.x, C.y, C.z};
+        uint64_t best[KMAX];
+        int bj[KMAX];
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+            best[t] = ~0ull;
+            bj[t] = -1;
+        }
+        float worst = __int_as_float(e.y);
+        if (threadIdx.x == 0) s_npass = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < (1 << lc); i += NT) {
+            const int node = (1 << lc) + i;
+            if ((int64_t)i * span < nb &&
+                box_d2(__ldg(&T.lo[node]), __ldg(&T.hi[node]), q) <= worst)
+                s_pass[atomicAdd(&s_npass, 1)] = i;
+        }
+        __syncthreads();
+        const int64_t total = (int64_t)s_npass * span;
+        for (int64_t u = threadIdx.x; u < total; u += NT) {
+            const int64_t b = (int64_t)s_pass[u / span] * span + u % span;
+            if (b >= nb) continue;
+            const int64_t node = nleaf + b;
+            if (box_d2(__ldg(&T.lo[node]), __ldg(&T.hi[node]), q) > worst) continue;
+            const int64_t j0 = b * kBucket, j1 = min(j0 + kBucket, T.n);
+            for (int64_t j = j0; j < j1; ++j) {
+                const float d2 = pt_d2(__ldg(&T.p4[j]), q);
+                if (d2 > worst) continue;
+                const uint64_t key = knn_key(d2, __ldg(&T.perm[j]));
+                if (key < best[kk - 1]) {
+                    knn_insert<KMAX, FIXED>(key, (int)j, k, best, bj);
+                    if (best[kk - 1] != ~0ull)
+                        worst = fminf(worst, __uint_as_float((uint32_t)(best[kk - 1] >> 32)));
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+            s_key[threadIdx.x * KMAX + t] = best[t];
+            s_j[threadIdx.x * KMAX + t] = bj[t];
+        }
+        s_head[threadIdx.x] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const float4 A = faces[2 * f];
+            const long long vx = llrint((double)A.x * scale);
+            const long long vy = llrint((double)A.y * scale);
+            const long long vz = llrint((double)A.z * scale);
+            for (int r = 0; r < kk; ++r) {  // the r-th smallest key of the block
+                uint64_t m = ~0ull;
+                int win = -1;
+                for (int t = 0; t < NT; ++t) {
+                    const int hd = s_head[t];
+                    if (hd < kk && s_key[t * KMAX + hd] < m) {
+                        m = s_key[t * KMAX + hd];
+                        win = t;
+                    }
+                }
+                if (win < 0 || m == ~0ull) break;  // fewer than k points
+                const int j = s_j[win * KMAX + s_head[win]];
+                s_head[win] += 1;
+                unsigned long long *a = acc + 3 * (int64_t)j;
+                atomicAdd(a + 0, (unsigned long long)vx);
+                atomicAdd(a + 1, (unsigned long long)vy);
+                atomicAdd(a + 2, (unsigned long long)vz);
+            }
+        }
+        __syncthreads();  // the lists are read before the next face reuses them
+    }
+}
+
+template <int KMAX, bool FIXED>
+__global__ void __launch_bounds__(defer_threads<KMAX>())
+    k_knn_deferred(const float4 *__restrict__ faces, const IterState *st,
+                   const int2 *__restrict__ defer, KnnTree T, int k, double scale,
+                   unsigned long long *acc)
+{
+    knn_deferred_body<KMAX, FIXED>(faces, st, defer, T, k, scale, acc, blockIdx.x, gridDim.x);
 }
 
 template <int KMAX, bool FIXED>
@@ -1425,6 +1625,8 @@ void fill_cloud_iter(const Ctx *c, CloudIter *o)
     o->corner_pos = c->d_corner_pos;
     o->faces = c->d_faces;
     o->max_faces = c->max_faces;
+    o->defer = c->d_defer;
+    o->knn_budget = c->knn_budget;
     o->T = knn_tree(c);
     o->k = c->knn;
     const bool lists = c->knn_lists && c->cells_k == c->knn && c->d_cell_off;
@@ -1488,14 +1690,19 @@ cudaError_t launch_knn_scatter(Ctx *c)
     const bool lists = c->knn_lists && c->cells_k == c->knn && c->d_cell_off;
     const int64_t *off = lists ? c->d_cell_off : nullptr;
     const int *idx = lists ? c->d_cell_idx : nullptr;
-    if (c->knn == 10)
+    if (c->knn == 10) {
         k_knn_scatter<10, true><<<blocks, 128, 0, c->stream>>>(
             c->d_faces, c->d_state, c->max_faces, T, c->knn, off, idx, c->acc_scale, c->d_acc,
-            c->d_err);
-    else
+            c->d_defer, c->knn_budget, c->d_err);
+        k_knn_deferred<10, true><<<kDeferBlocks, defer_threads<10>(), 0, c->stream>>>(
+            c->d_faces, c->d_state, c->d_defer, T, c->knn, c->acc_scale, c->d_acc);
+    } else {
         k_knn_scatter<32, false><<<blocks, 128, 0, c->stream>>>(
             c->d_faces, c->d_state, c->max_faces, T, c->knn, off, idx, c->acc_scale, c->d_acc,
-            c->d_err);
+            c->d_defer, c->knn_budget, c->d_err);
+        k_knn_deferred<32, false><<<kDeferBlocks, defer_threads<32>(), 0, c->stream>>>(
+            c->d_faces, c->d_state, c->d_defer, T, c->knn, c->acc_scale, c->d_acc);
+    }
     return cudaGetLastError();
 }
 
@@ -1737,7 +1944,17 @@ __global__ void __launch_bounds__(128)
     const int ci = seg_cloud(off, ncl);
     const CloudIter &c = cl[ci];
     knn_scatter_body<KMAX, FIXED>(c.faces, c.st, c.max_faces, c.T, c.k, c.cell_off, c.cell_idx,
-                                  c.acc_scale, c.acc, c.err, (int64_t)blockIdx.x - off[ci]);
+                                  c.acc_scale, c.acc, c.defer, c.knn_budget, c.err,
+                                  (int64_t)blockIdx.x - off[ci]);
+}
+
+__global__ void __launch_bounds__(defer_threads<10>())
+    k_knn_deferred_b(const CloudIter *__restrict__ cl, const int *__restrict__ off, int ncl)
+{
+    const int ci = seg_cloud(off, ncl);
+    const CloudIter &c = cl[ci];
+    knn_deferred_body<10, true>(c.faces, c.st, c.defer, c.T, c.k, c.acc_scale, c.acc,
+                                (int64_t)blockIdx.x - off[ci], (int64_t)(off[ci + 1] - off[ci]));
 }
 
 __global__ void __launch_bounds__(256)
@@ -1789,6 +2006,9 @@ cudaError_t launch_iter_batch(int phase, const CloudIter *cl, const int *off, in
     case kPhIso: k_iso_b<<<(unsigned)ncl, 256, 0, s>>>(cl); break;
     case kPhMcFaces: k_mc_faces_b<<<g, 256, 0, s>>>(cl, off, ncl); break;
     case kPhKnn: k_knn_scatter_b<10, true><<<g, 128, 0, s>>>(cl, off, ncl); break;
+    case kPhKnnDefer:
+        k_knn_deferred_b<<<g, defer_threads<10>(), 0, s>>>(cl, off, ncl);
+        break;
     case kPhUpdate: k_normal_update_b<<<g, 256, 0, s>>>(cl, off, ncl); break;
     case kPhSelHist: k_sel_hist_b<<<g, kSelGridThreads, 0, s>>>(cl, off, ncl, arg); break;
     case kPhSelFind: k_sel_find_b<<<(unsigned)ncl, kSelThreads, 0, s>>>(cl, arg); break;

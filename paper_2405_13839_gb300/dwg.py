@@ -63,7 +63,8 @@ class dwg_stats(ctypes.Structure):
                 ("interactions_eval", ctypes.c_double),
                 ("interactions_points_step", ctypes.c_double),
                 ("interactions_corners_step", ctypes.c_double),
-                ("kernels_per_iteration", ctypes.c_int)]
+                ("kernels_per_iteration", ctypes.c_int),
+                ("knn_deferred_last", ctypes.c_int)]
 
 
 class dwg_tuning(ctypes.Structure):
@@ -105,6 +106,7 @@ def _load() -> ctypes.CDLL:
         "dwg_set_convergence": ([H, I], I),
         "dwg_set_compensation": ([H, I], I),
         "dwg_set_batch_mode": ([H, I], I),
+        "dwg_set_knn_budget": ([H, I], I),
         "dwg_set_weights": ([H, P], I),
         "dwg_voronoi_weights": ([H, I, P], I),
         "dwg_selfcheck_wait": ([H, I], I),
@@ -251,6 +253,12 @@ def dwg_set_batch_mode(h, lanes):
     lane's clouds, lanes concurrent; default 1), 0 one graph branch per
     cloud."""
     return _raise(h, _lib.dwg_set_batch_mode(h, int(lanes)))
+
+
+def dwg_set_knn_budget(h, budget):
+    """Node visits and distances after which a face's kNN search is handed
+    to a block (default 16384); -1: never.  The results do not change."""
+    return _raise(h, _lib.dwg_set_knn_budget(h, int(budget)))
 
 
 def dwg_set_compensation(h, on):
