@@ -491,16 +491,26 @@ __device__ __forceinline__ void knn_scan(const KnnTree &T, F3 q, int k, const in
 
 static KnnTree knn_tree(const Ctx *c);
 
-// The scatter's additions are first summed per block in a shared-memory
+// The scatter's additions are first summed per warp in a shared-memory
 // table keyed by point (open addressing, a few probes), then each distinct
-// point of the block takes one global addition per component.  Neighbouring
+// point of the warp takes one global addition per component.  Neighbouring
 // faces share most of their nearest points, and where the level set lies
 // away from the points many faces share the same few; summing them in the
-// block first keeps the global atomics few and uncontended.  The sums are
-// 64-bit fixed-point integers, so the grouping changes no bit of them.
-constexpr int kAggBits = 10;
-constexpr int kAggSlots = 1 << kAggBits;  // table entries per block of 128 faces
+// warp first keeps the global atomics few and uncontended.  A table per warp
+// (not per block) lets each warp leave as soon as its own faces are done.
+// The sums are 64-bit fixed-point integers, so the grouping changes no bit.
+// The tables take 28 KB of shared memory per block, which the SM takes from
+// its L1 cache: on clouds of millions of points the searches' gathers lose
+// more to the smaller cache than the tables save (a 3M-point union: 80.8 ->
+// 40.7 ms with them; a 15M-point union: 49 -> 70 ms), so clouds above
+// kAggMaxPoints add straight to the points' sums.
+constexpr int kAggBits = 8;
+constexpr int kAggSlots = 1 << kAggBits;  // table entries per warp of 32 faces
+constexpr int kAggWarps = 4;              // warps of a 128-thread block
 constexpr int kAggProbes = 8;    // entries tried before adding to global memory directly
+constexpr int64_t kAggMaxPoints = 4000000;
+constexpr size_t kAggSmem =
+    (size_t)kAggWarps * kAggSlots * (3 * sizeof(unsigned long long) + sizeof(int));
 
 // A face whose own search (no candidate list for its cell) runs past
 // kSearchBudget -- a face far from the points, about as far from many of
@@ -514,16 +524,23 @@ __device__ __forceinline__ void knn_scatter_body(const float4 *__restrict__ face
                                                  const int64_t *__restrict__ cell_off,
                                                  const int *__restrict__ cell_idx, double scale,
                                                  unsigned long long *acc, int2 *defer,
-                                                 int budget, int *err, int64_t bid)
+                                                 int budget, bool agg, int *err, int64_t bid)
 {
     if (cloud_idle(st)) return;  // finished cloud of a batch
     const int64_t nf = min((int64_t)st->nfaces, max_faces);
-    if (bid * blockDim.x >= nf) return;  // the whole block is past the faces
-    __shared__ int s_key[kAggSlots];
-    __shared__ unsigned long long s_v[3][kAggSlots];
-    for (int i = threadIdx.x; i < kAggSlots; i += blockDim.x) {
-        s_key[i] = -1;
-        s_v[0][i] = s_v[1][i] = s_v[2][i] = 0ull;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (bid * blockDim.x + wid * 32 >= nf) return;  // the whole warp is past the faces
+    // agg: kAggSmem bytes of dynamic shared memory, per warp 3 x kAggSlots
+    // sums, then every warp's kAggSlots keys
+    extern __shared__ unsigned long long s_agg[];
+    unsigned long long *s_v = s_agg + (size_t)wid * 3 * kAggSlots;
+    int *s_key = reinterpret_cast<int *>(s_agg + (size_t)kAggWarps * 3 * kAggSlots) +
+                 wid * kAggSlots;
+    if (agg) {
+        for (int i = lane; i < kAggSlots; i += 32) {
+            s_key[i] = -1;
+            s_v[i] = s_v[kAggSlots + i] = s_v[2 * kAggSlots + i] = 0ull;
+        }
     }
     const int64_t f = bid * blockDim.x + threadIdx.x;
     const bool active = f < nf;
@@ -542,25 +559,38 @@ __device__ __forceinline__ void knn_scatter_body(const float4 *__restrict__ face
         if (c1 > c0) {
             knn_scan<KMAX, FIXED>(T, F3{C.x, C.y, C.z}, k, cell_idx, c0, c1, bj);
         } else {
-            float bound = INFINITY;
+            // one inlined search: budgeted first, unbounded when the list is full
             const F3 q{C.x, C.y, C.z};
             const int64_t seed = (int64_t)__float_as_int(C.w);
-            if (!knn_search<KMAX, FIXED>(T, q, k, bj, err, seed, budget, &bound)) {
+            int bud = budget;
+            float bound = INFINITY;
+            while (!knn_search<KMAX, FIXED>(T, q, k, bj, err, seed, bud, &bound)) {
                 const int slot = atomicAdd(&st->ndefer, 1);
                 if (slot < kDeferCap) {
                     defer[slot] = make_int2((int)f, __float_as_int(bound));
 #pragma unroll
                     for (int t = 0; t < KMAX; ++t) bj[t] = -1;  // added by k_knn_deferred
-                } else {
-                    knn_search<KMAX, FIXED>(T, q, k, bj, err, seed);
+                    break;
                 }
+                bud = -1;
             }
         }
         vx = llrint((double)A.x * scale);
         vy = llrint((double)A.y * scale);
         vz = llrint((double)A.z * scale);
     }
-    __syncthreads();  // the table is cleared
+    if (!agg) {  // straight to the points' sums
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+            if (t >= k || bj[t] < 0) continue;
+            unsigned long long *a = acc + 3 * (int64_t)bj[t];
+            atomicAdd(a + 0, (unsigned long long)vx);
+            atomicAdd(a + 1, (unsigned long long)vy);
+            atomicAdd(a + 2, (unsigned long long)vz);
+        }
+        return;
+    }
+    __syncwarp();  // the table is cleared
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) {
         if (t >= k || bj[t] < 0) continue;
@@ -570,9 +600,9 @@ __device__ __forceinline__ void knn_scatter_body(const float4 *__restrict__ face
         for (int p = 0; p < kAggProbes; ++p, h = (h + 1) & (kAggSlots - 1)) {
             const int prev = atomicCAS(&s_key[h], -1, j);
             if (prev == -1 || prev == j) {
-                atomicAdd(&s_v[0][h], (unsigned long long)vx);
-                atomicAdd(&s_v[1][h], (unsigned long long)vy);
-                atomicAdd(&s_v[2][h], (unsigned long long)vz);
+                atomicAdd(&s_v[h], (unsigned long long)vx);
+                atomicAdd(&s_v[kAggSlots + h], (unsigned long long)vy);
+                atomicAdd(&s_v[2 * kAggSlots + h], (unsigned long long)vz);
                 added = true;
                 break;
             }
@@ -584,26 +614,28 @@ __device__ __forceinline__ void knn_scatter_body(const float4 *__restrict__ face
             atomicAdd(a + 2, (unsigned long long)vz);
         }
     }
-    __syncthreads();  // every addition is in the table
-    for (int i = threadIdx.x; i < kAggSlots; i += blockDim.x) {
+    __syncwarp();  // every addition is in the table
+    for (int i = lane; i < kAggSlots; i += 32) {
         const int j = s_key[i];
         if (j < 0) continue;
         unsigned long long *a = acc + 3 * (int64_t)j;
-        atomicAdd(a + 0, s_v[0][i]);
-        atomicAdd(a + 1, s_v[1][i]);
-        atomicAdd(a + 2, s_v[2][i]);
+        atomicAdd(a + 0, s_v[i]);
+        atomicAdd(a + 1, s_v[kAggSlots + i]);
+        atomicAdd(a + 2, s_v[2 * kAggSlots + i]);
     }
 }
 
+// 8 resident blocks per SM (64 registers): the search is a chain of
+// dependent loads that wants the warps
 template <int KMAX, bool FIXED>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, KMAX > 16 ? 1 : 8)
     k_knn_scatter(const float4 *__restrict__ faces, IterState *st, int64_t max_faces,
                   KnnTree T, int k, const int64_t *__restrict__ cell_off,
                   const int *__restrict__ cell_idx, double scale, unsigned long long *acc,
-                  int2 *defer, int budget, int *err)
+                  int2 *defer, int budget, int agg, int *err)
 {
     knn_scatter_body<KMAX, FIXED>(faces, st, max_faces, T, k, cell_off, cell_idx, scale, acc,
-                                  defer, budget, err, blockIdx.x);
+                                  defer, budget, agg != 0, err, blockIdx.x);
 }
 
 // The deferred faces, one block per face (the blocks take the list in
@@ -1690,16 +1722,20 @@ cudaError_t launch_knn_scatter(Ctx *c)
     const bool lists = c->knn_lists && c->cells_k == c->knn && c->d_cell_off;
     const int64_t *off = lists ? c->d_cell_off : nullptr;
     const int *idx = lists ? c->d_cell_idx : nullptr;
+    // the per-warp sum tables (dynamic shared memory) on clouds up to
+    // kAggMaxPoints; batched clouds always take them
+    const int agg = c->n <= kAggMaxPoints ? 1 : 0;
+    const size_t smem = agg ? kAggSmem : 0;
     if (c->knn == 10) {
-        k_knn_scatter<10, true><<<blocks, 128, 0, c->stream>>>(
+        k_knn_scatter<10, true><<<blocks, 128, smem, c->stream>>>(
             c->d_faces, c->d_state, c->max_faces, T, c->knn, off, idx, c->acc_scale, c->d_acc,
-            c->d_defer, c->knn_budget, c->d_err);
+            c->d_defer, c->knn_budget, agg, c->d_err);
         k_knn_deferred<10, true><<<kDeferBlocks, defer_threads<10>(), 0, c->stream>>>(
             c->d_faces, c->d_state, c->d_defer, T, c->knn, c->acc_scale, c->d_acc);
     } else {
-        k_knn_scatter<32, false><<<blocks, 128, 0, c->stream>>>(
+        k_knn_scatter<32, false><<<blocks, 128, smem, c->stream>>>(
             c->d_faces, c->d_state, c->max_faces, T, c->knn, off, idx, c->acc_scale, c->d_acc,
-            c->d_defer, c->knn_budget, c->d_err);
+            c->d_defer, c->knn_budget, agg, c->d_err);
         k_knn_deferred<32, false><<<kDeferBlocks, defer_threads<32>(), 0, c->stream>>>(
             c->d_faces, c->d_state, c->d_defer, T, c->knn, c->acc_scale, c->d_acc);
     }
@@ -1944,7 +1980,7 @@ __global__ void __launch_bounds__(128)
     const int ci = seg_cloud(off, ncl);
     const CloudIter &c = cl[ci];
     knn_scatter_body<KMAX, FIXED>(c.faces, c.st, c.max_faces, c.T, c.k, c.cell_off, c.cell_idx,
-                                  c.acc_scale, c.acc, c.defer, c.knn_budget, c.err,
+                                  c.acc_scale, c.acc, c.defer, c.knn_budget, true, c.err,
                                   (int64_t)blockIdx.x - off[ci]);
 }
 
@@ -2005,7 +2041,7 @@ cudaError_t launch_iter_batch(int phase, const CloudIter *cl, const int *off, in
     switch (phase) {
     case kPhIso: k_iso_b<<<(unsigned)ncl, 256, 0, s>>>(cl); break;
     case kPhMcFaces: k_mc_faces_b<<<g, 256, 0, s>>>(cl, off, ncl); break;
-    case kPhKnn: k_knn_scatter_b<10, true><<<g, 128, 0, s>>>(cl, off, ncl); break;
+    case kPhKnn: k_knn_scatter_b<10, true><<<g, 128, kAggSmem, s>>>(cl, off, ncl); break;
     case kPhKnnDefer:
         k_knn_deferred_b<<<g, defer_threads<10>(), 0, s>>>(cl, off, ncl);
         break;
