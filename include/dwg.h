@@ -393,7 +393,8 @@ typedef struct {
     double interactions_points_step;  /* dwg_profile_step: evaluations at the points */
     double interactions_corners_step; /* dwg_profile_step: evaluations at the corners */
     int kernels_per_iteration;        /* kernel launches in one iteration of the graph */
-    int knn_deferred_last;   /* faces of the last iteration whose search a block finished */
+    int knn_deferred_last;   /* faces of the last iteration handed to a block (dwg_set_knn_budget);
+                                beyond 65,536 the rest search alone */
 } dwg_stats;
 
 int dwg_get_stats(dwg_handle h, dwg_stats *out);
