@@ -57,6 +57,21 @@ FP32_OPS = {("w", 0): 12, ("wg", 0): 20, ("w", 1): 16, ("wg", 1): 27}
 FP32_LANES_PER_SM = 128
 
 
+def alu_peaks(what, kind, sm_count, fmax_hz, ffma=None, rsq=None, ex2=None):
+    """Interactions per second of an evaluator.  what: "w" or "wg"; kind: 0
+    plain, 1 screened.  derived: SMs x 128 FP32 lanes x clock / FP32
+    operations per interaction.  With the microbenchmarks' rates (packed-FMA
+    lane operations, MUFU rsqrt and ex2 per second): the FMA-pipe bound, the
+    MUFU bound (one rsqrt, and for the screened kernel one ex2, per
+    interaction) and the lower of the two."""
+    ops = FP32_OPS[(what, kind)]
+    out = {"ops": ops, "derived": sm_count * FP32_LANES_PER_SM * fmax_hz / ops}
+    if ffma is not None:
+        mufu = 1.0 / (1.0 / rsq + (1.0 / ex2 if kind else 0.0))
+        out.update(fma_bound=ffma / ops, mufu_bound=mufu, measured=min(ffma / ops, mufu))
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,10 +537,10 @@ def run_ours(args, rank, world, local):
         dom = "eval_corners" if kms.get("eval_corners", 0) >= kms["eval_points"] else "eval_points"
         if dom == "eval_corners":
             work = float(nc) * n
-            ops = FP32_OPS[("w", kind)]
+            what = "w"
         else:
             work = float(n) * n
-            ops = FP32_OPS[("wg", kind)]
+            what = "wg"
         achieved = work / (kms[dom] / 1e3)
         shape = f"corners_pairs={tuning['corners_pairs']},corners_threads={tuning['corners_threads']}"
         traffic_basis = "ncu dram bytes per launch (profiles/eval_corners_torus100k.md)"
@@ -537,9 +552,9 @@ def run_ours(args, rank, world, local):
         # points, w at the corners), its evaluations performed (counted on the
         # device during the profiled step) per second of its launch
         if kms.get("eval_corners", 0) >= kms["eval_points"]:
-            dom, work, ops = "eval_corners", st["interactions_corners_step"], FP32_OPS[("w", kind)]
+            dom, work, what = "eval_corners", st["interactions_corners_step"], "w"
         else:
-            dom, work, ops = "eval_points", st["interactions_points_step"], FP32_OPS[("wg", kind)]
+            dom, work, what = "eval_points", st["interactions_points_step"], "wg"
         dom += " (Barnes-Hut lists)"
         achieved = work / (kms[dom.split()[0]] / 1e3)
         # DRAM bytes of the same list kernel captured by ncu on metaballs-1m,
@@ -550,7 +565,8 @@ def run_ours(args, rank, world, local):
         traffic = bpi * work if (bpi is not None and tuning.get("tree_group")) else None
         traffic_basis = ("ncu dram bytes of k_tree_eval_lists on metaballs-1m per interaction "
                          "(profiles/tree_lists_metaballs1m.md) x this launch's interactions")
-    peak = lanes / ops
+    pk = alu_peaks(what, kind, sm_count, fmax)
+    ops, peak = pk["ops"], pk["derived"]
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "Ginteractions/s", "frac": achieved / peak, "traffic": traffic,
             "traffic_basis": traffic_basis,
@@ -562,14 +578,13 @@ def run_ours(args, rank, world, local):
     # the same denominator measured: packed-FMA and MUFU rsqrt microbenchmarks
     try:
         ffma, rsq, ex2 = dwg.dwg_measure_fp32_peaks(local)
-        # the MUFU time of one interaction: an rsqrt and, screened, an ex2
-        mufu_rate = 1.0 / (1.0 / rsq + (1.0 / ex2 if kind else 0.0))
-        pk_meas = min(ffma / ops, mufu_rate)
+        pm = alu_peaks(what, kind, sm_count, fmax, ffma, rsq, ex2)
         roof["fp32_measured"] = {
             "ffma_lane_ops_per_s": ffma, "rsqrt_per_s": rsq, "ex2_per_s": ex2,
             "derived_lane_ops_per_s": lanes, "ffma_over_derived": ffma / lanes,
-            "mufu_bound_interactions_per_s": mufu_rate,
-            "peak_from_measured": pk_meas / 1e9, "frac_of_measured": achieved / pk_meas}
+            "mufu_bound_interactions_per_s": pm["mufu_bound"],
+            "peak_from_measured": pm["measured"] / 1e9,
+            "frac_of_measured": achieved / pm["measured"]}
     except Exception as e:  # reported beside the derived peak, never instead of it
         roof["fp32_measured"] = {"error": str(e)}
 
