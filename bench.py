@@ -575,7 +575,7 @@ def run_ours(args, rank, world, local):
                           f"rsqrt and ex2 rates, is in fp32_measured)",
             "kernel_ms": {k: round(v, 4) for k, v in kms.items()},
             "share": {k: round(v / iter_ms, 4) for k, v in kms.items()}}
-    # the same denominator measured: packed-FMA and MUFU rsqrt microbenchmarks
+    # the same denominator measured: packed-FMA, MUFU rsqrt and ex2 microbenchmarks
     try:
         ffma, rsq, ex2 = dwg.dwg_measure_fp32_peaks(local)
         pm = alu_peaks(what, kind, sm_count, fmax, ffma, rsq, ex2)
